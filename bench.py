@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of Radic's determinant on one GB300 (or N, one process each).
+
+One step = one det_R call over the 8 x 32 binary64 workload (C(32,8) =
+10,518,300 signed minors): stage A and the binomial table, unrank, successor,
+gather, binary32 partial-pivot LU, sign, compensated accumulation, binary64
+recompute of flagged minors, fixed-order reduction.  The headline `value` is
+signed minors per second of this mixed path, beside the plain binary64 kernel
+on the same input, the relative error of each against the exact value
+(|err| / sum|terms|), and the fraction of the binary32 FMA roofline.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run; every rank computes its own
+determinant (independent problems, weak scaling, no collective on the data
+path) and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "signed minors/sec & % FMA peak, mixed vs plain FP64 GPU at stated rel err"
+UNIT = "minors/s"
+M, N = 8, 32
+MINORS = math.comb(N, M)
+FLOP_PER_MINOR = 2 * ((M - 1) * M * (2 * M - 1) // 6) + (M - 1) * M // 2 + (M - 1)  # 2*FMA + mul = 315
+# Binary32 FMA peak from unit counts and the maximum clock: 152 SMs x 128 lanes x 2 flop x 2.070 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+WORKLOAD = (f"fp64_8x32: one 8x32 binary64 matrix, entries uniform[-1,1) from numpy PCG64 seed 2, "
+            f"C(32,8)={MINORS} minors")
+ORACLE_SAMPLE_OFFSET = 1_000_000
+
+
+def golden(name: str) -> tuple[int, int, float]:
+    path = os.path.join(ROOT, "tests", "golden", "workload_exact.txt")
+    with open(path) as f:
+        for line in f:
+            p = line.split()
+            if p and p[0] == name:
+                return int(p[2]), int(p[3]), float(p[4])
+    raise KeyError(name)
+
+
+def rel_err(value: float, abs_sum: float, num: int, den: int) -> float:
+    from fractions import Fraction
+
+    return float(abs(Fraction(value) - Fraction(num, den))) / abs_sum
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled with nvidia-smi while the GPU works
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle baseline (CPU, spawn pool)
+# ---------------------------------------------------------------------------
+def _oracle_chunk(args):
+    lo, hi = args
+    sys.path.insert(0, ROOT)
+    import oracle.radic_oracle as orc
+    from paper_1508_01326_gb300 import workloads as W
+
+    terms = orc.radic_terms_exact(W.fp64_8x32(), range(lo, hi))
+    return hi - lo, float(sum(terms))
+
+
+def oracle_rate(pool, cores: int, sample: int, offset: int) -> float:
+    per = -(-sample // cores)
+    chunks = [(offset + i * per, min(offset + (i + 1) * per, offset + sample)) for i in range(cores)]
+    chunks = [c for c in chunks if c[0] < c[1]]
+    t0 = time.perf_counter()
+    done = sum(n for n, _ in pool.map(_oracle_chunk, chunks))
+    return done / (time.perf_counter() - t0)
+
+
+def make_pool():
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(cores)
+    pool.map(_oracle_chunk, [(0, 1)] * cores)  # import the oracle in every worker before timing
+    return pool, cores
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    pool, cores = make_pool()
+    sample = 4 * cores * 500
+    try:
+        for _ in range(args.warmup):
+            oracle_rate(pool, cores, sample, ORACLE_SAMPLE_OFFSET)
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            oracle_rate(pool, cores, sample, ORACLE_SAMPLE_OFFSET + s * sample)
+        dt = time.perf_counter() - t0
+    finally:
+        pool.terminate()
+    value = sample * args.steps / dt
+    desc = (f"exact Bareiss minors of Eq. (1) for {sample} consecutive dictionary ranks of the fp64_8x32 "
+            f"workload per step, split over {cores} spawn workers")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "exact", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "minors": MINORS, "mode": "oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank: int, world: int, local_rank: int) -> None:
+    import numpy as np
+    import torch
+
+    pool = None
+    cores = 0
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool, cores = make_pool()  # spawn context: safe to start before CUDA
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_1508_01326_gb300 import build as B
+
+    B.build()
+    import paper_1508_01326_gb300 as R
+    from paper_1508_01326_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+    A = torch.from_numpy(W.fp64_8x32()).cuda()
+    num, den, _ = golden("fp64_8x32")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    out_mixed = R.new_result()
+    out_fp64 = R.new_result()
+    ws_mixed = torch.empty(R.radic_workspace_bytes(M, N, "mixed"), dtype=torch.uint8, device="cuda")
+    ws_fp64 = torch.empty(R.radic_workspace_bytes(M, N, "fp64"), dtype=torch.uint8, device="cuda")
+    kev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    import ctypes
+
+    def timed_steps(mode, out, ws, steps, kernel_events=False):
+        step_ms, kern_ms = [], []
+        opts = None
+        if kernel_events:
+            for e in kev:
+                e.record(stream)  # materialise the events
+            handles = (ctypes.c_void_p * 2)(kev[0].cuda_event, kev[1].cuda_event)
+            opts = R.make_options(kernel_events=ctypes.addressof(handles))
+            timed_steps.handles = handles
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            R.radic_det(A, mode=mode, options=opts, out=out, workspace=ws, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            if kernel_events:
+                kern_ms.append(kev[0].elapsed_time(kev[1]))
+        return step_ms, kern_ms
+
+    sampler = ClockSampler(local_rank)
+    # warm-up: at least args.warmup steps and about one second of work so clocks settle
+    timed_steps("mixed", out_mixed, ws_mixed, args.warmup)
+    sampler.start()
+    t_end = time.time() + 1.0
+    while time.time() < t_end:
+        R.radic_det(A, mode="mixed", out=out_mixed, workspace=ws_mixed, stream=stream)
+    torch.cuda.synchronize()
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms, kern_ms = timed_steps("mixed", out_mixed, ws_mixed, args.steps, kernel_events=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * MINORS / (ms_per_step / 1e3)
+    res_mixed = R.parse_result(out_mixed)
+    err_mixed = rel_err(res_mixed["value"], res_mixed["abs_sum"], num, den)
+
+    # plain binary64 kernel on the same input
+    fp64_steps = max(3, args.steps // 4)
+    timed_steps("fp64", out_fp64, ws_fp64, 2)
+    f_ms, f_kern = timed_steps("fp64", out_fp64, ws_fp64, fp64_steps, kernel_events=True)
+    res_fp64 = R.parse_result(out_fp64)
+    err_fp64 = rel_err(res_fp64["value"], res_fp64["abs_sum"], num, den)
+    fp64_rate = MINORS / (statistics.mean(f_ms) / 1e3)
+
+    # end to end through the public API from pinned host memory
+    a_host = torch.from_numpy(W.fp64_8x32()).pin_memory()
+    res_host = torch.empty(16, dtype=torch.int64).pin_memory()
+    a_dev = torch.empty_like(A)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        a_dev.copy_(a_host, non_blocking=True)
+        R.radic_det(a_dev, mode="mixed", out=out_mixed, workspace=ws_mixed, stream=stream)
+        res_host.copy_(out_mixed, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_rate = world * MINORS / (statistics.mean(e2e_ms) / 1e3)
+
+    kern_mean_ms = statistics.mean(kern_ms)
+    achieved = FLOP_PER_MINOR * MINORS / (kern_mean_ms / 1e3) / 1e12
+    fp64_kern_ms = statistics.mean(f_kern)
+
+    cpu = None
+    if pool is not None:
+        sample = 160_000
+        rate = oracle_rate(pool, cores, sample, ORACLE_SAMPLE_OFFSET)
+        pool.terminate()
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"exact Bareiss minors of Eq. (1) for {sample} consecutive dictionary ranks "
+                         f"(from rank {ORACLE_SAMPLE_OFFSET}) of the same workload over {cores} spawn workers"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": M, "n": N, "minors": MINORS, "mode": "mixed",
+                       "l2": "flushed between timed iterations (256 MB write, untimed)",
+                       "parallelism": f"replicas{world}"},
+            "rel_err": err_mixed, "flagged": res_mixed["flagged"],
+            "fp64_plain": {"value": fp64_rate, "unit": UNIT, "rel_err": err_fp64,
+                           "kernel_ms": fp64_kern_ms, "speedup_mixed_over_fp64": value / world / fp64_rate},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_fp_thread<float,8,mixed>", "kernel_ms": kern_mean_ms,
+                         "flop_per_launch": FLOP_PER_MINOR * MINORS},
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": A.numel() * 8,
+                    "d2h_bytes_per_step": 16 * 8},
+            "gpu_launches": 2 * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * radic.h -- C ABI of the GB300 (sm_103a) library for Radic's determinant of
+ * a non-square matrix.
+ *
+ * Definition (Definition 3, Eq. (1) of Abdollahi, Jafari, Bayat, Amiri and
+ * Fathy, "An efficient parallel algorithm for computing determinant of
+ * non-square matrices based on Radic's definition", arXiv 1508.01326):
+ * for an m x n matrix A with m <= n,
+ *
+ *     det_R(A) = sum over 1 <= j1 < ... < jm <= n of
+ *                (-1)^(r+s) * det(A[:, j1..jm]),
+ *     r = 1 + 2 + ... + m,   s = j1 + ... + jm,
+ *
+ * and det_R(A) = 0 when m > n.  The C(n,m) column sequences are numbered
+ * 0 .. C(n,m)-1 in dictionary order (Definition 2, Table 2); each one is
+ * produced directly from its number (Section 4, Theorem 2), so every minor is
+ * independent of every other one and the GPU processes contiguous runs of
+ * numbers (Section 5).
+ *
+ * Conventions for every entry point below:
+ *  - Matrices are row-major: element (i, j) of A is A[i * lda + j], lda >= n.
+ *  - "device" pointers are CUDA device memory on the current device and are
+ *    owned by the caller; the library never frees them.  "host" pointers are
+ *    ordinary host memory.  Except where stated (radic_batch_graph_create),
+ *    the library allocates no memory: scratch memory is the caller's
+ *    `workspace` of at least the size that the matching *_workspace_bytes
+ *    function returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work on it and return without waiting; results
+ *    are valid once the stream reaches that point.
+ *  - The return value reports host-side validation and launch errors only
+ *    (RADIC_OK, RADIC_EINVAL, ...).  Errors found on the device are written
+ *    to the `status` field of the device-resident result.
+ *  - Limits: 1 <= m <= RADIC_MAX_M, 1 <= n <= RADIC_MAX_N.  m > n is valid
+ *    and gives 0 (Definition 3).  With n <= 64 every rank fits in 63 bits.
+ */
+#ifndef RADIC_H
+#define RADIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RADIC_MAX_M 32
+#define RADIC_MAX_N 64
+#define RADIC_MAX_PRIMES 4
+
+/* Status codes (return values and radic_result.status). */
+enum {
+  RADIC_OK = 0,
+  RADIC_EINVAL = 1,      /* bad argument: size, pointer, dtype, mode, lda     */
+  RADIC_EOVERFLOW = 2,   /* exact result may need more than the prime budget  */
+  RADIC_ECUDA = 3,       /* a CUDA runtime call failed                         */
+  RADIC_ETIMEOUT = 4,    /* a bounded device-side wait gave up                 */
+  RADIC_EWORKSPACE = 5,  /* workspace pointer null/misaligned or too small     */
+  RADIC_EUNSUPPORTED = 6 /* valid request this build does not implement        */
+};
+
+/* Element type of A. */
+enum { RADIC_I8 = 0, RADIC_I32 = 1, RADIC_F32 = 2, RADIC_F64 = 3 };
+
+/* Arithmetic of the minor determinants.
+ *  FP64  -- binary64 partial-pivot LU per minor, binary64 compensated sum.
+ *  MIXED -- binary32 partial-pivot LU per minor; minors whose pivot growth
+ *           exceeds the threshold, or whose result is not finite, are
+ *           recomputed in binary64; sums are compensated (float-float per
+ *           run of ranks, then binary64 two-sum across runs and blocks).
+ *  EXACT -- integer inputs only: LU modulo 31-bit primes (as many as a
+ *           Hadamard bound needs, at most RADIC_MAX_PRIMES) and Chinese
+ *           remaindering to a signed 128-bit integer, bit-exact. */
+enum { RADIC_MODE_FP64 = 0, RADIC_MODE_MIXED = 1, RADIC_MODE_EXACT = 2 };
+
+/* Minor-to-thread mapping.
+ *  THREAD -- one thread factors one minor in registers (m <= 8 for FP64,
+ *            m <= 12 for MIXED and EXACT).
+ *  GROUP  -- a group of `group_width` lanes of one warp (16 or 32) factors
+ *            one minor, one row per lane, pivot rows shared by warp shuffles.
+ *  AUTO   -- THREAD when m <= 8 (EXACT: m <= 12), GROUP above that. */
+enum { RADIC_MAP_AUTO = 0, RADIC_MAP_THREAD = 1, RADIC_MAP_GROUP = 2 };
+
+/* Launch and precision options.  Pass NULL for the defaults; a zero field
+ * also means "default". */
+typedef struct radic_options {
+  int32_t mapping;          /* RADIC_MAP_*                                    */
+  int32_t group_width;      /* GROUP mapping: 16 or 32 lanes per minor        */
+  int32_t ranks_per_task;   /* consecutive ranks per task (default 64)        */
+  int32_t threads_per_block;/* 32..256 (EXACT: ..128), multiple of 32 (128)   */
+  int32_t blocks;           /* grid size (default: SMs x resident blocks)     */
+  int32_t flag_capacity;    /* MIXED: flagged ranks kept per warp (default 32)*/
+  double growth_threshold;  /* MIXED: flag when max|pivot| > t * max|a| (64)  */
+  void* kernel_events;      /* optional: two cudaEvent_t recorded on the
+                               stream right before and right after the main
+                               per-minor kernel (profiling hook)             */
+  int64_t reserved[3];
+} radic_options;
+
+/* Device-resident result of one determinant (16 eight-byte words). */
+typedef struct radic_result {
+  double value;     /* det_R(A) rounded to binary64 (EXACT: from exact value)  */
+  double abs_sum;   /* sum over J of |det(A[:, J])| in the mode's arithmetic   */
+  double err_est;   /* a-priori error estimate m * u * abs_sum (not a bound)   */
+  int64_t exact_lo; /* EXACT: low 64 bits of det_R(A), two's complement int128 */
+  int64_t exact_hi; /* EXACT: high 64 bits                                     */
+  int64_t minors;   /* C(n, m), or 0 when m > n                                */
+  int64_t flagged;  /* MIXED: minors recomputed in binary64                    */
+  int64_t status;   /* RADIC_OK, RADIC_EOVERFLOW, RADIC_ETIMEOUT ...           */
+  int64_t n_primes; /* EXACT: primes used                                      */
+  int64_t tier;     /* mode that produced value (batched router decision)      */
+  int64_t reserved[6];
+} radic_result;
+
+/* ---- general ------------------------------------------------------------ */
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* radic_status_string(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int radic_version(void);
+
+/* The 31-bit primes of the EXACT mode, in the order they are used.
+ * primes: host array of at least max_count entries.  Returns how many
+ * primes were written (at most RADIC_MAX_PRIMES). */
+int radic_primes(uint32_t* primes, int max_count);
+
+/* ---- one matrix --------------------------------------------------------- */
+
+/* Bytes of workspace radic_det needs for this shape, mode and options
+ * (a multiple of 256; the workspace must be 256-byte aligned).  Returns 0
+ * for invalid arguments. */
+size_t radic_workspace_bytes(int m, int n, int mode, const radic_options* opts);
+
+/* det_R(A) of one m x n matrix (Eq. (1)).
+ * A:        device, m x n, row-major with leading dimension lda, type dtype.
+ * out:      device, one radic_result, fully overwritten.
+ * workspace:device scratch, >= radic_workspace_bytes(m, n, mode, opts).
+ * The hot path per minor: unrank its dictionary-order number with a binomial
+ * table staged in shared memory (Section 4), step to the next numbers with
+ * the dictionary successor (Section 5), gather the m x m minor from shared
+ * memory, factor it (LU with partial pivoting, or modular elimination),
+ * apply the sign (-1)^(r+s), and accumulate; per-block partial sums are
+ * combined in a fixed order by the last block (tree sum of Section 6).
+ * Calls on different streams need separate workspaces.
+ * Errors: RADIC_EINVAL (m or n out of range, lda < n, NULL A or out,
+ * unknown dtype/mode, EXACT with a real dtype), RADIC_EWORKSPACE,
+ * RADIC_ECUDA.  Device: out->status = RADIC_EOVERFLOW when the exact value
+ * could exceed the prime budget. */
+int radic_det(const void* A, int m, int n, int64_t lda, int dtype, int mode,
+              const radic_options* opts, radic_result* out, void* workspace,
+              size_t workspace_bytes, void* stream);
+
+/* The signed terms (-1)^(r+s) det(A[:, J_q]) of Eq. (1) for the consecutive
+ * dictionary ranks q = q0 .. q0+count-1 (all < C(n,m)), computed by the same
+ * per-minor device code as radic_det with the same options.
+ * terms: device.  FP64: count doubles.  MIXED: count doubles holding the
+ *        binary32 results (flagged minors are not recomputed here; a NaN
+ *        marks each flagged minor).  EXACT: RADIC_MAX_PRIMES x count uint32
+ *        residues in [0, p), prime-major in the order of radic_primes; only
+ *        the first K rows are written, K being the number of primes
+ *        radic_det uses for this A (radic_result.n_primes).
+ * No workspace.  Errors: RADIC_EINVAL (as radic_det, or a rank outside
+ * [0, C(n,m))), RADIC_ECUDA. */
+int radic_terms(const void* A, int m, int n, int64_t lda, int dtype, int mode,
+                const radic_options* opts, uint64_t q0, uint64_t count,
+                void* terms, void* stream);
+
+/* Column sequences of the dictionary ranks q0 .. q0+count-1 (Section 4 and
+ * the successor of Section 5), as the device computes them.
+ * cols: device, count x m bytes, 0-based column indices.
+ * Errors: RADIC_EINVAL (bad sizes or a rank outside [0, C(n,m))),
+ * RADIC_ECUDA. */
+int radic_unrank(int n, int m, uint64_t q0, uint64_t count, uint8_t* cols,
+                 const radic_options* opts, void* stream);
+
+#ifdef __cplusplus
+} /* extern "C" */
+#endif
+
+#endif /* RADIC_H */

@@ -1,0 +1,149 @@
+"""Python binding of the C ABI (include/radic.h): same entry-point names, torch
+tensors in and out.  PyTorch supplies device memory and streams only; every
+step of the computation runs in libradic.so.  There is no CPU fallback: when
+the library is missing or CUDA is unavailable these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from fractions import Fraction
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_TORCH_DTYPES = {torch.int8: 0, torch.int32: 1, torch.float32: 2, torch.float64: 3}
+_NP_TO_TORCH = {np.dtype(np.int8): torch.int8, np.dtype(np.int32): torch.int32,
+                np.dtype(np.float32): torch.float32, np.dtype(np.float64): torch.float64}
+
+
+def _mode(mode) -> int:
+    return L.MODES[mode] if isinstance(mode, str) else int(mode)
+
+
+def _opts(options) -> Optional[ctypes.POINTER(L.RadicOptions)]:
+    if options is None:
+        return None
+    if isinstance(options, dict):
+        options = L.make_options(**options)
+    return ctypes.pointer(options)
+
+
+def _stream(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check_matrix(A: torch.Tensor) -> None:
+    if not isinstance(A, torch.Tensor) or not A.is_cuda:
+        raise TypeError("A must be a CUDA tensor")
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a 2-D row-major tensor with unit column stride")
+    if A.dtype not in _TORCH_DTYPES:
+        raise TypeError(f"unsupported dtype {A.dtype}")
+
+
+def radic_status_string(code: int) -> str:
+    return L.lib().radic_status_string(int(code)).decode()
+
+
+def radic_version() -> int:
+    return L.lib().radic_version()
+
+
+def radic_primes() -> list:
+    buf = (ctypes.c_uint32 * L.RADIC_MAX_PRIMES)()
+    k = L.lib().radic_primes(buf, L.RADIC_MAX_PRIMES)
+    return [int(buf[i]) for i in range(k)]
+
+
+def radic_workspace_bytes(m: int, n: int, mode="fp64", options=None) -> int:
+    return int(L.lib().radic_workspace_bytes(int(m), int(n), _mode(mode), _opts(options)))
+
+
+def new_result(device=None) -> torch.Tensor:
+    """Device buffer for one radic_result (sixteen int64 words)."""
+    return torch.empty(L.RESULT_WORDS, dtype=torch.int64, device=device or "cuda")
+
+
+def radic_det(A: torch.Tensor, mode="fp64", options=None, out: Optional[torch.Tensor] = None,
+              workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Enqueues det_R(A) on `stream`; returns the device result buffer (not synchronised)."""
+    _check_matrix(A)
+    m, n = A.shape
+    md = _mode(mode)
+    lib = L.lib()
+    if out is None:
+        out = new_result(A.device)
+    ws_bytes = int(lib.radic_workspace_bytes(int(m), int(n), md, _opts(options)))
+    if workspace is None:
+        workspace = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=A.device)
+    rc = lib.radic_det(A.data_ptr(), int(m), int(n), int(A.stride(0)), _TORCH_DTYPES[A.dtype], md, _opts(options),
+                       out.data_ptr(), workspace.data_ptr(), workspace.numel(), _stream(stream))
+    L.check("radic_det", rc)
+    return out
+
+
+def radic_terms(A: torch.Tensor, q0: int, count: int, mode="fp64", options=None,
+                out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Signed terms of Eq. (1) for dictionary ranks q0 .. q0+count-1 (device tensor)."""
+    _check_matrix(A)
+    m, n = A.shape
+    md = _mode(mode)
+    if out is None:
+        if md == L.MODES["exact"]:
+            out = torch.zeros((L.RADIC_MAX_PRIMES, max(int(count), 1)), dtype=torch.int32, device=A.device)
+        else:
+            out = torch.empty(max(int(count), 1), dtype=torch.float64, device=A.device)
+    rc = L.lib().radic_terms(A.data_ptr(), int(m), int(n), int(A.stride(0)), _TORCH_DTYPES[A.dtype], md,
+                             _opts(options), int(q0), int(count), out.data_ptr(), _stream(stream))
+    L.check("radic_terms", rc)
+    return out
+
+
+def radic_unrank(n: int, m: int, q0: int, count: int, options=None, out: Optional[torch.Tensor] = None,
+                 stream=None, device="cuda") -> torch.Tensor:
+    """Column sequences (0-based) of dictionary ranks q0 .. q0+count-1, shape (count, m), uint8."""
+    if out is None:
+        out = torch.empty((max(int(count), 1), int(m)), dtype=torch.uint8, device=device)
+    rc = L.lib().radic_unrank(int(n), int(m), int(q0), int(count), out.data_ptr(), _opts(options), _stream(stream))
+    L.check("radic_unrank", rc)
+    return out
+
+
+def parse_result(buf: torch.Tensor) -> dict:
+    """Host dictionary of a radic_result buffer (copies it to the host)."""
+    w = buf.detach().to("cpu").contiguous()
+    f = w.view(torch.float64)
+    lo = int(w[3]) & ((1 << 64) - 1)
+    hi = int(w[4])
+    exact = (hi << 64) | lo
+    return {
+        "value": float(f[0]),
+        "abs_sum": float(f[1]),
+        "err_est": float(f[2]),
+        "exact": exact,
+        "minors": int(w[5]),
+        "flagged": int(w[6]),
+        "status": int(w[7]),
+        "n_primes": int(w[8]),
+        "tier": int(w[9]),
+    }
+
+
+def det(A, mode="fp64", options=None, stream=None) -> dict:
+    """Convenience call: host (numpy) or device input, synchronises and returns a dict.
+
+    A host array is copied to the device first (this is the end-to-end path).
+    """
+    if isinstance(A, np.ndarray):
+        A = torch.from_numpy(np.ascontiguousarray(A)).to("cuda")
+    out = radic_det(A, mode=mode, options=options, stream=stream)
+    res = parse_result(out)
+    if res["status"] != 0:
+        raise L.RadicError("radic_det (device)", res["status"])
+    if _mode(mode) == L.MODES["exact"]:
+        res["value_exact"] = Fraction(res["exact"])
+    return res

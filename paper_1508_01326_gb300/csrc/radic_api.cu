@@ -1,0 +1,344 @@
+// C-ABI entry points of the single-matrix path: argument validation, launch
+// planning (mapping, grid, workspace layout) and launches.  Validation happens
+// entirely on the host before anything is enqueued.
+#include <cstring>
+
+#include "radic_device.cuh"
+
+namespace radic {
+
+unsigned long long binom_host(int n, int k) {
+  if (k < 0 || k > n) return 0ull;
+  unsigned long long c[kMaxN + 1] = {1ull};
+  for (int v = 1; v <= n; ++v)
+    for (int j = (v < k ? v : k); j >= 1; --j) c[j] += c[j - 1];
+  return c[k];
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+namespace {
+
+bool valid_dtype(int d) { return d == kI8 || d == kI32 || d == kF32 || d == kF64; }
+bool valid_mode(int md) { return md == kModeFp64 || md == kModeMixed || md == kModeExact; }
+
+int thread_limit(int mode) {
+  return mode == kModeFp64 ? kThreadMaxMFp64 : (mode == kModeMixed ? kThreadMaxMFp32 : kThreadMaxMModp);
+}
+
+int blocks_per_sm(const SinglePlan& p) {
+  switch (p.mode) {
+    case kModeFp64: return blocks_per_sm_fp64(p);
+    case kModeMixed: return blocks_per_sm_mixed(p);
+    default: return blocks_per_sm_modp(p);
+  }
+}
+
+size_t smem_of(const SinglePlan& p) {
+  switch (p.mode) {
+    case kModeFp64: return smem_fp64(p);
+    case kModeMixed: return smem_mixed(p);
+    default: return smem_modp(p);
+  }
+}
+
+// Plans a launch over `units` ranks (C(n,m) for radic_det, `count` for
+// radic_terms).  Returns a RADIC_* code.
+int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long units, SinglePlan* p) {
+  if (m < 1 || m > kMaxM || n < 1 || n > kMaxN || !valid_mode(mode)) return RADIC_EINVAL;
+  radic_options d;
+  std::memset(&d, 0, sizeof(d));
+  if (o) d = *o;
+  SinglePlan pl;
+  pl.mode = mode;
+  pl.m = m;
+  pl.n = n;
+  pl.total = (m <= n) ? binom_host(n, m) : 0ull;
+  const int auto_limit = (mode == kModeExact) ? kThreadMaxMModp : 8;
+  int mapping = d.mapping ? d.mapping : (m <= auto_limit ? RADIC_MAP_THREAD : RADIC_MAP_GROUP);
+  if (mapping != RADIC_MAP_THREAD && mapping != RADIC_MAP_GROUP) return RADIC_EINVAL;
+  if (mapping == RADIC_MAP_THREAD && m > thread_limit(mode)) return RADIC_EUNSUPPORTED;
+  pl.mapping = mapping;
+  if (mapping == RADIC_MAP_GROUP) {
+    const int gw = d.group_width ? d.group_width : (m <= 16 ? 16 : 32);
+    if ((gw != 16 && gw != 32) || gw < m) return RADIC_EINVAL;
+    pl.group = gw;
+  }
+  const int max_threads = (mode == kModeExact) ? 128 : 256;
+  pl.threads = d.threads_per_block ? d.threads_per_block : 128;
+  if (pl.threads < 32 || pl.threads > max_threads || pl.threads % 32) return RADIC_EINVAL;
+  pl.ranks_per_task = d.ranks_per_task ? d.ranks_per_task : 64;
+  if (pl.ranks_per_task < 1 || pl.ranks_per_task > (1 << 20)) return RADIC_EINVAL;
+  pl.flag_cap = d.flag_capacity ? d.flag_capacity : 32;
+  if (pl.flag_cap < 1 || pl.flag_cap > (1 << 16)) return RADIC_EINVAL;
+  pl.growth = d.growth_threshold > 0.0 ? d.growth_threshold : 64.0;
+  pl.events = d.kernel_events;
+  pl.tasks = (units + pl.ranks_per_task - 1) / pl.ranks_per_task;
+  pl.smem = smem_of(pl);
+
+  const int sms = device_sm_count();
+  const int per_sm = blocks_per_sm(pl);
+  if (sms <= 0) return RADIC_ECUDA;
+  if (per_sm <= 0) return RADIC_EUNSUPPORTED;
+  const unsigned long long per_block =
+      (mapping == RADIC_MAP_THREAD) ? (unsigned long long)pl.threads : (unsigned long long)(pl.threads / pl.group);
+  const unsigned long long need = (pl.tasks + per_block - 1) / per_block;
+  const unsigned long long cap = (unsigned long long)sms * per_sm;
+  unsigned long long blocks = need < cap ? need : cap;
+  if (d.blocks > 0) blocks = (unsigned long long)d.blocks;
+  if (blocks < 1) blocks = 1;
+  if (blocks > (1ull << 20)) return RADIC_EINVAL;
+  pl.blocks = (int)blocks;
+  pl.blocks2 = sms * 4;
+
+  const int n_warps = pl.blocks * pl.threads / 32;
+  size_t off = 256;
+  pl.off_partials = off;
+  off = align_up(off + (size_t)pl.blocks * sizeof(FpPartial), 256);
+  if (mode == kModeMixed) {
+    pl.off_partials2 = off;
+    off = align_up(off + (size_t)pl.blocks2 * sizeof(FpPartial), 256);
+    pl.off_flag_count = off;
+    off = align_up(off + (size_t)n_warps * sizeof(int), 256);
+    pl.off_flag_ranks = off;
+    off = align_up(off + (size_t)n_warps * pl.flag_cap * sizeof(unsigned long long), 256);
+  }
+  if (mode == kModeExact) {
+    pl.off_modp = off;
+    off = align_up(off + (size_t)pl.blocks * kMaxPrimes * sizeof(uint32_t), 256);
+  }
+  pl.ws_bytes = off;
+  *p = pl;
+  return RADIC_OK;
+}
+
+__global__ void k_zero_result(radic_result* out, int tier) {
+  out->value = 0.0;
+  out->abs_sum = 0.0;
+  out->err_est = 0.0;
+  out->exact_lo = 0;
+  out->exact_hi = 0;
+  out->minors = 0;
+  out->flagged = 0;
+  out->status = RADIC_OK;
+  out->n_primes = (tier == kModeExact) ? 1 : 0;
+  out->tier = tier;
+  for (int i = 0; i < 6; ++i) out->reserved[i] = 0;
+}
+
+template <int M>
+__global__ void k_unrank(int n, unsigned long long q0, unsigned long long count, int L, uint8_t* cols) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* binom = reinterpret_cast<uint64_t*>(smem_raw);
+  build_binom(binom, n, M);
+  const unsigned long long tasks = (count + L - 1) / L;
+  const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += nthreads) {
+    unsigned long long q = q0 + t * L;
+    const unsigned long long q1 = min(q + L, q0 + count);
+    int c[M];
+    unrank<M>(q, n, binom, M + 1, c);
+    for (; q < q1; ++q) {
+#pragma unroll
+      for (int i = 0; i < M; ++i) cols[(q - q0) * M + i] = static_cast<uint8_t>(c[i]);
+      if (q + 1 < q1) successor<M>(c, n);
+    }
+  }
+}
+
+template <int G>
+__global__ void k_unrank_dyn(int n, int m, unsigned long long q0, unsigned long long count, int L, uint8_t* cols) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* binom = reinterpret_cast<uint64_t*>(smem_raw);
+  build_binom(binom, n, m);
+  const unsigned long long tasks = (count + L - 1) / L;
+  const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += nthreads) {
+    unsigned long long q = q0 + t * L;
+    const unsigned long long q1 = min(q + L, q0 + count);
+    int c[G];
+    unrank_dyn<G>(q, n, m, binom, m + 1, c);
+    for (; q < q1; ++q) {
+#pragma unroll
+      for (int i = 0; i < G; ++i)
+        if (i < m) cols[(q - q0) * m + i] = static_cast<uint8_t>(c[i]);
+      if (q + 1 < q1) successor_dyn<G>(c, n, m);
+    }
+  }
+}
+
+const void* unrank_kernel(int m) {
+  switch (m) {
+    case 1: return reinterpret_cast<const void*>(&k_unrank<1>);
+    case 2: return reinterpret_cast<const void*>(&k_unrank<2>);
+    case 3: return reinterpret_cast<const void*>(&k_unrank<3>);
+    case 4: return reinterpret_cast<const void*>(&k_unrank<4>);
+    case 5: return reinterpret_cast<const void*>(&k_unrank<5>);
+    case 6: return reinterpret_cast<const void*>(&k_unrank<6>);
+    case 7: return reinterpret_cast<const void*>(&k_unrank<7>);
+    case 8: return reinterpret_cast<const void*>(&k_unrank<8>);
+    case 9: return reinterpret_cast<const void*>(&k_unrank<9>);
+    case 10: return reinterpret_cast<const void*>(&k_unrank<10>);
+    case 11: return reinterpret_cast<const void*>(&k_unrank<11>);
+    case 12: return reinterpret_cast<const void*>(&k_unrank<12>);
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+int launch_unrank(int n, int m, unsigned long long q0, unsigned long long count, uint8_t* cols, int L,
+                  cudaStream_t s) {
+  const int sms = device_sm_count();
+  if (sms <= 0) return RADIC_ECUDA;
+  const unsigned long long tasks = (count + L - 1) / L;
+  unsigned long long blocks = (tasks + 127) / 128;
+  if (blocks > (unsigned long long)sms * 8) blocks = (unsigned long long)sms * 8;
+  if (blocks < 1) blocks = 1;
+  const size_t smem = (size_t)(n + 1) * (m + 1) * 8;
+  unsigned long long qq = q0, cc = count;
+  int nn = n, mm = m, ll = L;
+  cudaError_t e;
+  if (const void* k = unrank_kernel(m)) {
+    void* params[] = {&nn, &qq, &cc, &ll, &cols};
+    e = cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(128), params, smem, s);
+  } else {
+    void* params[] = {&nn, &mm, &qq, &cc, &ll, &cols};
+    const void* k2 = (m <= 16) ? reinterpret_cast<const void*>(&k_unrank_dyn<16>)
+                               : reinterpret_cast<const void*>(&k_unrank_dyn<32>);
+    e = cudaLaunchKernel(k2, dim3((unsigned)blocks), dim3(128), params, smem, s);
+  }
+  return e == cudaSuccess ? RADIC_OK : RADIC_ECUDA;
+}
+
+}  // namespace radic
+
+using namespace radic;
+
+extern "C" {
+
+const char* radic_status_string(int status) {
+  switch (status) {
+    case RADIC_OK: return "ok";
+    case RADIC_EINVAL: return "invalid argument";
+    case RADIC_EOVERFLOW: return "exact value may exceed the prime budget";
+    case RADIC_ECUDA: return "CUDA runtime error";
+    case RADIC_ETIMEOUT: return "device-side wait timed out";
+    case RADIC_EWORKSPACE: return "workspace missing, misaligned or too small";
+    case RADIC_EUNSUPPORTED: return "unsupported combination of arguments";
+    default: return "unknown status";
+  }
+}
+
+int radic_version(void) { return 10000; }
+
+int radic_primes(uint32_t* primes, int max_count) {
+  if (!primes || max_count <= 0) return 0;
+  const int k = max_count < kMaxPrimes ? max_count : kMaxPrimes;
+  for (int i = 0; i < k; ++i) primes[i] = kPrimes[i];
+  return k;
+}
+
+size_t radic_workspace_bytes(int m, int n, int mode, const radic_options* opts) {
+  SinglePlan p;
+  if (make_plan(m, n, mode, opts, (m <= n && n <= kMaxN && m >= 1) ? binom_host(n, m) : 0ull, &p) != RADIC_OK)
+    return 0;
+  return p.ws_bytes;
+}
+
+int radic_det(const void* A, int m, int n, int64_t lda, int dtype, int mode, const radic_options* opts,
+              radic_result* out, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!A || !out || lda < n || !valid_dtype(dtype)) return RADIC_EINVAL;
+  if (mode == kModeExact && (dtype == kF32 || dtype == kF64)) return RADIC_EINVAL;
+  SinglePlan p;
+  const unsigned long long total = (m >= 1 && n >= 1 && m <= n && n <= kMaxN) ? binom_host(n, m) : 0ull;
+  const int rc = make_plan(m, n, mode, opts, total, &p);
+  if (rc != RADIC_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p.total == 0) {
+    k_zero_result<<<1, 1, 0, s>>>(out, mode);
+    return cudaGetLastError() == cudaSuccess ? RADIC_OK : RADIC_ECUDA;
+  }
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u) || workspace_bytes < p.ws_bytes)
+    return RADIC_EWORKSPACE;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  if (cudaMemsetAsync(ws, 0, 256, s) != cudaSuccess) return RADIC_ECUDA;
+  SingleArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.A = A;
+  a.lda = lda;
+  a.dtype = dtype;
+  a.m = m;
+  a.n = n;
+  a.ranks_per_task = p.ranks_per_task;
+  a.total = p.total;
+  a.tasks = p.tasks;
+  a.growth = p.growth;
+  a.flag_cap = p.flag_cap;
+  a.n_warps = p.blocks * p.threads / 32;
+  a.hdr = reinterpret_cast<WsHeader*>(ws);
+  a.partials = reinterpret_cast<FpPartial*>(ws + p.off_partials);
+  a.partials2 = reinterpret_cast<FpPartial*>(ws + p.off_partials2);
+  a.flag_count = reinterpret_cast<int*>(ws + p.off_flag_count);
+  a.flag_ranks = reinterpret_cast<unsigned long long*>(ws + p.off_flag_ranks);
+  a.modp_partials = reinterpret_cast<uint32_t*>(ws + p.off_modp);
+  a.out = out;
+  int r;
+  switch (mode) {
+    case kModeFp64: r = launch_fp64(p, a, s); break;
+    case kModeMixed: r = launch_mixed(p, a, s); break;
+    default: r = launch_modp(p, a, s); break;
+  }
+  return r;
+}
+
+int radic_terms(const void* A, int m, int n, int64_t lda, int dtype, int mode, const radic_options* opts,
+                uint64_t q0, uint64_t count, void* terms, void* stream) {
+  if (!A || !terms || lda < n || !valid_dtype(dtype)) return RADIC_EINVAL;
+  if (mode == kModeExact && (dtype == kF32 || dtype == kF64)) return RADIC_EINVAL;
+  if (m < 1 || n < 1 || m > n || n > kMaxN || m > kMaxM) return RADIC_EINVAL;
+  const unsigned long long total = binom_host(n, m);
+  if (q0 >= total || count > total - q0) return RADIC_EINVAL;
+  if (count == 0) return RADIC_OK;
+  SinglePlan p;
+  const int rc = make_plan(m, n, mode, opts, count, &p);
+  if (rc != RADIC_OK) return rc;
+  SingleArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.A = A;
+  a.lda = lda;
+  a.dtype = dtype;
+  a.m = m;
+  a.n = n;
+  a.ranks_per_task = p.ranks_per_task;
+  a.total = total;
+  a.tasks = p.tasks;
+  a.growth = p.growth;
+  a.flag_cap = p.flag_cap;
+  a.q0 = q0;
+  a.count = count;
+  a.terms = terms;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (mode) {
+    case kModeFp64: return launch_fp64(p, a, s);
+    case kModeMixed: return launch_mixed(p, a, s);
+    default: return launch_modp(p, a, s);
+  }
+}
+
+int radic_unrank(int n, int m, uint64_t q0, uint64_t count, uint8_t* cols, const radic_options* opts,
+                 void* stream) {
+  if (!cols || m < 1 || n < 1 || m > n || n > kMaxN || m > kMaxM) return RADIC_EINVAL;
+  const unsigned long long total = binom_host(n, m);
+  if (q0 >= total || count > total - q0) return RADIC_EINVAL;
+  if (count == 0) return RADIC_OK;
+  const int L = (opts && opts->ranks_per_task > 0) ? opts->ranks_per_task : 64;
+  return launch_unrank(n, m, q0, count, cols, L, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

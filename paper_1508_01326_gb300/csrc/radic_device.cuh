@@ -1,0 +1,370 @@
+// Device building blocks shared by the Radic-determinant kernels (sm_103a).
+//
+// Notation follows arXiv 1508.01326: an m x n matrix A, column sequences
+// J = (j1 < ... < jm) numbered 0 .. C(n,m)-1 in dictionary order (Definition
+// 2), the sign (-1)^(r+s) of Eq. (1), and the binomial table of Section 4.
+// All column indices here are 0-based.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "radic_internal.h"
+
+namespace radic {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Binomial table (Section 4, Table 1 / Fig. 1): binom[v * stride + k] = C(v, k)
+// for 0 <= v <= n, 0 <= k <= kmax, built in shared memory by the Pascal
+// recurrence, one table row per step.  Every thread of the block must call.
+// ---------------------------------------------------------------------------
+__device__ inline void build_binom(uint64_t* binom, int n, int kmax) {
+  const int stride = kmax + 1;
+  for (int v = 0; v <= n; ++v) {
+    for (int k = threadIdx.x; k <= kmax; k += blockDim.x) {
+      uint64_t val;
+      if (k == 0) val = 1;
+      else if (v == 0) val = 0;
+      else val = binom[(v - 1) * stride + k - 1] + binom[(v - 1) * stride + k];
+      binom[v * stride + k] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Unranking.  The paper's "combinatorial addition" (Section 4) walks left in
+// the Pascal table; the same map is reached in closed form through the
+// combinatorial number system: with r = C(n,m) - 1 - q, position i takes the
+// largest v with C(v, m-i) <= r, sets j_i = n - 1 - v and subtracts C(v, m-i).
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void unrank(uint64_t q, int n, const uint64_t* binom, int bstride,
+                                       int (&c)[M]) {
+  uint64_t r = binom[n * bstride + M] - 1 - q;
+  int v = n;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const int k = M - i;
+    int w = v - 1;
+    uint64_t b = binom[w * bstride + k];
+    while (b > r) {
+      --w;
+      b = binom[w * bstride + k];
+    }
+    c[i] = n - 1 - w;
+    r -= b;
+    v = w;
+  }
+}
+
+// Dynamic-m form for the group mapping (c has capacity G >= m).
+template <int G>
+__device__ __forceinline__ void unrank_dyn(uint64_t q, int n, int m, const uint64_t* binom,
+                                           int bstride, int (&c)[G]) {
+  uint64_t r = binom[n * bstride + m] - 1 - q;
+  int v = n;
+#pragma unroll
+  for (int i = 0; i < G; ++i) {
+    if (i < m) {
+      const int k = m - i;
+      int w = v - 1;
+      uint64_t b = binom[w * bstride + k];
+      while (b > r) {
+        --w;
+        b = binom[w * bstride + k];
+      }
+      c[i] = n - 1 - w;
+      r -= b;
+      v = w;
+    }
+  }
+}
+
+// Dictionary successor (Section 5, "dictionary sequence"): the rightmost
+// position below its maximum n-m+i moves up by one and the positions after it
+// follow consecutively.  Must not be called on the last sequence.
+template <int M>
+__device__ __forceinline__ void successor(int (&c)[M], int n) {
+  int pos = 0;
+#pragma unroll
+  for (int t = 0; t < M; ++t)
+    if (c[t] < n - M + t) pos = t;
+#pragma unroll
+  for (int t = 0; t < M; ++t) {
+    if (t == pos) c[t] += 1;
+    if (t > 0 && t > pos) c[t] = c[t - 1] + 1;
+  }
+}
+
+template <int G>
+__device__ __forceinline__ void successor_dyn(int (&c)[G], int n, int m) {
+  int pos = 0;
+#pragma unroll
+  for (int t = 0; t < G; ++t)
+    if (t < m && c[t] < n - m + t) pos = t;
+#pragma unroll
+  for (int t = 0; t < G; ++t) {
+    if (t == pos) c[t] += 1;
+    if (t > 0 && t > pos && t < m) c[t] = c[t - 1] + 1;
+  }
+}
+
+// (-1)^(r+s) of Eq. (1): r = m(m+1)/2 and s = sum of the 1-based indices,
+// i.e. sum(c_i + 1).  Returns true when the sign is negative.
+template <int M>
+__device__ __forceinline__ bool sign_negative(const int (&c)[M]) {
+  int s = M * (M + 1) / 2 + M;
+#pragma unroll
+  for (int t = 0; t < M; ++t) s += c[t];
+  return s & 1;
+}
+
+template <int G>
+__device__ __forceinline__ bool sign_negative_dyn(const int (&c)[G], int m) {
+  int s = m * (m + 1) / 2 + m;
+#pragma unroll
+  for (int t = 0; t < G; ++t)
+    if (t < m) s += c[t];
+  return s & 1;
+}
+
+// ---------------------------------------------------------------------------
+// Reciprocals.  Hardware approximation refined by Newton-Raphson iterations
+// x <- x + x (1 - d x) (quadratic convergence); a zero pivot gives 0 so that
+// the elimination of an all-zero column stays finite.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_f32(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return d == 0.0f ? 0.0f : r;
+}
+
+__device__ __forceinline__ double rcp_f64(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  return d == 0.0 ? 0.0 : r;
+}
+
+// Magnitude keys for pivot comparisons that stay off the FP64 pipe: the high
+// word of |x| orders binary64 magnitudes up to ties within 2^-20.
+__device__ __forceinline__ uint32_t mag_key(double x) {
+  return static_cast<uint32_t>(__double2hiint(x)) & 0x7fffffffu;
+}
+__device__ __forceinline__ uint32_t mag_key(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+
+// ---------------------------------------------------------------------------
+// Partial-pivot LU of one m x m minor held in registers (thread mapping).
+// Row exchanges are branch-free compare-and-swap steps that bubble the
+// largest remaining |a_ik| into row k.  Returns det; `gmax` receives the
+// largest pivot magnitude (growth check of the MIXED mode).
+// ---------------------------------------------------------------------------
+template <typename T, int M>
+__device__ __forceinline__ T lu_det(T (&a)[M][M], T& gmax) {
+  T det = T(1);
+  bool neg = false;
+  gmax = T(0);
+#pragma unroll
+  for (int k = 0; k < M - 1; ++k) {
+#pragma unroll
+    for (int i = k + 1; i < M; ++i) {
+      const bool sw = mag_key(a[i][k]) > mag_key(a[k][k]);
+#pragma unroll
+      for (int j = k; j < M; ++j) {
+        const T x = a[k][j], y = a[i][j];
+        a[k][j] = sw ? y : x;
+        a[i][j] = sw ? x : y;
+      }
+      neg ^= sw;
+    }
+    const T piv = a[k][k];
+    T r;
+    if constexpr (sizeof(T) == 8) r = rcp_f64(piv);
+    else r = rcp_f32(piv);
+    det *= piv;
+    gmax = fmax(gmax, fabs(piv));
+#pragma unroll
+    for (int i = k + 1; i < M; ++i) {
+      const T l = a[i][k] * r;
+#pragma unroll
+      for (int j = k + 1; j < M; ++j) a[i][j] = fma(-l, a[k][j], a[i][j]);
+    }
+  }
+  det *= a[M - 1][M - 1];
+  gmax = fmax(gmax, fabs(a[M - 1][M - 1]));
+  return neg ? -det : det;
+}
+
+// Gather the minor A[:, c] from the column-major shared copy (column j of A
+// at As + j * CS, CS = padded column stride) into registers.
+template <typename T, int M, int CS>
+__device__ __forceinline__ void gather(const T* __restrict__ As, const int (&c)[M], T (&a)[M][M]) {
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const T* col = As + c[j] * CS;
+    if constexpr (sizeof(T) == 4 && CS % 4 == 0) {
+#pragma unroll
+      for (int i = 0; i < M; i += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(col + i);
+        a[i][j] = v.x;
+        if (i + 1 < M) a[i + 1][j] = v.y;
+        if (i + 2 < M) a[i + 2][j] = v.z;
+        if (i + 3 < M) a[i + 3][j] = v.w;
+      }
+    } else if constexpr (sizeof(T) == 8 && CS % 2 == 0) {
+#pragma unroll
+      for (int i = 0; i < M; i += 2) {
+        const double2 v = *reinterpret_cast<const double2*>(col + i);
+        a[i][j] = v.x;
+        if (i + 1 < M) a[i + 1][j] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < M; ++i) a[i][j] = col[i];
+    }
+  }
+}
+
+template <typename T, int M>
+struct ColStride {
+  static constexpr int value = (sizeof(T) == 8) ? ((M + 1) / 2) * 2 : ((M + 3) / 4) * 4;
+};
+
+// ---------------------------------------------------------------------------
+// Compensated sums
+// ---------------------------------------------------------------------------
+struct Dd {  // binary64 value + error term (Knuth two-sum)
+  double hi = 0.0, lo = 0.0;
+  __device__ __forceinline__ void add(double x) {
+    const double s = hi + x;
+    const double bp = s - hi;
+    const double err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+  }
+  __device__ __forceinline__ void merge(const Dd& o) {
+    add(o.hi);
+    lo += o.lo;
+  }
+};
+
+struct Ff {  // binary32 value + error term, flushed to Dd per run of ranks
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+  }
+};
+
+__device__ __forceinline__ double shfl_xor_d(double x, int off) {
+  return __shfl_xor_sync(kFull, x, off);
+}
+
+// Block-wide reduction of (hi, lo, abs, count) in a fixed order; the result
+// is valid in thread 0.  `scratch` holds 4 * (blockDim.x / 32) words.
+__device__ inline void block_reduce_dd(Dd& acc, double& abs_sum, long long& count, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Dd o;
+    o.hi = shfl_xor_d(acc.hi, off);
+    o.lo = shfl_xor_d(acc.lo, off);
+    acc.merge(o);
+    abs_sum += shfl_xor_d(abs_sum, off);
+    count += __shfl_xor_sync(kFull, count, off);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    scratch[4 * warp + 0] = acc.hi;
+    scratch[4 * warp + 1] = acc.lo;
+    scratch[4 * warp + 2] = abs_sum;
+    scratch[4 * warp + 3] = __longlong_as_double(count);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Dd t;
+    double ab = 0.0;
+    long long cnt = 0;
+    for (int w = 0; w < nw; ++w) {
+      Dd o;
+      o.hi = scratch[4 * w + 0];
+      o.lo = scratch[4 * w + 1];
+      t.merge(o);
+      ab += scratch[4 * w + 2];
+      cnt += __double_as_longlong(scratch[4 * w + 3]);
+    }
+    acc = t;
+    abs_sum = ab;
+    count = cnt;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Staging of A into shared memory (column-major, padded column stride CS),
+// with every row scaled by a power of two so that its largest magnitude lies
+// in [0.5, 1).  Row scaling multiplies det_R by the same power of two (each
+// minor is linear in every row), which the finaliser restores exactly.
+// Returns, in every thread, the total exponent sum_i e_i.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double load_elem(const void* A, int dtype, long long idx) {
+  switch (dtype) {
+    case kI8: return static_cast<double>(static_cast<const int8_t*>(A)[idx]);
+    case kI32: return static_cast<double>(static_cast<const int32_t*>(A)[idx]);
+    case kF32: return static_cast<double>(static_cast<const float*>(A)[idx]);
+    default: return static_cast<const double*>(A)[idx];
+  }
+}
+
+template <typename T>
+__device__ inline int stage_scaled(const void* A, int dtype, int m, int n, long long lda, T* As, int cs,
+                                   int* row_exp /* smem, m ints */) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double mx = 0.0;
+    for (int j = 0; j < n; ++j) mx = fmax(mx, fabs(load_elem(A, dtype, (long long)i * lda + j)));
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    row_exp[i] = e;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    const double v = load_elem(A, dtype, (long long)i * lda + j);
+    As[j * cs + i] = static_cast<T>(ldexp(v, -row_exp[i]));
+  }
+  // zero the padding rows of every column so vector loads read defined values
+  for (int idx = threadIdx.x; idx < (cs - m) * n; idx += blockDim.x) {
+    const int j = idx / (cs - m), i = m + (idx - j * (cs - m));
+    As[j * cs + i] = T(0);
+  }
+  __syncthreads();
+  int tot = 0;
+  for (int i = 0; i < m; ++i) tot += row_exp[i];
+  return tot;
+}
+
+// Last-block finalisation: every block stores its partial, and the block that
+// takes the last ticket sums all partials in block order.  Returns true in the
+// last block (all its threads), which then holds the totals in thread 0.
+__device__ inline bool last_block(unsigned int* ticket) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+}  // namespace radic

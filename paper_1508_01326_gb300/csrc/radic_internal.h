@@ -1,0 +1,107 @@
+// Internal declarations shared by the host launchers and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/radic.h"
+
+namespace radic {
+
+// dtype / mode / mapping codes (same values as the C enums)
+enum : int { kI8 = RADIC_I8, kI32 = RADIC_I32, kF32 = RADIC_F32, kF64 = RADIC_F64 };
+enum : int { kModeFp64 = RADIC_MODE_FP64, kModeMixed = RADIC_MODE_MIXED, kModeExact = RADIC_MODE_EXACT };
+
+constexpr int kMaxM = RADIC_MAX_M;
+constexpr int kMaxN = RADIC_MAX_N;
+constexpr int kMaxPrimes = RADIC_MAX_PRIMES;
+constexpr int kThreadMaxMFp64 = 8;   // thread mapping limits (register budget)
+constexpr int kThreadMaxMFp32 = 12;
+constexpr int kThreadMaxMModp = 12;
+
+// 31-bit primes of the exact mode (largest primes below 2^31).
+constexpr uint32_t kPrime0 = 2147483647u, kPrime1 = 2147483629u, kPrime2 = 2147483587u, kPrime3 = 2147483579u;
+constexpr uint32_t kPrimes[kMaxPrimes] = {kPrime0, kPrime1, kPrime2, kPrime3};  // host use
+
+// Header at the start of every workspace (zeroed by the launcher).
+struct WsHeader {
+  unsigned int ticket[4];   // last-block tickets of up to four kernels
+  int overflow;             // MIXED: some warp's flag list overflowed
+  int status;               // device-side status
+  long long reserved[6];
+};
+static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
+
+// Per-block partial of the floating-point kernels.
+struct FpPartial {
+  double hi, lo, abs_sum;
+  long long count;
+};
+
+// Launch plan of one single-matrix call (computed identically by
+// radic_workspace_bytes and radic_det).
+struct SinglePlan {
+  int mode = 0, m = 0, n = 0;
+  int mapping = RADIC_MAP_THREAD;  // resolved mapping
+  int group = 0;                   // lanes per minor for the group mapping
+  int threads = 128;
+  int blocks = 1;
+  int ranks_per_task = 64;
+  int flag_cap = 32;
+  double growth = 64.0;
+  unsigned long long total = 0;    // C(n, m)
+  unsigned long long tasks = 0;
+  size_t smem = 0;
+  void* events = nullptr;          // optional cudaEvent_t[2] around the main kernel
+  // workspace layout (byte offsets)
+  size_t off_partials = 0, off_partials2 = 0, off_flag_count = 0, off_flag_ranks = 0, off_modp = 0;
+  int blocks2 = 0;                 // MIXED fix-up kernel grid
+  size_t ws_bytes = 0;
+};
+
+// Arguments passed by value to every single-matrix kernel.
+struct SingleArgs {
+  const void* A;
+  long long lda;
+  int dtype, m, n;
+  int ranks_per_task;
+  unsigned long long total, tasks;
+  double growth;
+  int flag_cap;
+  int n_warps;  // warps in the main grid (flag lists)
+  WsHeader* hdr;
+  FpPartial* partials;
+  FpPartial* partials2;
+  int* flag_count;
+  unsigned long long* flag_ranks;
+  uint32_t* modp_partials;  // blocks x kMaxPrimes residues
+  radic_result* out;
+  // terms mode
+  unsigned long long q0, count;
+  void* terms;
+};
+
+unsigned long long binom_host(int n, int k);  // exact C(n, k) for n <= 64 (0 if k > n)
+int device_sm_count();
+
+// Launchers (return a RADIC_* code).  When `args.terms` is non-null the
+// kernel writes per-rank terms instead of reducing.
+int launch_fp64(const SinglePlan& p, const SingleArgs& a, cudaStream_t s);
+int launch_mixed(const SinglePlan& p, const SingleArgs& a, cudaStream_t s);
+int launch_modp(const SinglePlan& p, const SingleArgs& a, cudaStream_t s);
+int launch_unrank(int n, int m, unsigned long long q0, unsigned long long count, uint8_t* cols,
+                  int ranks_per_task, cudaStream_t s);
+
+// Occupancy helpers filled in by the arithmetic files.
+int blocks_per_sm_fp64(const SinglePlan& p);
+int blocks_per_sm_mixed(const SinglePlan& p);
+int blocks_per_sm_modp(const SinglePlan& p);
+size_t smem_fp64(const SinglePlan& p);
+size_t smem_mixed(const SinglePlan& p);
+size_t smem_modp(const SinglePlan& p);
+
+inline int ceil_div(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace radic

@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI: the library builds, loads, exports every symbol
+that include/*.h declares, and rejects bad arguments before touching a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from oracle.radic_oracle import is_prime
+from tests.conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1508_01326_gb300 import build as B
+    from paper_1508_01326_gb300 import _lib as L
+
+    B.build()
+    return L.lib()
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(radic_[a-z0-9_]+)\s*\(", text):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ["radic_det", "radic_terms", "radic_unrank", "radic_workspace_bytes", "radic_primes"]:
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls(lib):
+    assert lib.radic_version() >= 10000
+    assert lib.radic_status_string(0) == b"ok"
+    assert lib.radic_status_string(1) == b"invalid argument"
+    buf = (ctypes.c_uint32 * 4)()
+    assert lib.radic_primes(buf, 4) == 4
+    primes = list(buf)
+    assert len(set(primes)) == 4
+    for p in primes:
+        assert is_prime(p) and (1 << 30) < p < (1 << 31)
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    from paper_1508_01326_gb300 import _lib as L
+
+    dummy = ctypes.c_void_p(0x1000)
+    # NULL matrix
+    assert lib.radic_det(None, 3, 5, 5, 3, 0, None, dummy, dummy, 1 << 20, None) == 1
+    # lda < n
+    assert lib.radic_det(dummy, 3, 5, 4, 3, 0, None, dummy, dummy, 1 << 20, None) == 1
+    # exact mode with a real dtype
+    assert lib.radic_det(dummy, 3, 5, 5, 3, 2, None, dummy, dummy, 1 << 20, None) == 1
+    # unknown dtype, unknown mode
+    assert lib.radic_det(dummy, 3, 5, 5, 9, 0, None, dummy, dummy, 1 << 20, None) == 1
+    assert lib.radic_det(dummy, 3, 5, 5, 3, 7, None, dummy, dummy, 1 << 20, None) == 1
+    # sizes out of range
+    for m, n in [(0, 5), (3, 0), (33, 40), (3, 65)]:
+        assert lib.radic_det(dummy, m, n, max(n, 1), 3, 0, None, dummy, dummy, 1 << 20, None) == 1
+    # unrank: rank range outside [0, C(n, m))
+    assert lib.radic_unrank(8, 5, 56, 1, dummy, None, None) == 1
+    assert lib.radic_unrank(8, 5, 50, 7, dummy, None, None) == 1
+    assert lib.radic_unrank(8, 9, 0, 1, dummy, None, None) == 1
+    assert lib.radic_terms(dummy, 5, 8, 8, 3, 0, None, 0, 57, dummy, None) == 1
+    opts = L.make_options(mapping="thread")
+    assert lib.radic_workspace_bytes(0, 8, 0, ctypes.byref(opts)) == 0

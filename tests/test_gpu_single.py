@@ -1,0 +1,376 @@
+"""GPU parity of the single-matrix path against the exact oracle.
+
+Element-by-element: the per-minor signed terms and the unranked column
+sequences of the device are compared with the oracle for every rank of small
+cases (several tasks and a ragged tail).  Whole results: det_R(A) against the
+exact value, bit-exact for the multi-modular path, within
+1e-12 * sum|terms| for binary64 and within a derived bound for the mixed
+binary32 path.  Full-size workloads run in the launch configuration the bench
+uses and are checked against the Pfaffian closed form and sampled terms.
+"""
+import itertools
+import math
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.radic_oracle as orc
+from paper_1508_01326_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1508_01326_gb300 import build as B
+
+    B.build()
+
+
+def R():
+    import paper_1508_01326_gb300 as R_
+
+    return R_
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def hadamard_terms(a, combos):
+    """Per-minor Hadamard bounds prod_i ||A[i, J]||_2 (tolerance scale)."""
+    a = np.asarray(a, dtype=np.float64)
+    j = np.asarray(combos, dtype=np.int64)
+    sq = a[:, j] ** 2  # (m, count, m)
+    return np.prod(np.sqrt(sq.sum(axis=2)), axis=0)
+
+
+def combos0(n, m):
+    return [tuple(c - 1 for c in cols) for cols in orc.lex_combinations(n, m)]
+
+
+OPTS = {
+    "thread": dict(mapping="thread"),
+    "thread_l13": dict(mapping="thread", ranks_per_task=13, threads_per_block=64),
+    "g16": dict(mapping="group", group_width=16),
+    "g16_l5": dict(mapping="group", group_width=16, ranks_per_task=5),
+    "g32": dict(mapping="group", group_width=32, ranks_per_task=7),
+}
+
+
+# ---------------------------------------------------------------------------
+# Unranking and successor (Section 4, Section 5)
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("n,m", [(8, 5), (10, 1), (10, 10), (12, 6), (13, 12), (16, 14), (18, 17), (20, 3)])
+@pytest.mark.parametrize("L", [1, 7, 64])
+def test_unrank_matches_dictionary_order(n, m, L):
+    want = np.array(combos0(n, m), dtype=np.uint8)
+    got = R().radic_unrank(n, m, 0, len(want), options=dict(ranks_per_task=L)).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+def test_unrank_table2():
+    from tests.conftest import read_golden_rows
+
+    rows = read_golden_rows("table2_lex_n8_m5.txt")
+    want = np.array([[int(x) - 1 for x in r[1:]] for r in rows], dtype=np.uint8)
+    got = R().radic_unrank(8, 5, 0, 56).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("n,m", [(64, 32), (64, 1), (64, 63), (40, 12), (32, 8), (28, 6), (30, 20)])
+def test_unrank_large_runs(n, m):
+    total = math.comb(n, m)
+    rng = random.Random(n * 100 + m)
+    starts = {0, max(total - 150, 0)} | {rng.randrange(total) for _ in range(4)}
+    for q0 in sorted(starts):
+        count = min(150, total - q0)
+        got = R().radic_unrank(n, m, q0, count, options=dict(ranks_per_task=11)).cpu().numpy()
+        seq = orc.unrank_combinatorial_addition(q0, n, m)
+        for r in range(count):
+            assert list(got[r] + 1) == seq, (q0 + r)
+            if r + 1 < count:
+                seq = orc.lex_successor(seq, n)
+
+
+# ---------------------------------------------------------------------------
+# Per-minor terms, element by element
+# ---------------------------------------------------------------------------
+
+TERM_CASES = [
+    # (m, n, dtype, options key)
+    (1, 9, np.float64, "thread"),
+    (3, 12, np.int32, "thread"),
+    (5, 16, np.float64, "thread_l13"),
+    (8, 14, np.float64, "thread"),
+    (8, 13, np.float32, "thread_l13"),
+    (6, 11, np.int8, "thread"),
+    (10, 14, np.float64, "g16"),
+    (12, 15, np.float64, "g16_l5"),
+    (17, 19, np.float64, "g32"),
+]
+
+
+def _matrix(m, n, dtype, seed):
+    if np.dtype(dtype).kind == "i":
+        return W.integer_matrix(seed, m, n, 3 if dtype == np.int8 else 9, dtype)
+    return W.uniform_matrix(seed, m, n, dtype)
+
+
+@pytest.mark.parametrize("m,n,dtype,key", TERM_CASES)
+def test_terms_fp64_elementwise(m, n, dtype, key):
+    if key == "thread" and m > 8 or key == "thread_l13" and m > 8:
+        pytest.skip("binary64 thread mapping covers m <= 8")
+    a = _matrix(m, n, dtype, 100 + m * n)
+    total = math.comb(n, m)
+    q0 = total // 7
+    count = total - q0
+    got = R().radic_terms(dev(a), q0, count, mode="fp64", options=OPTS[key]).cpu().numpy()
+    want = np.array([float(x) for x in orc.radic_terms_exact(a, range(q0, q0 + count))])
+    h = hadamard_terms(a, combos0(n, m)[q0:])
+    assert np.all(np.abs(got - want) <= 1e-13 * h + 1e-300), np.max(np.abs(got - want) / h)
+
+
+@pytest.mark.parametrize("m,n,dtype,key", TERM_CASES)
+def test_terms_mixed_elementwise(m, n, dtype, key):
+    if key.startswith("thread") and m > 12:
+        pytest.skip("binary32 thread mapping covers m <= 12")
+    a = _matrix(m, n, dtype, 200 + m * n)
+    total = math.comb(n, m)
+    q0 = total // 5
+    count = total - q0
+    got = R().radic_terms(dev(a), q0, count, mode="mixed", options=OPTS[key]).cpu().numpy()
+    want = np.array([float(x) for x in orc.radic_terms_exact(a, range(q0, q0 + count))])
+    h = hadamard_terms(a, combos0(n, m)[q0:])
+    ok = ~np.isnan(got)
+    assert ok.mean() > 0.99
+    # binary32 LU: backward error O(m u) per entry, plus the binary32 cast of binary64 input
+    assert np.all(np.abs(got[ok] - want[ok]) <= 8 * m * U32 * h[ok]), np.max(np.abs(got[ok] - want[ok]) / h[ok])
+
+
+EXACT_CASES = [
+    (1, 7, np.int32, "thread", 50),
+    (3, 12, np.int32, "thread", 9),
+    (4, 10, np.int8, "thread", 1),  # many zeros: zero pivots, singular minors
+    (7, 12, np.int8, "thread_l13", 3),
+    (12, 14, np.int8, "thread", 3),
+    (9, 13, np.int32, "thread", 1000000),
+    (13, 16, np.int8, "g16", 3),
+    (14, 15, np.int32, "g16_l5", 100),
+    (18, 19, np.int8, "g32", 2),
+]
+
+
+@pytest.mark.parametrize("m,n,dtype,key,bound", EXACT_CASES)
+def test_terms_exact_elementwise(m, n, dtype, key, bound):
+    a = W.integer_matrix(300 + m * n, m, n, bound, dtype)
+    total = math.comb(n, m)
+    q0 = total // 3
+    count = total - q0
+    out = R().radic_terms(dev(a), q0, count, mode="exact", options=OPTS[key]).cpu().numpy().view(np.uint32)
+    res = R().det(a, mode="exact", options=OPTS[key])
+    k_used = res["n_primes"]
+    primes = R().radic_primes()
+    want = orc.radic_terms_exact(a.astype(np.int64), range(q0, q0 + count))
+    for k in range(k_used):
+        p = primes[k]
+        assert [int(x) for x in out[k, :count]] == [int(w) % p for w in want], k
+
+
+# ---------------------------------------------------------------------------
+# Whole determinants on small cases
+# ---------------------------------------------------------------------------
+
+DET_CASES = [
+    (1, 1, np.float64), (1, 11, np.float64), (2, 3, np.float32), (3, 12, np.int32), (4, 4, np.float64),
+    (5, 9, np.int8), (6, 13, np.float64), (7, 12, np.float32), (8, 8, np.float64), (8, 15, np.float64),
+    (9, 13, np.float64), (10, 14, np.float32), (12, 16, np.float64), (16, 18, np.float64),
+    (20, 22, np.float64), (3, 2, np.float64),
+]
+
+
+def _exact(a):
+    return orc.radic_det_exact(a)
+
+
+@pytest.mark.parametrize("m,n,dtype", DET_CASES)
+def test_det_fp64_small(m, n, dtype):
+    a = _matrix(m, n, dtype, 400 + m * n)
+    val, abs_sum = _exact(a)
+    res = R().det(a, mode="fp64")
+    assert res["minors"] == (math.comb(n, m) if m <= n else 0)
+    assert abs(Fraction(res["value"]) - val) <= Fraction(1e-12) * abs_sum
+    if abs_sum:
+        assert abs(res["abs_sum"] - float(abs_sum)) <= 1e-12 * float(abs_sum)
+
+
+@pytest.mark.parametrize("m,n,dtype", DET_CASES)
+def test_det_mixed_small(m, n, dtype):
+    a = _matrix(m, n, dtype, 500 + m * n)
+    val, abs_sum = _exact(a)
+    res = R().det(a, mode="mixed")
+    if m > n:
+        assert res["value"] == 0.0 and res["minors"] == 0
+        return
+    h = hadamard_terms(a, combos0(n, m)).sum()
+    assert abs(res["value"] - float(val)) <= 8 * m * U32 * h
+    assert res["tier"] == 1
+
+
+@pytest.mark.parametrize("m,n,dtype,bound", [(1, 5, np.int32, 7), (3, 12, np.int32, 9), (5, 9, np.int8, 3),
+                                             (8, 11, np.int32, 40000), (10, 13, np.int8, 3),
+                                             (12, 13, np.int32, 1000), (13, 15, np.int8, 3),
+                                             (16, 17, np.int32, 50), (4, 3, np.int8, 3)])
+def test_det_exact_small(m, n, dtype, bound):
+    a = W.integer_matrix(600 + m * n, m, n, bound, dtype)
+    val, _ = _exact(a.astype(np.int64))
+    res = R().det(a, mode="exact")
+    assert res["status"] == 0
+    assert res["exact"] == val
+    assert res["value"] == float(val)
+
+
+def test_det_square_and_row_special_cases():
+    rng = np.random.default_rng(9)
+    for size in [1, 2, 5, 8]:
+        a = rng.uniform(-1, 1, (size, size))
+        assert abs(R().det(a)["value"] - np.linalg.det(a)) <= 1e-13 * max(1.0, abs(np.linalg.det(a)))
+    row = np.array([[3, 1, 4, 1, 5]], dtype=np.int32)
+    assert R().det(row, mode="exact")["exact"] == 10
+    assert R().det(row.astype(np.float64))["value"] == 10.0
+
+
+def test_det_leading_dimension():
+    a = W.uniform_matrix(77, 6, 15)
+    wide = np.zeros((6, 21))
+    wide[:, :15] = a
+    t = dev(wide)[:, :15]
+    assert t.stride(0) == 21
+    out = R().radic_det(t, mode="fp64")
+    ref = R().det(a, mode="fp64")
+    assert R().parse_result(out)["value"] == ref["value"]
+
+
+def test_det_is_deterministic():
+    a = dev(W.uniform_matrix(3, 7, 20))
+    for mode in ["fp64", "mixed"]:
+        v1 = R().parse_result(R().radic_det(a, mode=mode))["value"]
+        v2 = R().parse_result(R().radic_det(a, mode=mode))["value"]
+        assert v1 == v2
+
+
+def test_mixed_growth_flag_recomputes_in_binary64():
+    m, n = 8, 11
+    w = np.eye(m) - np.tril(np.ones((m, m)), -1)
+    w[:, -1] = 1.0  # partial pivoting growth 2^(m-1) on this minor
+    a = np.concatenate([w, W.uniform_matrix(8, m, n - m)], axis=1)
+    val, abs_sum = _exact(a)
+    res = R().det(a, mode="mixed")
+    assert res["flagged"] >= 1
+    h = hadamard_terms(a, combos0(n, m)).sum()
+    assert abs(res["value"] - float(val)) <= 8 * m * U32 * h
+
+
+def test_mixed_flag_list_overflow_falls_back_to_binary64():
+    a = W.uniform_matrix(12, 6, 14)
+    val, abs_sum = _exact(a)
+    res = R().det(a, mode="mixed", options=dict(flag_capacity=1, growth_threshold=1e-30))
+    assert res["flagged"] == math.comb(14, 6)
+    assert abs(res["value"] - float(val)) <= 1e-12 * float(abs_sum)
+
+
+def test_exact_overflow_status():
+    a = W.integer_matrix(5, 12, 14, 2 ** 30, np.int32)
+    from paper_1508_01326_gb300 import RadicError
+
+    with pytest.raises(RadicError) as e:
+        R().det(a, mode="exact")
+    assert e.value.code == 2
+
+
+def test_workspace_too_small():
+    from paper_1508_01326_gb300 import RadicError
+
+    a = dev(W.uniform_matrix(1, 4, 9))
+    ws = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(RadicError) as e:
+        R().radic_det(a, workspace=ws)
+    assert e.value.code == 5
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads (bench launch configuration)
+# ---------------------------------------------------------------------------
+
+
+def test_full_int_3x12_exact_and_fp64():
+    a = W.int_3x12()
+    val, abs_sum = orc.radic_det_exact(a.astype(np.int64))
+    assert R().det(a, mode="exact")["exact"] == val
+    res = R().det(a, mode="fp64")
+    assert res["value"] == float(val)
+    assert R().det(a, mode="mixed")["value"] == float(val)
+
+
+@pytest.fixture(scope="module")
+def fp64_8x32():
+    a = W.fp64_8x32()
+    return a, orc.radic_det_pfaffian(a)
+
+
+def test_full_fp64_8x32_binary64(fp64_8x32):
+    a, exact = fp64_8x32
+    res = R().det(a, mode="fp64")
+    assert res["minors"] == 10_518_300
+    assert abs(Fraction(res["value"]) - exact) <= Fraction(1e-12) * Fraction(res["abs_sum"])
+    # sum|terms| against a seeded sample of exact minors (unbiased estimate)
+    rng = random.Random(2)
+    ranks = [rng.randrange(10_518_300) for _ in range(3000)]
+    est = float(sum(abs(t) for t in orc.radic_terms_exact(a, ranks))) / len(ranks) * 10_518_300
+    assert abs(res["abs_sum"] - est) <= 0.05 * est
+
+
+def test_full_fp64_8x32_mixed(fp64_8x32):
+    a, exact = fp64_8x32
+    res = R().det(a, mode="mixed")
+    rel = abs(float(Fraction(res["value"]) - exact)) / res["abs_sum"]
+    assert rel <= 1e-10, rel
+
+
+def test_full_fp64_8x32_sampled_terms(fp64_8x32):
+    a, _ = fp64_8x32
+    rng = random.Random(22)
+    t = dev(a)
+    all_combos = None
+    for _ in range(6):
+        q0 = rng.randrange(10_518_300 - 300)
+        got = R().radic_terms(t, q0, 300, mode="fp64").cpu().numpy()
+        want = np.array([float(x) for x in orc.radic_terms_exact(a, range(q0, q0 + 300))])
+        cols = [np.array(orc.unrank_combinatorial_addition(q, 32, 8)) - 1 for q in range(q0, q0 + 300)]
+        h = hadamard_terms(a, cols)
+        assert np.all(np.abs(got - want) <= 1e-13 * h)
+
+
+def test_full_int8_10x24_exact():
+    a = W.int8_10x24()
+    exact = orc.radic_det_pfaffian(a.astype(np.int64))
+    res = R().det(a, mode="exact")
+    assert res["exact"] == exact
+
+
+def test_full_int8_12x40_exact():
+    a = W.int8_12x40()
+    exact = orc.radic_det_pfaffian(a.astype(np.int64))
+    res = R().det(a, mode="exact")
+    assert res["minors"] == math.comb(40, 12)
+    assert res["n_primes"] == 3
+    assert res["exact"] == exact
