@@ -72,29 +72,39 @@ int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long
   const int max_threads = (mode == kModeExact) ? 128 : 256;
   pl.threads = d.threads_per_block ? d.threads_per_block : 128;
   if (pl.threads < 32 || pl.threads > max_threads || pl.threads % 32) return RADIC_EINVAL;
-  pl.ranks_per_task = d.ranks_per_task ? d.ranks_per_task : 64;
-  if (pl.ranks_per_task < 1 || pl.ranks_per_task > (1 << 20)) return RADIC_EINVAL;
+  if (d.ranks_per_task < 0 || d.ranks_per_task > (1 << 30)) return RADIC_EINVAL;
   pl.flag_cap = d.flag_capacity ? d.flag_capacity : 32;
   if (pl.flag_cap < 1 || pl.flag_cap > (1 << 16)) return RADIC_EINVAL;
   pl.growth = d.growth_threshold > 0.0 ? d.growth_threshold : 64.0;
   pl.events = d.kernel_events;
-  pl.tasks = (units + pl.ranks_per_task - 1) / pl.ranks_per_task;
   pl.smem = smem_of(pl);
 
   const int sms = device_sm_count();
   const int per_sm = blocks_per_sm(pl);
   if (sms <= 0) return RADIC_ECUDA;
   if (per_sm <= 0) return RADIC_EUNSUPPORTED;
+  // Work split of Section 5: K processors (threads, or lane groups) each take
+  // one contiguous run of about C(n,m)/K ranks.  K is the number of resident
+  // processors of a full-occupancy grid, so every processor gets one task and
+  // no SM waits on a tail; an explicit ranks_per_task overrides the run length.
   const unsigned long long per_block =
       (mapping == RADIC_MAP_THREAD) ? (unsigned long long)pl.threads : (unsigned long long)(pl.threads / pl.group);
-  const unsigned long long need = (pl.tasks + per_block - 1) / per_block;
   const unsigned long long cap = (unsigned long long)sms * per_sm;
+  unsigned long long L = (unsigned long long)d.ranks_per_task;
+  if (L == 0) {
+    const unsigned long long procs = cap * per_block;
+    L = (units + procs - 1) / procs;
+    if (L < 1) L = 1;
+  }
+  pl.ranks_per_task = L;
+  pl.tasks = (units + L - 1) / L;
+  const unsigned long long need = (pl.tasks + per_block - 1) / per_block;
   unsigned long long blocks = need < cap ? need : cap;
   if (d.blocks > 0) blocks = (unsigned long long)d.blocks;
   if (blocks < 1) blocks = 1;
   if (blocks > (1ull << 20)) return RADIC_EINVAL;
   pl.blocks = (int)blocks;
-  pl.blocks2 = sms * 4;
+  pl.blocks2 = sms;
 
   const int n_warps = pl.blocks * pl.threads / 32;
   size_t off = 256;

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
   const int lane = threadIdx.x & 31;
   const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int L = a.ranks_per_task;
+  const unsigned long long L = a.ranks_per_task;
   const unsigned long long qbase = kTerms ? a.q0 : 0ull;
   const unsigned long long qlim = kTerms ? a.q0 + a.count : a.total;
   const T thr = static_cast<T>(a.growth);
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
     unrank<M>(q0, n, sm.binom, M + 1, c);
     Ff run;
     float run_abs = 0.0f;
-    for (int it = 0; it < L; ++it) {
+    for (unsigned long long it = 0; it < L; ++it) {
       const unsigned long long q = q0 + it;
       const bool act = tact && q < q1;
       T mm[M][M];
@@ -137,6 +137,15 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
           abs_sum += fabs(static_cast<double>(det));
         }
       }
+      if constexpr (kMixed && !kTerms) {
+        if ((it & 255) == 255) {  // keep the binary32 partial sums short
+          acc.add(static_cast<double>(run.hi));
+          acc.add(static_cast<double>(run.lo));
+          abs_sum += static_cast<double>(run_abs);
+          run = Ff();
+          run_abs = 0.0f;
+        }
+      }
       if (q + 1 < q1) successor<M>(c, n);
     }
     if constexpr (kMixed && !kTerms) {
@@ -162,12 +171,11 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
         double ab = 0.0;
         long long c2 = 0;
         for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-          const FpPartial p = a.partials[b];
           Dd o;
-          o.hi = p.hi;
-          o.lo = p.lo;
+          o.hi = __ldcg(&a.partials[b].hi);
+          o.lo = __ldcg(&a.partials[b].lo);
           t.merge(o);
-          ab += p.abs_sum;
+          ab += __ldcg(&a.partials[b].abs_sum);
         }
         block_reduce_dd(t, ab, c2, sm.scratch);
         if (threadIdx.x == 0)
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
   constexpr int kSegs = 32 / G;
   const unsigned long long gwarp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nsegs = (unsigned long long)gridDim.x * blockDim.x / G;
-  const int L = a.ranks_per_task;
+  const unsigned long long L = a.ranks_per_task;
   const unsigned long long qbase = kTerms ? a.q0 : 0ull;
   const unsigned long long qlim = kTerms ? a.q0 + a.count : a.total;
   const T thr = static_cast<T>(a.growth);
@@ -251,7 +259,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
     unrank_dyn<G>(q0, n, m, sm.binom, m + 1, c);
     Ff run;
     float run_abs = 0.0f;
-    for (int it = 0; it < L; ++it) {
+    for (unsigned long long it = 0; it < L; ++it) {
       const unsigned long long q = q0 + it;
       const bool act = tact && q < q1;
       T x[G];
@@ -287,6 +295,15 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
           abs_sum += fabs(static_cast<double>(det));
         }
       }
+      if constexpr (kMixed && !kTerms) {
+        if ((it & 255) == 255) {
+          acc.add(static_cast<double>(run.hi));
+          acc.add(static_cast<double>(run.lo));
+          abs_sum += static_cast<double>(run_abs);
+          run = Ff();
+          run_abs = 0.0f;
+        }
+      }
       if (q + 1 < q1) successor_dyn<G>(c, n, m);
     }
     if constexpr (kMixed && !kTerms) {
@@ -312,12 +329,11 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
         double ab = 0.0;
         long long c2 = 0;
         for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-          const FpPartial p = a.partials[b];
           Dd o;
-          o.hi = p.hi;
-          o.lo = p.lo;
+          o.hi = __ldcg(&a.partials[b].hi);
+          o.lo = __ldcg(&a.partials[b].lo);
           t.merge(o);
-          ab += p.abs_sum;
+          ab += __ldcg(&a.partials[b].abs_sum);
         }
         block_reduce_dd(t, ab, c2, sm.scratch);
         if (threadIdx.x == 0)

@@ -47,7 +47,7 @@ struct SinglePlan {
   int group = 0;                   // lanes per minor for the group mapping
   int threads = 128;
   int blocks = 1;
-  int ranks_per_task = 64;
+  unsigned long long ranks_per_task = 64;
   int flag_cap = 32;
   double growth = 64.0;
   unsigned long long total = 0;    // C(n, m)
@@ -65,7 +65,7 @@ struct SingleArgs {
   const void* A;
   long long lda;
   int dtype, m, n;
-  int ranks_per_task;
+  unsigned long long ranks_per_task;
   unsigned long long total, tasks;
   double growth;
   int flag_cap;

