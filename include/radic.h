@@ -174,6 +174,40 @@ int radic_terms(const void* A, int m, int n, int64_t lda, int dtype, int mode,
 int radic_unrank(int n, int m, uint64_t q0, uint64_t count, uint8_t* cols,
                  const radic_options* opts, void* stream);
 
+/* ---- allocation-free variant ------------------------------------------- */
+
+/* Capacity in bytes of the library's own static scratch array. */
+#define RADIC_NOALLOC_SCRATCH_BYTES 131072
+
+/* det_R(A) in RADIC_MODE_FP64 without any caller workspace.  The paper has
+ * no counterpart to this entry point; it exists for callers that cannot call
+ * cudaMalloc when they need a determinant -- for example code whose device
+ * memory is entirely owned by another allocator or a fixed pool, or a loop
+ * that cannot afford the device synchronisation an allocation may cause.
+ * Such callers still provide A and `out`, but no workspace.
+ *
+ * Scratch lives in one file-scope __device__ array of
+ * RADIC_NOALLOC_SCRATCH_BYTES bytes inside libradic.so; every GPU that loads
+ * the library holds it until the process exits.  The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress, with
+ * that device current) and caches it; make that first call before any
+ * stream capture.  The call itself allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ * All calls on one device share the array and it keeps the last call's
+ * contents; each call clears the part that must start at zero.  Calls that
+ * overlap on the GPU (other streams, other host threads) race on the array
+ * and give wrong results: serialise them.
+ *
+ * Arguments are those of radic_det with mode RADIC_MODE_FP64.  Errors:
+ * as radic_det; RADIC_EWORKSPACE when the launch plan for these options
+ * needs more than RADIC_NOALLOC_SCRATCH_BYTES of scratch (the default
+ * options fit on GPUs with up to 255 SMs; GB300 has 152); RADIC_ECUDA when the
+ * symbol lookup fails. */
+int radic_det_noalloc(const void* A, int m, int n, int64_t lda, int dtype,
+                      const radic_options* opts, radic_result* out,
+                      void* stream);
+
 #ifdef __cplusplus
 } /* extern "C" */
 #endif

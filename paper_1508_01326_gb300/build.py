@@ -24,6 +24,7 @@ SOURCES = [
     "radic_fp64.cu",
     "radic_mixed.cu",
     "radic_modp.cu",
+    "radic_noalloc.cu",
 ]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
