@@ -172,8 +172,28 @@ def run_reference(args, rank: int, world: int) -> None:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def prefix_flops(m: int, n: int) -> int:
+    """Algorithmic flops (2 per FMA, 1 per add or multiply) of the prefix-sharing path.
+
+    Per (m-2)-column prefix: the partial-pivot elimination of its m x (m-2)
+    matrix, the product of pivots and W = -L21 L11^-1; per candidate column:
+    its two Schur-complement entries and the scale; per leaf minor: the 2 x 2
+    determinant (one multiply, one FMA) and two additions into the sums.
+    """
+    P = m - 2
+    f_pre = sum((m - k - 1) + 2 * (m - k - 1) * (P - k - 1) for k in range(P)) + P + 2 * P * (P - 1)
+    f_col = 4 * P + 1
+    f_leaf = 5
+    total = 0
+    for v in range(P - 1, n - 2):
+        k = n - 1 - v
+        total += math.comb(v, P - 1) * (f_pre + k * f_col + math.comb(k, 2) * f_leaf)
+    return total
+
+
 def run_ours(args, rank: int, world: int, local_rank: int) -> None:
-    import numpy as np
+    import ctypes
+
     import torch
 
     pool = None
@@ -196,48 +216,60 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     A = torch.from_numpy(W.fp64_8x32()).cuda()
     num, den, _ = golden("fp64_8x32")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
-    out_mixed = R.new_result()
-    out_fp64 = R.new_result()
-    ws_mixed = torch.empty(R.radic_workspace_bytes(M, N, "mixed"), dtype=torch.uint8, device="cuda")
-    ws_fp64 = torch.empty(R.radic_workspace_bytes(M, N, "fp64"), dtype=torch.uint8, device="cuda")
     kev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    import ctypes
+    for e in kev:
+        e.record(stream)  # create the underlying events
+    handles = (ctypes.c_void_p * 2)(kev[0].cuda_event, kev[1].cuda_event)
 
-    def timed_steps(mode, out, ws, steps, kernel_events=False):
-        step_ms, kern_ms = [], []
-        opts = None
-        if kernel_events:
-            for e in kev:
-                e.record(stream)  # materialise the events
-            handles = (ctypes.c_void_p * 2)(kev[0].cuda_event, kev[1].cuda_event)
-            opts = R.make_options(kernel_events=ctypes.addressof(handles))
-            timed_steps.handles = handles
-        for _ in range(steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            R.radic_det(A, mode=mode, options=opts, out=out, workspace=ws, stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-            if kernel_events:
-                kern_ms.append(kev[0].elapsed_time(kev[1]))
-        return step_ms, kern_ms
+    class Path:
+        def __init__(self, mode, mapping):
+            self.mode, self.mapping = mode, mapping
+            self.opts = R.make_options(mapping=mapping)
+            self.opts_ev = R.make_options(mapping=mapping, kernel_events=ctypes.addressof(handles))
+            self.out = R.new_result()
+            self.ws = torch.empty(R.radic_workspace_bytes(M, N, mode, self.opts), dtype=torch.uint8, device="cuda")
+
+        def run(self, opts=None, a=None):
+            R.radic_det(A if a is None else a, mode=self.mode, options=opts or self.opts, out=self.out,
+                        workspace=self.ws, stream=stream)
+
+        def timed(self, steps, kernel_events=True):
+            step_ms, kern_ms = [], []
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                self.run(self.opts_ev if kernel_events else None)
+                e1.record(stream)
+                e1.synchronize()
+                step_ms.append(e0.elapsed_time(e1))
+                if kernel_events:
+                    kern_ms.append(kev[0].elapsed_time(kev[1]))
+            return step_ms, kern_ms
+
+        def result(self):
+            res = R.parse_result(self.out)
+            res["rel_err"] = rel_err(res["value"], res["abs_sum"], num, den)
+            return res
+
+    head = Path("mixed", "auto")      # prefix-sharing mixed path (library default)
+    per_minor = Path("mixed", "thread")
+    fp64_plain = Path("fp64", "thread")
+    fp64_prefix = Path("fp64", "auto")
 
     sampler = ClockSampler(local_rank)
-    # warm-up: at least args.warmup steps and about one second of work so clocks settle
-    timed_steps("mixed", out_mixed, ws_mixed, args.warmup)
+    head.timed(args.warmup, kernel_events=False)
     sampler.start()
-    t_end = time.time() + 1.0
+    t_end = time.time() + args.settle_seconds  # work so clocks settle before timing
     while time.time() < t_end:
-        R.radic_det(A, mode="mixed", out=out_mixed, workspace=ws_mixed, stream=stream)
+        head.run()
     torch.cuda.synchronize()
 
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    step_ms, kern_ms = timed_steps("mixed", out_mixed, ws_mixed, args.steps, kernel_events=True)
+    step_ms, kern_ms = head.timed(args.steps)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -250,16 +282,20 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = world * MINORS / (ms_per_step / 1e3)
-    res_mixed = R.parse_result(out_mixed)
-    err_mixed = rel_err(res_mixed["value"], res_mixed["abs_sum"], num, den)
+    res_head = head.result()
 
-    # plain binary64 kernel on the same input
-    fp64_steps = max(3, args.steps // 4)
-    timed_steps("fp64", out_fp64, ws_fp64, 2)
-    f_ms, f_kern = timed_steps("fp64", out_fp64, ws_fp64, fp64_steps, kernel_events=True)
-    res_fp64 = R.parse_result(out_fp64)
-    err_fp64 = rel_err(res_fp64["value"], res_fp64["abs_sum"], num, den)
-    fp64_rate = MINORS / (statistics.mean(f_ms) / 1e3)
+    side = {}
+    for name, path, steps in [("per_minor_mixed", per_minor, max(5, args.steps // 2)),
+                              ("fp64_plain", fp64_plain, max(3, args.steps // 5)),
+                              ("fp64_prefix", fp64_prefix, max(5, args.steps // 2))]:
+        path.timed(2, kernel_events=False)
+        s_ms, k_ms = path.timed(steps)
+        res = path.result()
+        side[name] = {"value": MINORS / (statistics.mean(s_ms) / 1e3), "unit": UNIT, "rel_err": res["rel_err"],
+                      "kernel_ms": statistics.mean(k_ms), "flagged": res["flagged"]}
+    pm = side["per_minor_mixed"]
+    pm["fma_frac"] = FLOP_PER_MINOR * MINORS / (pm["kernel_ms"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS
+    side["fp64_plain"]["speedup_of_headline"] = value / world / side["fp64_plain"]["value"]
 
     # end to end through the public API from pinned host memory
     a_host = torch.from_numpy(W.fp64_8x32()).pin_memory()
@@ -272,8 +308,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         a_dev.copy_(a_host, non_blocking=True)
-        R.radic_det(a_dev, mode="mixed", out=out_mixed, workspace=ws_mixed, stream=stream)
-        res_host.copy_(out_mixed, non_blocking=True)
+        head.run(a=a_dev)
+        res_host.copy_(head.out, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         if i >= args.warmup:
@@ -281,8 +317,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     e2e_rate = world * MINORS / (statistics.mean(e2e_ms) / 1e3)
 
     kern_mean_ms = statistics.mean(kern_ms)
-    achieved = FLOP_PER_MINOR * MINORS / (kern_mean_ms / 1e3) / 1e12
-    fp64_kern_ms = statistics.mean(f_kern)
+    flops = prefix_flops(M, N)
+    achieved = flops / (kern_mean_ms / 1e3) / 1e12
 
     cpu = None
     if pool is not None:
@@ -299,15 +335,16 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "m": M, "n": N, "minors": MINORS, "mode": "mixed",
+                       "mapping": "prefix (binary32 elimination shared per 6-column prefix, binary64 sums)",
                        "l2": "flushed between timed iterations (256 MB write, untimed)",
                        "parallelism": f"replicas{world}"},
-            "rel_err": err_mixed, "flagged": res_mixed["flagged"],
-            "fp64_plain": {"value": fp64_rate, "unit": UNIT, "rel_err": err_fp64,
-                           "kernel_ms": fp64_kern_ms, "speedup_mixed_over_fp64": value / world / fp64_rate},
+            "rel_err": res_head["rel_err"], "flagged": res_head["flagged"],
+            **side,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "k_fp_thread<float,8,mixed>", "kernel_ms": kern_mean_ms,
-                         "flop_per_launch": FLOP_PER_MINOR * MINORS},
+                         "kernel": "k_fp_prefix<float,8,mixed>", "kernel_ms": kern_mean_ms,
+                         "flop_per_launch": flops,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (derived)"},
             "clocks": clocks,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": A.numel() * 8,
@@ -326,6 +363,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--settle-seconds", type=float, default=1.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

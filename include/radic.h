@@ -78,8 +78,16 @@ enum { RADIC_MODE_FP64 = 0, RADIC_MODE_MIXED = 1, RADIC_MODE_EXACT = 2 };
  *            m <= 12 for MIXED and EXACT).
  *  GROUP  -- a group of `group_width` lanes of one warp (16 or 32) factors
  *            one minor, one row per lane, pivot rows shared by warp shuffles.
- *  AUTO   -- THREAD when m <= 8 (EXACT: m <= 12), GROUP above that. */
-enum { RADIC_MAP_AUTO = 0, RADIC_MAP_THREAD = 1, RADIC_MAP_GROUP = 2 };
+ *  PREFIX -- FP64 and MIXED, 3 <= m <= 10 (FP64) or 12 (MIXED): one thread
+ *            factors the m x (m-2) matrix of an ascending (m-2)-column
+ *            prefix once with partial pivoting; every minor of that
+ *            prefix's lexicographic subtree then costs one 2 x 2
+ *            determinant of Schur-complement entries.  Same pivots and
+ *            elimination steps as per-minor LU, shared by the subtree.
+ *  AUTO   -- FP64/MIXED: PREFIX when 3 <= m within its limit, else THREAD
+ *            when m <= 8, else GROUP.  EXACT: THREAD when m <= 12, else
+ *            GROUP. */
+enum { RADIC_MAP_AUTO = 0, RADIC_MAP_THREAD = 1, RADIC_MAP_GROUP = 2, RADIC_MAP_PREFIX = 3 };
 
 /* Launch and precision options.  Pass NULL for the defaults; a zero field
  * also means "default". */

@@ -15,7 +15,7 @@ STATUS = {0: "RADIC_OK", 1: "RADIC_EINVAL", 2: "RADIC_EOVERFLOW", 3: "RADIC_ECUD
           5: "RADIC_EWORKSPACE", 6: "RADIC_EUNSUPPORTED"}
 DTYPES = {"int8": 0, "int32": 1, "float32": 2, "float64": 3}
 MODES = {"fp64": 0, "mixed": 1, "exact": 2}
-MAPPINGS = {"auto": 0, "thread": 1, "group": 2}
+MAPPINGS = {"auto": 0, "thread": 1, "group": 2, "prefix": 3}
 
 
 class RadicOptions(ctypes.Structure):

@@ -31,7 +31,7 @@ def main() -> None:
     ap.add_argument("--workload", default="fp64_8x32", choices=sorted(WORKLOADS))
     ap.add_argument("--mode", default="mixed", choices=["fp64", "mixed", "exact"])
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--mapping", default="auto", choices=["auto", "thread", "group"])
+    ap.add_argument("--mapping", default="auto", choices=["auto", "thread", "group", "prefix"])
     ap.add_argument("--group-width", type=int, default=0)
     ap.add_argument("--ranks-per-task", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)

@@ -47,6 +47,59 @@ size_t smem_of(const SinglePlan& p) {
   }
 }
 
+void layout_workspace(SinglePlan& pl);
+
+// Prefix mapping: groups v (last prefix column) with C(v, m-3) prefixes each;
+// runs per lane sized so that warp tasks cost about the same.  Cost model per
+// prefix: factorisation ~ m (m-2)^2, each candidate column ~ 3m, each leaf 6.
+int plan_prefix(SinglePlan pl, const radic_options& d, int sms, int per_sm, unsigned long long units,
+                SinglePlan* out) {
+  const int m = pl.m, n = pl.n, P = m - 2;
+  PrefixTable& t = pl.ptab;
+  t.v_lo = P - 1;
+  t.v_hi = n - 3;
+  double total_cost = 0.0;
+  double cost[kMaxN] = {0};
+  for (int v = t.v_lo; v <= t.v_hi; ++v) {
+    const int k = n - 1 - v;
+    t.count[v] = binom_host(v, P - 1);
+    cost[v] = (double)m * P * P + 3.0 * m * k + 6.0 * k * (k - 1) / 2.0;
+    total_cost += cost[v] * (double)t.count[v];
+  }
+  const unsigned long long lanes = (unsigned long long)sms * per_sm * pl.threads;
+  const double per_lane = total_cost / (double)lanes / 4.0;  // about four tasks per warp
+  unsigned long long start = 0;
+  for (int v = t.v_lo; v <= t.v_hi; ++v) {
+    double r = per_lane / cost[v];
+    unsigned long long run = r < 1.0 ? 1ull : (unsigned long long)r;
+    if (d.ranks_per_task > 0) run = (unsigned long long)d.ranks_per_task;
+    const unsigned long long maxrun = (t.count[v] + 31) / 32;
+    if (run > maxrun) run = maxrun > 0 ? maxrun : 1;
+    t.run[v] = run;
+    t.task_start[v] = start;
+    start += (t.count[v] + 32 * run - 1) / (32 * run);
+  }
+  if (t.v_hi + 1 < kMaxN) t.task_start[t.v_hi + 1] = start;
+  t.total_tasks = start;
+  const unsigned long long warps_per_block = pl.threads / 32;
+  const unsigned long long need = (start + warps_per_block - 1) / warps_per_block;
+  const unsigned long long cap = (unsigned long long)sms * per_sm;
+  unsigned long long blocks = need < cap ? need : cap;
+  if (d.blocks > 0) blocks = (unsigned long long)d.blocks;
+  if (blocks < 1) blocks = 1;
+  if (blocks > (1ull << 20)) return RADIC_EINVAL;
+  pl.blocks = (int)blocks;
+  pl.blocks2 = sms;
+  // per-minor split used by the binary64 fall-back pass of the mixed mode
+  const unsigned long long procs = (unsigned long long)pl.blocks2 * 128;
+  pl.ranks_per_task = (units + procs - 1) / procs;
+  if (pl.ranks_per_task < 1) pl.ranks_per_task = 1;
+  pl.tasks = (units + pl.ranks_per_task - 1) / pl.ranks_per_task;
+  layout_workspace(pl);
+  *out = pl;
+  return RADIC_OK;
+}
+
 // Plans a launch over `units` ranks (C(n,m) for radic_det, `count` for
 // radic_terms).  Returns a RADIC_* code.
 int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long units, SinglePlan* p) {
@@ -60,16 +113,22 @@ int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long
   pl.n = n;
   pl.total = (m <= n) ? binom_host(n, m) : 0ull;
   const int auto_limit = (mode == kModeExact) ? kThreadMaxMModp : 8;
-  int mapping = d.mapping ? d.mapping : (m <= auto_limit ? RADIC_MAP_THREAD : RADIC_MAP_GROUP);
-  if (mapping != RADIC_MAP_THREAD && mapping != RADIC_MAP_GROUP) return RADIC_EINVAL;
+  const int prefix_limit = (mode == kModeFp64) ? kPrefixMaxMFp64 : (mode == kModeMixed ? kPrefixMaxMFp32 : 0);
+  int mapping = d.mapping;
+  if (mapping == RADIC_MAP_AUTO) {
+    if (m >= 3 && m <= prefix_limit && m <= n) mapping = RADIC_MAP_PREFIX;
+    else mapping = (m <= auto_limit ? RADIC_MAP_THREAD : RADIC_MAP_GROUP);
+  }
+  if (mapping != RADIC_MAP_THREAD && mapping != RADIC_MAP_GROUP && mapping != RADIC_MAP_PREFIX) return RADIC_EINVAL;
   if (mapping == RADIC_MAP_THREAD && m > thread_limit(mode)) return RADIC_EUNSUPPORTED;
+  if (mapping == RADIC_MAP_PREFIX && (m < 3 || m > prefix_limit || m > n)) return RADIC_EUNSUPPORTED;
   pl.mapping = mapping;
   if (mapping == RADIC_MAP_GROUP) {
     const int gw = d.group_width ? d.group_width : (m <= 16 ? 16 : 32);
     if ((gw != 16 && gw != 32) || gw < m) return RADIC_EINVAL;
     pl.group = gw;
   }
-  const int max_threads = (mode == kModeExact) ? 128 : 256;
+  const int max_threads = (mode == kModeExact || mapping == RADIC_MAP_PREFIX) ? 128 : 256;
   pl.threads = d.threads_per_block ? d.threads_per_block : 128;
   if (pl.threads < 32 || pl.threads > max_threads || pl.threads % 32) return RADIC_EINVAL;
   if (d.ranks_per_task < 0 || d.ranks_per_task > (1 << 30)) return RADIC_EINVAL;
@@ -87,9 +146,10 @@ int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long
   // one contiguous run of about C(n,m)/K ranks.  K is the number of resident
   // processors of a full-occupancy grid, so every processor gets one task and
   // no SM waits on a tail; an explicit ranks_per_task overrides the run length.
+  const unsigned long long cap = (unsigned long long)sms * per_sm;
+  if (mapping == RADIC_MAP_PREFIX) return plan_prefix(pl, d, sms, per_sm, units, p);
   const unsigned long long per_block =
       (mapping == RADIC_MAP_THREAD) ? (unsigned long long)pl.threads : (unsigned long long)(pl.threads / pl.group);
-  const unsigned long long cap = (unsigned long long)sms * per_sm;
   unsigned long long L = (unsigned long long)d.ranks_per_task;
   if (L == 0) {
     const unsigned long long procs = cap * per_block;
@@ -105,7 +165,13 @@ int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long
   if (blocks > (1ull << 20)) return RADIC_EINVAL;
   pl.blocks = (int)blocks;
   pl.blocks2 = sms;
+  layout_workspace(pl);
+  *p = pl;
+  return RADIC_OK;
+}
 
+void layout_workspace(SinglePlan& pl) {
+  const int mode = pl.mode;
   const int n_warps = pl.blocks * pl.threads / 32;
   size_t off = 256;
   pl.off_partials = off;
@@ -123,8 +189,6 @@ int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long
     off = align_up(off + (size_t)pl.blocks * kMaxPrimes * sizeof(uint32_t), 256);
   }
   pl.ws_bytes = off;
-  *p = pl;
-  return RADIC_OK;
 }
 
 __global__ void k_zero_result(radic_result* out, int tier) {
@@ -290,6 +354,7 @@ int radic_det(const void* A, int m, int n, int64_t lda, int dtype, int mode, con
   a.tasks = p.tasks;
   a.growth = p.growth;
   a.flag_cap = p.flag_cap;
+  a.flag_prefix = (p.mapping == RADIC_MAP_PREFIX) ? m - 2 : 0;
   a.n_warps = p.blocks * p.threads / 32;
   a.hdr = reinterpret_cast<WsHeader*>(ws);
   a.partials = reinterpret_cast<FpPartial*>(ws + p.off_partials);

@@ -16,22 +16,34 @@ namespace radic {
 constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
-// Binomial table (Section 4, Table 1 / Fig. 1): binom[v * stride + k] = C(v, k)
-// for 0 <= v <= n, 0 <= k <= kmax, built in shared memory by the Pascal
-// recurrence, one table row per step.  Every thread of the block must call.
+// Binomial table (Section 4, Table 1 / Fig. 1): C(v, k) for 0 <= v, k <= 64.
+// The table is generated at compile time by the Pascal recurrence (every
+// entry is the sum of the two entries above it) and lives in constant memory;
+// each block copies the (n+1) x (kmax+1) part it needs into shared memory as
+// binom[v * (kmax + 1) + k] with one barrier.
 // ---------------------------------------------------------------------------
+struct BinomConst {
+  unsigned long long v[kMaxN + 1][kMaxN + 1];
+};
+
+constexpr BinomConst make_binom_const() {
+  BinomConst t{};
+  for (int v = 0; v <= kMaxN; ++v) {
+    t.v[v][0] = 1ull;
+    for (int k = 1; k <= kMaxN; ++k) t.v[v][k] = (v == 0) ? 0ull : t.v[v - 1][k - 1] + t.v[v - 1][k];
+  }
+  return t;
+}
+
+static __constant__ BinomConst c_binom = make_binom_const();
+
 __device__ inline void build_binom(uint64_t* binom, int n, int kmax) {
   const int stride = kmax + 1;
-  for (int v = 0; v <= n; ++v) {
-    for (int k = threadIdx.x; k <= kmax; k += blockDim.x) {
-      uint64_t val;
-      if (k == 0) val = 1;
-      else if (v == 0) val = 0;
-      else val = binom[(v - 1) * stride + k - 1] + binom[(v - 1) * stride + k];
-      binom[v * stride + k] = val;
-    }
-    __syncthreads();
+  for (int idx = threadIdx.x; idx < (n + 1) * stride; idx += blockDim.x) {
+    const int v = idx / stride, k = idx - v * stride;
+    binom[idx] = c_binom.v[v][k];
   }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -263,6 +275,16 @@ struct Ff {  // binary32 value + error term, flushed to Dd per run of ranks
     hi = s;
     lo += err;
   }
+  // adds another float-float value (two-sum of the leading parts, then
+  // renormalisation), keeping about twice binary32 precision
+  __device__ __forceinline__ void merge(const Ff& o) {
+    const float s = hi + o.hi;
+    const float bp = s - hi;
+    float err = (hi - (s - bp)) + (o.hi - bp);
+    err += lo + o.lo;
+    hi = s + err;
+    lo = err - (hi - s);
+  }
 };
 
 __device__ __forceinline__ double shfl_xor_d(double x, int off) {
@@ -327,20 +349,26 @@ __device__ __forceinline__ double load_elem(const void* A, int dtype, long long 
 template <typename T>
 __device__ inline int stage_scaled(const void* A, int dtype, int m, int n, long long lda, T* As, int cs,
                                    int* row_exp /* smem, m ints */) {
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+  // 1. one warp per row: largest magnitude -> exponent e_i (|row| in [0.5, 1) after scaling)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < m; i += nw) {
     double mx = 0.0;
-    for (int j = 0; j < n; ++j) mx = fmax(mx, fabs(load_elem(A, dtype, (long long)i * lda + j)));
-    int e = 0;
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
-    row_exp[i] = e;
+    for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(load_elem(A, dtype, (long long)i * lda + j)));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, off));
+    if (lane == 0) {
+      int e = 0;
+      if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+      row_exp[i] = e;
+    }
   }
   __syncthreads();
+  // 2. scaled copy (binary64 arithmetic, exact power-of-two scaling) into the
+  //    column-major shared copy, padding rows zeroed for vector loads
   for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
-    const double v = load_elem(A, dtype, (long long)i * lda + j);
-    As[j * cs + i] = static_cast<T>(ldexp(v, -row_exp[i]));
+    As[j * cs + i] = static_cast<T>(ldexp(load_elem(A, dtype, (long long)i * lda + j), -row_exp[i]));
   }
-  // zero the padding rows of every column so vector loads read defined values
   for (int idx = threadIdx.x; idx < (cs - m) * n; idx += blockDim.x) {
     const int j = idx / (cs - m), i = m + (idx - j * (cs - m));
     As[j * cs + i] = T(0);

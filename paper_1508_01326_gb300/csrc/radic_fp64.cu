@@ -1,6 +1,6 @@
 // Plain binary64 path: partial-pivot LU per minor in binary64 and a binary64
 // compensated (two-sum) reduction.
-#include "radic_fp_kernels.cuh"
+#include "radic_prefix.cuh"
 
 namespace radic {
 
@@ -18,7 +18,26 @@ const void* group_kernel(bool terms) {
                : reinterpret_cast<const void*>(&k_fp_group<double, G, false, false>);
 }
 
+template <int M>
+const void* prefix_kernel(bool terms) {
+  return terms ? reinterpret_cast<const void*>(&k_fp_prefix<double, M, false, true>)
+               : reinterpret_cast<const void*>(&k_fp_prefix<double, M, false, false>);
+}
+
 const void* pick(const SinglePlan& p, bool terms) {
+  if (p.mapping == RADIC_MAP_PREFIX) {
+    switch (p.m) {
+      case 3: return prefix_kernel<3>(terms);
+      case 4: return prefix_kernel<4>(terms);
+      case 5: return prefix_kernel<5>(terms);
+      case 6: return prefix_kernel<6>(terms);
+      case 7: return prefix_kernel<7>(terms);
+      case 8: return prefix_kernel<8>(terms);
+      case 9: return prefix_kernel<9>(terms);
+      case 10: return prefix_kernel<10>(terms);
+      default: return nullptr;
+    }
+  }
   if (p.mapping == RADIC_MAP_THREAD) {
     switch (p.m) {
       case 1: return thread_kernel<1>(terms);
@@ -40,7 +59,8 @@ const void* pick(const SinglePlan& p, bool terms) {
 }  // namespace
 
 size_t smem_fp64(const SinglePlan& p) {
-  const int cs = (p.mapping == RADIC_MAP_THREAD) ? ((p.m + 1) / 2) * 2 : p.m;
+  const int cs = (p.mapping != RADIC_MAP_GROUP) ? ((p.m + 1) / 2) * 2 : p.m;
+  if (p.mapping == RADIC_MAP_PREFIX) return prefix_smem_bytes(p.n, p.m, cs, 8, p.threads);
   return fp_smem_bytes(p.n, p.m, cs, 8, p.threads);
 }
 
@@ -48,6 +68,7 @@ int blocks_per_sm_fp64(const SinglePlan& p) {
   const void* k = pick(p, false);
   if (!k) return 0;
   int nb = 0;
+  if (!allow_smem(k, smem_fp64(p))) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, p.threads, smem_fp64(p)) != cudaSuccess) return 0;
   return nb;
 }
@@ -55,8 +76,10 @@ int blocks_per_sm_fp64(const SinglePlan& p) {
 int launch_fp64(const SinglePlan& p, const SingleArgs& a, cudaStream_t s) {
   const void* k = pick(p, a.terms != nullptr);
   if (!k) return RADIC_EUNSUPPORTED;
+  if (!allow_smem(k, smem_fp64(p))) return RADIC_EUNSUPPORTED;
   SingleArgs args = a;
-  void* params[] = {&args};
+  PrefixTable tab = p.ptab;
+  void* params[] = {&args, &tab};
   cudaEvent_t* ev = static_cast<cudaEvent_t*>(p.events);
   if (ev && cudaEventRecord(ev[0], s) != cudaSuccess) return RADIC_ECUDA;
   if (cudaLaunchKernel(k, dim3(p.blocks), dim3(p.threads), params, smem_fp64(p), s) != cudaSuccess)

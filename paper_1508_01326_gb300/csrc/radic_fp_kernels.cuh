@@ -18,6 +18,13 @@ namespace radic {
 
 constexpr int kMaxThreadsFp = 256;
 
+// Kernels whose dynamic shared memory exceeds the default 48 KiB must opt in.
+inline bool allow_smem(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return true;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) ==
+         cudaSuccess;
+}
+
 // Shared-memory layout of the floating-point kernels.
 __host__ __device__ inline size_t fp_smem_bytes(int n, int m, int cs, int elem, int threads) {
   size_t off = ((size_t)(n + 1) * (m + 1) * 8 + 15) / 16 * 16;
@@ -66,6 +73,37 @@ __device__ inline void write_fp_result(radic_result* out, const Dd& t, double ab
   out->n_primes = 0;
   out->tier = tier;
   for (int i = 0; i < 6; ++i) out->reserved[i] = 0;
+}
+
+// Last block of the main kernel: sums the per-block partials in block order
+// and writes the result.  In the mixed mode it also leaves the totals and the
+// number of flagged entries in the workspace header for the fix-up kernel,
+// which rewrites the result only when something was flagged.
+template <bool kMixed>
+__device__ inline void finish_fp_main(const SingleArgs& a, double* scratch, int escale, int m) {
+  if (!last_block(&a.hdr->ticket[0])) return;
+  Dd t;
+  double ab = 0.0;
+  long long fl = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    Dd o;
+    o.hi = __ldcg(&a.partials[b].hi);
+    o.lo = __ldcg(&a.partials[b].lo);
+    t.merge(o);
+    ab += __ldcg(&a.partials[b].abs_sum);
+    fl += __ldcg(&a.partials[b].count);
+  }
+  block_reduce_dd(t, ab, fl, scratch);
+  if (threadIdx.x == 0) {
+    if constexpr (kMixed) {
+      a.hdr->main_hi = t.hi;
+      a.hdr->main_lo = t.lo;
+      a.hdr->main_abs = ab;
+      a.hdr->flag_total = fl;
+      a.hdr->escale = escale;
+    }
+    write_fp_result(a.out, t, ab, escale, m, a.total, 0, a.hdr->status, kMixed ? kModeMixed : kModeFp64);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -165,23 +203,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
     }
     block_reduce_dd(acc, abs_sum, cnt, sm.scratch);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, cnt};
-    if constexpr (!kMixed) {
-      if (last_block(&a.hdr->ticket[0])) {
-        Dd t;
-        double ab = 0.0;
-        long long c2 = 0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-          Dd o;
-          o.hi = __ldcg(&a.partials[b].hi);
-          o.lo = __ldcg(&a.partials[b].lo);
-          t.merge(o);
-          ab += __ldcg(&a.partials[b].abs_sum);
-        }
-        block_reduce_dd(t, ab, c2, sm.scratch);
-        if (threadIdx.x == 0)
-          write_fp_result(a.out, t, ab, escale, M, a.total, 0, a.hdr->status, kModeFp64);
-      }
-    }
+    finish_fp_main<kMixed>(a, sm.scratch, escale, M);
   }
 }
 
@@ -323,23 +345,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
     }
     block_reduce_dd(acc, abs_sum, cnt, sm.scratch);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, cnt};
-    if constexpr (!kMixed) {
-      if (last_block(&a.hdr->ticket[0])) {
-        Dd t;
-        double ab = 0.0;
-        long long c2 = 0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-          Dd o;
-          o.hi = __ldcg(&a.partials[b].hi);
-          o.lo = __ldcg(&a.partials[b].lo);
-          t.merge(o);
-          ab += __ldcg(&a.partials[b].abs_sum);
-        }
-        block_reduce_dd(t, ab, c2, sm.scratch);
-        if (threadIdx.x == 0)
-          write_fp_result(a.out, t, ab, escale, m, a.total, 0, a.hdr->status, kModeFp64);
-      }
-    }
+    finish_fp_main<kMixed>(a, sm.scratch, escale, m);
   }
 }
 

@@ -19,6 +19,8 @@ constexpr int kMaxPrimes = RADIC_MAX_PRIMES;
 constexpr int kThreadMaxMFp64 = 8;   // thread mapping limits (register budget)
 constexpr int kThreadMaxMFp32 = 12;
 constexpr int kThreadMaxMModp = 12;
+constexpr int kPrefixMaxMFp64 = 10;  // prefix mapping limits
+constexpr int kPrefixMaxMFp32 = 12;
 
 // 31-bit primes of the exact mode (largest primes below 2^31).
 constexpr uint32_t kPrime0 = 2147483647u, kPrime1 = 2147483629u, kPrime2 = 2147483587u, kPrime3 = 2147483579u;
@@ -29,7 +31,12 @@ struct WsHeader {
   unsigned int ticket[4];   // last-block tickets of up to four kernels
   int overflow;             // MIXED: some warp's flag list overflowed
   int status;               // device-side status
-  long long reserved[6];
+  double main_hi, main_lo;  // MIXED: binary32 kernel total (scaled rows), two-sum form
+  double main_abs;          // MIXED: its sum of |terms|
+  long long flag_total;     // MIXED: flagged minors or prefixes seen by the main kernel
+  int escale;               // exponent of the row scaling
+  int pad;
+  long long reserved[1];
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
 
@@ -39,12 +46,24 @@ struct FpPartial {
   long long count;
 };
 
+// Per-group task table of the prefix mapping, passed by value to the kernel.
+// Group v holds the prefixes whose last column is v; a warp task covers 32
+// runs of run[v] consecutive prefixes of one group.
+struct PrefixTable {
+  int v_lo, v_hi;                          // groups v_lo .. v_hi
+  unsigned long long total_tasks;          // warp tasks over all groups
+  unsigned long long count[kMaxN];         // prefixes in group v: C(v, m-3)
+  unsigned long long run[kMaxN];           // prefixes per lane in one task
+  unsigned long long task_start[kMaxN];    // first task index of group v
+};
+
 // Launch plan of one single-matrix call (computed identically by
 // radic_workspace_bytes and radic_det).
 struct SinglePlan {
   int mode = 0, m = 0, n = 0;
   int mapping = RADIC_MAP_THREAD;  // resolved mapping
   int group = 0;                   // lanes per minor for the group mapping
+  PrefixTable ptab{};              // prefix mapping only
   int threads = 128;
   int blocks = 1;
   unsigned long long ranks_per_task = 64;
@@ -69,7 +88,8 @@ struct SingleArgs {
   unsigned long long total, tasks;
   double growth;
   int flag_cap;
-  int n_warps;  // warps in the main grid (flag lists)
+  int flag_prefix;  // 0: flag lists hold ranks; P > 0: they hold P-column prefixes
+  int n_warps;      // warps in the main grid (flag lists)
   WsHeader* hdr;
   FpPartial* partials;
   FpPartial* partials2;

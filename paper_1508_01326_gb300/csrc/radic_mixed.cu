@@ -5,7 +5,7 @@
 // the same stream recomputes exactly those minors in binary64 and performs
 // the final fixed-order reduction.  If any list overflowed, the second kernel
 // recomputes every minor in binary64 instead.
-#include "radic_fp_kernels.cuh"
+#include "radic_prefix.cuh"
 
 namespace radic {
 
@@ -57,31 +57,50 @@ __device__ double signed_minor_f64(const FpSmem<double>& sm, int n, int m, unsig
   return sign_negative_dyn<MC>(c, m) ? -det : det;
 }
 
-// Row exponents of the staging scale (sum_i e_i), computed without staging A.
-__device__ inline int row_scale_exponent(const SingleArgs& a, int* row_exp) {
-  for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
-    double mx = 0.0;
-    for (int j = 0; j < a.n; ++j) mx = fmax(mx, fabs(load_elem(a.A, a.dtype, (long long)i * a.lda + j)));
-    int e = 0;
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
-    row_exp[i] = e;
+// Binary64 sum over every minor of the lexicographic subtree of one
+// (m-2)-column prefix (given by its rank among all (m-2)-subsets of
+// {0..n-1}): the minors that the prefix kernel left out after flagging.
+template <int MC>
+__device__ long long prefix_leaves_f64(const FpSmem<double>& sm, int n, int m, int P, unsigned long long rp, Dd& acc,
+                                       double& abs_sum) {
+  long long cnt = 0;
+  int pre[MC];
+  // the binomial table is built for k <= m, which covers P = m - 2
+  unrank_dyn<MC>(rp, n, P, sm.binom, m + 1, pre);
+  const int v = pre[P - 1];
+  for (int c1 = v + 1; c1 < n; ++c1) {
+    for (int c2 = c1 + 1; c2 < n; ++c2) {
+      int cols[MC];
+      for (int j = 0; j < P; ++j) cols[j] = pre[j];
+      cols[P] = c1;
+      cols[P + 1] = c2;
+      double a[MC * MC];
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) a[i * MC + j] = sm.As[cols[j] * m + i];
+      double det = lu_det_local<MC>(a, m);
+      if (sign_negative_dyn<MC>(cols, m)) det = -det;
+      acc.add(det);
+      abs_sum += fabs(det);
+      ++cnt;
+    }
   }
-  __syncthreads();
-  int tot = 0;
-  for (int i = 0; i < a.m; ++i) tot += row_exp[i];
-  return tot;
+  return cnt;
 }
 
-// Binary64 recomputation of the flagged minors and final reduction.  Block b
-// owns the flag lists of a contiguous range of warps of the main kernel; a
-// block whose lists are empty skips staging altogether.
+// Binary64 recomputation of the flagged minors (or of every minor when a flag
+// list overflowed).  The main kernel has already written the result without
+// the flagged minors; when nothing was flagged every block returns at once.
+// Otherwise block b owns the flag lists of a contiguous range of warps of the
+// main kernel, and the last block adds the recomputed sums to the main totals
+// kept in the workspace header and rewrites the result.
 template <int MC>
 __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_blocks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int has_work;
+  const bool overflow = __ldcg(&a.hdr->overflow) != 0;
+  if (!overflow && __ldcg(&a.hdr->flag_total) == 0) return;
   const int n = a.n, m = a.m;
   FpSmem<double> sm(smem_raw, n, m, m);
-  const bool overflow = __ldcg(&a.hdr->overflow) != 0;
   const int wpb = (a.n_warps + gridDim.x - 1) / gridDim.x;
   const int w0 = blockIdx.x * wpb, w1 = min(w0 + wpb, a.n_warps);
   if (threadIdx.x == 0) has_work = overflow ? 1 : 0;
@@ -95,6 +114,7 @@ __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_bloc
 
   Dd acc;
   double abs_sum = 0.0;
+  long long done = 0;
   if (has_work) {
     build_binom(sm.binom, n, m);
     stage_scaled<double>(a.A, a.dtype, m, n, a.lda, sm.As, m, sm.row_exp);
@@ -108,6 +128,7 @@ __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_bloc
           double absd;
           acc.add(signed_minor_f64<MC>(sm, n, m, q, absd));
           abs_sum += absd;
+          ++done;
         }
       }
     } else {
@@ -115,42 +136,44 @@ __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_bloc
       for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
         const long long w = s / a.flag_cap, i = s - w * a.flag_cap;
         if (i < __ldcg(&a.flag_count[w])) {
-          double absd;
-          acc.add(signed_minor_f64<MC>(sm, n, m, __ldcg(&a.flag_ranks[s]), absd));
-          abs_sum += absd;
+          const unsigned long long e = __ldcg(&a.flag_ranks[s]);
+          if (a.flag_prefix == 0) {
+            double absd;
+            acc.add(signed_minor_f64<MC>(sm, n, m, e, absd));
+            abs_sum += absd;
+            ++done;
+          } else {
+            done += prefix_leaves_f64<MC>(sm, n, m, a.flag_prefix, e, acc, abs_sum);
+          }
         }
       }
     }
   }
-  long long cnt = 0;
-  block_reduce_dd(acc, abs_sum, cnt, sm.scratch);
-  if (threadIdx.x == 0) a.partials2[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, 0};
+  block_reduce_dd(acc, abs_sum, done, sm.scratch);
+  if (threadIdx.x == 0) a.partials2[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, done};
   if (last_block(&a.hdr->ticket[1])) {
-    const int escale = row_scale_exponent(a, sm.row_exp);
     Dd t;
     double ab = 0.0;
     long long flagged = 0;
-    if (!overflow) {
-      for (int b = threadIdx.x; b < main_blocks; b += blockDim.x) {
-        Dd o;
-        o.hi = __ldcg(&a.partials[b].hi);
-        o.lo = __ldcg(&a.partials[b].lo);
-        t.merge(o);
-        ab += __ldcg(&a.partials[b].abs_sum);
-        flagged += __ldcg(&a.partials[b].count);
-      }
-    }
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
       Dd o;
       o.hi = __ldcg(&a.partials2[b].hi);
       o.lo = __ldcg(&a.partials2[b].lo);
       t.merge(o);
       ab += __ldcg(&a.partials2[b].abs_sum);
+      flagged += __ldcg(&a.partials2[b].count);
     }
     block_reduce_dd(t, ab, flagged, sm.scratch);
     if (threadIdx.x == 0) {
-      if (overflow) flagged = static_cast<long long>(a.total);
-      write_fp_result(a.out, t, ab, escale, m, a.total, flagged, __ldcg(&a.hdr->status), kModeMixed);
+      if (!overflow) {
+        Dd mainsum;
+        mainsum.hi = __ldcg(&a.hdr->main_hi);
+        mainsum.lo = __ldcg(&a.hdr->main_lo);
+        t.merge(mainsum);
+        ab += __ldcg(&a.hdr->main_abs);
+      }
+      write_fp_result(a.out, t, ab, __ldcg(&a.hdr->escale), m, a.total, flagged, __ldcg(&a.hdr->status),
+                      kModeMixed);
     }
   }
 }
@@ -167,7 +190,28 @@ const void* group_kernel(bool terms) {
                : reinterpret_cast<const void*>(&k_fp_group<float, G, true, false>);
 }
 
+template <int M>
+const void* prefix_kernel(bool terms) {
+  return terms ? reinterpret_cast<const void*>(&k_fp_prefix<float, M, true, true>)
+               : reinterpret_cast<const void*>(&k_fp_prefix<float, M, true, false>);
+}
+
 const void* pick(const SinglePlan& p, bool terms) {
+  if (p.mapping == RADIC_MAP_PREFIX) {
+    switch (p.m) {
+      case 3: return prefix_kernel<3>(terms);
+      case 4: return prefix_kernel<4>(terms);
+      case 5: return prefix_kernel<5>(terms);
+      case 6: return prefix_kernel<6>(terms);
+      case 7: return prefix_kernel<7>(terms);
+      case 8: return prefix_kernel<8>(terms);
+      case 9: return prefix_kernel<9>(terms);
+      case 10: return prefix_kernel<10>(terms);
+      case 11: return prefix_kernel<11>(terms);
+      case 12: return prefix_kernel<12>(terms);
+      default: return nullptr;
+    }
+  }
   if (p.mapping == RADIC_MAP_THREAD) {
     switch (p.m) {
       case 1: return thread_kernel<1>(terms);
@@ -199,7 +243,8 @@ const void* pick_fixup(int m) {
 }  // namespace
 
 size_t smem_mixed(const SinglePlan& p) {
-  const int cs = (p.mapping == RADIC_MAP_THREAD) ? ((p.m + 3) / 4) * 4 : p.m;
+  const int cs = (p.mapping != RADIC_MAP_GROUP) ? ((p.m + 3) / 4) * 4 : p.m;
+  if (p.mapping == RADIC_MAP_PREFIX) return prefix_smem_bytes(p.n, p.m, cs, 4, p.threads);
   return fp_smem_bytes(p.n, p.m, cs, 4, p.threads);
 }
 
@@ -209,6 +254,7 @@ int blocks_per_sm_mixed(const SinglePlan& p) {
   const void* k = pick(p, false);
   if (!k) return 0;
   int nb = 0;
+  if (!allow_smem(k, smem_mixed(p))) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, p.threads, smem_mixed(p)) != cudaSuccess) return 0;
   return nb;
 }
@@ -217,8 +263,10 @@ int launch_mixed(const SinglePlan& p, const SingleArgs& a, cudaStream_t s) {
   const bool terms = a.terms != nullptr;
   const void* k = pick(p, terms);
   if (!k) return RADIC_EUNSUPPORTED;
+  if (!allow_smem(k, smem_mixed(p))) return RADIC_EUNSUPPORTED;
   SingleArgs args = a;
-  void* params[] = {&args};
+  PrefixTable tab = p.ptab;
+  void* params[] = {&args, &tab};
   cudaEvent_t* ev = static_cast<cudaEvent_t*>(p.events);
   if (ev && cudaEventRecord(ev[0], s) != cudaSuccess) return RADIC_ECUDA;
   if (cudaLaunchKernel(k, dim3(p.blocks), dim3(p.threads), params, smem_mixed(p), s) != cudaSuccess)

@@ -121,17 +121,25 @@ __device__ __forceinline__ long long load_int(const void* A, int dtype, long lon
                       : static_cast<long long>(static_cast<const int32_t*>(A)[idx]);
 }
 
-// Number of primes for |det_R(A)| <= C(n,m) prod_i ||row_i||_2, plus sign.
-__device__ inline int primes_needed(const void* A, int dtype, int m, int n, long long lda, double log2_count) {
-  double bits = log2_count;
-  for (int i = 0; i < m; ++i) {
+// Number of primes for |det_R(A)| <= C(n,m) prod_i ||row_i||_2 (Hadamard's
+// inequality for every minor), plus a sign bit and a margin.  One warp per
+// row computes the squared row norms into row_sq[]; thread 0 sums the logs.
+__device__ inline int primes_needed(const void* A, int dtype, int m, int n, long long lda, double log2_count,
+                                    double* row_sq) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < m; i += nw) {
     double s = 0.0;
-    for (int j = 0; j < n; ++j) {
+    for (int j = lane; j < n; j += 32) {
       const double v = static_cast<double>(load_int(A, dtype, (long long)i * lda + j));
       s += v * v;
     }
-    bits += 0.5 * log2(fmax(s, 1.0));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+    if (lane == 0) row_sq[i] = s;
   }
+  __syncthreads();
+  double bits = log2_count;
+  for (int i = 0; i < m; ++i) bits += 0.5 * log2(fmax(row_sq[i], 1.0));
   const int k = static_cast<int>(ceil((bits + 2.0) / 30.99));
   return k < 1 ? 1 : k;
 }
@@ -142,9 +150,12 @@ __device__ inline int stage_modp(const SingleArgs& a, const ModpSmem& sm, int m,
   const int n = a.n;
   build_binom(sm.binom, n, m);
   if (threadIdx.x < kMaxPrimes) sm.mont[threadIdx.x] = make_mont(prime_at(threadIdx.x));
-  if (threadIdx.x == 0) {
+  {
+    // the rows scratch (m x n words) is free until the residues are staged
+    double* row_sq = reinterpret_cast<double*>(sm.rows);
     const double cnt = static_cast<double>(sm.binom[n * (m + 1) + m]);
-    sm.misc[0] = primes_needed(a.A, a.dtype, m, n, a.lda, log2(fmax(cnt, 1.0)));
+    const int need = primes_needed(a.A, a.dtype, m, n, a.lda, log2(fmax(cnt, 1.0)), row_sq);
+    if (threadIdx.x == 0) sm.misc[0] = need;
   }
   __syncthreads();
   *needed = sm.misc[0];

@@ -62,7 +62,12 @@ OPTS = {
     "g16": dict(mapping="group", group_width=16),
     "g16_l5": dict(mapping="group", group_width=16, ranks_per_task=5),
     "g32": dict(mapping="group", group_width=32, ranks_per_task=7),
+    "prefix": dict(mapping=3),
+    "prefix_r1": dict(mapping=3, ranks_per_task=1, threads_per_block=64),
 }
+
+FP64_LIMIT = {"thread": 8, "thread_l13": 8, "prefix": 10, "prefix_r1": 10}
+MIXED_LIMIT = {"thread": 12, "thread_l13": 12, "prefix": 12, "prefix_r1": 12}
 
 
 # ---------------------------------------------------------------------------
@@ -117,6 +122,13 @@ TERM_CASES = [
     (10, 14, np.float64, "g16"),
     (12, 15, np.float64, "g16_l5"),
     (17, 19, np.float64, "g32"),
+    (3, 9, np.float64, "prefix"),
+    (4, 13, np.int32, "prefix_r1"),
+    (5, 16, np.float64, "prefix"),
+    (8, 14, np.float64, "prefix"),
+    (8, 13, np.float32, "prefix_r1"),
+    (10, 14, np.float64, "prefix"),
+    (12, 15, np.float64, "prefix"),
 ]
 
 
@@ -128,8 +140,8 @@ def _matrix(m, n, dtype, seed):
 
 @pytest.mark.parametrize("m,n,dtype,key", TERM_CASES)
 def test_terms_fp64_elementwise(m, n, dtype, key):
-    if key == "thread" and m > 8 or key == "thread_l13" and m > 8:
-        pytest.skip("binary64 thread mapping covers m <= 8")
+    if m > FP64_LIMIT.get(key, 32):
+        pytest.skip("outside the binary64 limit of this mapping")
     a = _matrix(m, n, dtype, 100 + m * n)
     total = math.comb(n, m)
     q0 = total // 7
@@ -142,8 +154,8 @@ def test_terms_fp64_elementwise(m, n, dtype, key):
 
 @pytest.mark.parametrize("m,n,dtype,key", TERM_CASES)
 def test_terms_mixed_elementwise(m, n, dtype, key):
-    if key.startswith("thread") and m > 12:
-        pytest.skip("binary32 thread mapping covers m <= 12")
+    if m > MIXED_LIMIT.get(key, 32):
+        pytest.skip("outside the binary32 limit of this mapping")
     a = _matrix(m, n, dtype, 200 + m * n)
     total = math.comb(n, m)
     q0 = total // 5
@@ -202,22 +214,38 @@ def _exact(a):
     return orc.radic_det_exact(a)
 
 
+def _mapping_ok(mapping, m, n, limits):
+    if mapping == "auto":
+        return True
+    if mapping == "group":
+        return m <= 32
+    if mapping == "prefix":
+        return 3 <= m <= limits["prefix"] and m <= n
+    return m <= limits["thread"]
+
+
+@pytest.mark.parametrize("mapping", ["auto", "thread", "group", "prefix"])
 @pytest.mark.parametrize("m,n,dtype", DET_CASES)
-def test_det_fp64_small(m, n, dtype):
+def test_det_fp64_small(m, n, dtype, mapping):
+    if not _mapping_ok(mapping, m, n, FP64_LIMIT):
+        pytest.skip("mapping does not cover this shape")
     a = _matrix(m, n, dtype, 400 + m * n)
     val, abs_sum = _exact(a)
-    res = R().det(a, mode="fp64")
+    res = R().det(a, mode="fp64", options=dict(mapping=mapping))
     assert res["minors"] == (math.comb(n, m) if m <= n else 0)
     assert abs(Fraction(res["value"]) - val) <= Fraction(1e-12) * abs_sum
     if abs_sum:
         assert abs(res["abs_sum"] - float(abs_sum)) <= 1e-12 * float(abs_sum)
 
 
+@pytest.mark.parametrize("mapping", ["auto", "thread", "group", "prefix"])
 @pytest.mark.parametrize("m,n,dtype", DET_CASES)
-def test_det_mixed_small(m, n, dtype):
+def test_det_mixed_small(m, n, dtype, mapping):
+    if not _mapping_ok(mapping, m, n, MIXED_LIMIT):
+        pytest.skip("mapping does not cover this shape")
     a = _matrix(m, n, dtype, 500 + m * n)
     val, abs_sum = _exact(a)
-    res = R().det(a, mode="mixed")
+    res = R().det(a, mode="mixed", options=dict(mapping=mapping))
     if m > n:
         assert res["value"] == 0.0 and res["minors"] == 0
         return
@@ -268,7 +296,7 @@ def test_det_is_deterministic():
         assert v1 == v2
 
 
-@pytest.mark.parametrize("key", ["thread", "g16"])
+@pytest.mark.parametrize("key", ["thread", "g16", "prefix"])
 def test_mixed_growth_flag_recomputes_in_binary64(key):
     # Partial pivoting grows the last column of this minor to 2^(m-1) times
     # its entries (Wilkinson's example), above the default threshold 64.
@@ -283,10 +311,11 @@ def test_mixed_growth_flag_recomputes_in_binary64(key):
     assert abs(res["value"] - float(val)) <= 8 * m * U32 * h
 
 
-def test_mixed_flag_list_overflow_falls_back_to_binary64():
+@pytest.mark.parametrize("mapping", ["thread", "prefix"])
+def test_mixed_flag_list_overflow_falls_back_to_binary64(mapping):
     a = W.uniform_matrix(12, 6, 14)
     val, abs_sum = _exact(a)
-    res = R().det(a, mode="mixed", options=dict(flag_capacity=1, growth_threshold=1e-30))
+    res = R().det(a, mode="mixed", options=dict(mapping=mapping, flag_capacity=1, growth_threshold=1e-30))
     assert res["flagged"] == math.comb(14, 6)
     assert abs(res["value"] - float(val)) <= 1e-12 * float(abs_sum)
 
@@ -331,9 +360,10 @@ def fp64_8x32():
     return a, orc.radic_det_pfaffian(a)
 
 
-def test_full_fp64_8x32_binary64(fp64_8x32):
+@pytest.mark.parametrize("mapping", ["auto", "thread"])
+def test_full_fp64_8x32_binary64(fp64_8x32, mapping):
     a, exact = fp64_8x32
-    res = R().det(a, mode="fp64")
+    res = R().det(a, mode="fp64", options=dict(mapping=mapping))
     assert res["minors"] == 10_518_300
     assert abs(Fraction(res["value"]) - exact) <= Fraction(1e-12) * Fraction(res["abs_sum"])
     # sum|terms| against a seeded sample of exact minors (unbiased estimate)
@@ -343,9 +373,10 @@ def test_full_fp64_8x32_binary64(fp64_8x32):
     assert abs(res["abs_sum"] - est) <= 0.10 * est
 
 
-def test_full_fp64_8x32_mixed(fp64_8x32):
+@pytest.mark.parametrize("mapping", ["auto", "thread"])
+def test_full_fp64_8x32_mixed(fp64_8x32, mapping):
     a, exact = fp64_8x32
-    res = R().det(a, mode="mixed")
+    res = R().det(a, mode="mixed", options=dict(mapping=mapping))
     rel = abs(float(Fraction(res["value"]) - exact)) / res["abs_sum"]
     assert rel <= 1e-10, rel
 
