@@ -21,7 +21,7 @@
  *  - Matrices are row-major: element (i, j) of A is A[i * lda + j], lda >= n.
  *  - "device" pointers are CUDA device memory on the current device and are
  *    owned by the caller; the library never frees them.  "host" pointers are
- *    ordinary host memory.  Except where stated (radic_batch_graph_create),
+ *    ordinary host memory.  Except where stated (batch plans and graphs),
  *    the library allocates no memory: scratch memory is the caller's
  *    `workspace` of at least the size that the matching *_workspace_bytes
  *    function returns.
@@ -181,6 +181,70 @@ int radic_terms(const void* A, int m, int n, int64_t lda, int dtype, int mode,
  * RADIC_ECUDA. */
 int radic_unrank(int n, int m, uint64_t q0, uint64_t count, uint8_t* cols,
                  const radic_options* opts, void* stream);
+
+/* ---- batches of matrices of uneven shape ------------------------------- */
+
+/* Host-side plan (opaque) of one batch layout, and a captured CUDA graph of
+ * one batched call. */
+typedef struct radic_batch_plan radic_batch_plan;
+typedef struct radic_batch_graph radic_batch_graph;
+
+/* Per-m tuning of the batched path (written by the autotuner; zero fields
+ * mean "default").  kind[m]: RADIC_MAP_PREFIX or RADIC_MAP_THREAD (per-minor,
+ * m <= 8).  task_cost[m]: target work per lane and task, in the plan's cost
+ * units (default 30000; smaller = more, shorter tasks). */
+typedef struct radic_batch_tuning {
+  int32_t kind[RADIC_MAX_M + 1];
+  double task_cost[RADIC_MAX_M + 1];
+  double tol;              /* MIXED: target |err| / sum|terms| (default 1e-10) */
+  double growth_threshold; /* MIXED: growth flag threshold (default 64)         */
+  int32_t blocks_per_sm;   /* cap on resident blocks per SM (0: occupancy)     */
+  int32_t reserved[7];
+} radic_batch_tuning;
+
+/* Builds the plan of `batch` matrices: matrix b is m[b] x n[b], row-major
+ * with leading dimension n[b], starting offsets[b] elements into one packed
+ * buffer (all three arrays are host memory).  mode is RADIC_MODE_FP64 or
+ * RADIC_MODE_MIXED.  In MIXED mode each matrix is routed to binary32
+ * elimination (binary64 sums, binary64 recompute of flagged tasks) when the
+ * expected binary32 error, 2.5e-6 / sqrt(C(n,m)) relative to sum|terms|
+ * (an envelope of measured errors on random inputs), meets tuning->tol, and
+ * to binary64 otherwise; the result's `tier` field tells which.  The work of every matrix is cut into warp tasks
+ * (runs of prefixes or of dictionary ranks, per the tuning) for two
+ * persistent kernels with atomic work queues, one per tier, followed by a
+ * per-matrix fixed-order reduction.  Limits: 1 <= m <= 10, n <= 64.
+ * The plan is host memory owned by the library until
+ * radic_batch_plan_destroy.  Errors: RADIC_EINVAL, RADIC_EUNSUPPORTED
+ * (EXACT mode, m > 10), RADIC_ECUDA. */
+int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* offsets, int batch, int mode,
+                            const radic_batch_tuning* tuning, radic_batch_plan** plan);
+int radic_batch_plan_destroy(radic_batch_plan* plan);
+
+/* Workspace bytes the plan needs (256-byte aligned device memory). */
+size_t radic_batch_workspace_bytes(const radic_batch_plan* plan);
+
+/* info (host, 8 entries): tasks of the binary32 and binary64 tiers,
+ * matrices routed to each tier, minors in each tier, persistent grid sizes. */
+int radic_batch_plan_info(const radic_batch_plan* plan, int64_t* info);
+
+/* Copies the plan's task tables into `workspace` (once per workspace, before
+ * the first batched call or graph capture).  Waits for the copies. */
+int radic_batch_upload(const radic_batch_plan* plan, void* workspace, size_t workspace_bytes, void* stream);
+
+/* det_R of every matrix of the batch.  A: device, packed matrices of type
+ * dtype; out: device, `batch` radic_result; workspace: uploaded with
+ * radic_batch_upload.  Calls on the same workspace must not overlap. */
+int radic_det_batched(const radic_batch_plan* plan, const void* A, int dtype, radic_result* out, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* Captures one radic_det_batched call on these buffers into a CUDA graph
+ * owned by the library (the one allocation it makes); launch it any number
+ * of times with radic_batch_graph_launch, free it with
+ * radic_batch_graph_destroy. */
+int radic_batch_graph_create(const radic_batch_plan* plan, const void* A, int dtype, radic_result* out,
+                             void* workspace, size_t workspace_bytes, radic_batch_graph** graph);
+int radic_batch_graph_launch(radic_batch_graph* graph, void* stream);
+int radic_batch_graph_destroy(radic_batch_graph* graph);
 
 /* ---- allocation-free variant ------------------------------------------- */
 

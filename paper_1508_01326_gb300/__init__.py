@@ -8,7 +8,11 @@ library is loaded on first use and its absence is an error.
 """
 from ._lib import RadicError, make_options  # noqa: F401
 from .api import (  # noqa: F401
+    BatchGraph,
+    BatchPlan,
     det,
+    make_tuning,
+    parse_results,
     new_result,
     parse_result,
     radic_det,

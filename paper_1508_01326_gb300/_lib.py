@@ -34,6 +34,17 @@ class RadicOptions(ctypes.Structure):
 
 RESULT_WORDS = 16  # radic_result is sixteen 8-byte words
 
+
+class RadicBatchTuning(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32 * (RADIC_MAX_M + 1)),
+        ("task_cost", ctypes.c_double * (RADIC_MAX_M + 1)),
+        ("tol", ctypes.c_double),
+        ("growth_threshold", ctypes.c_double),
+        ("blocks_per_sm", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
+    ]
+
 _lib = None
 
 
@@ -77,17 +88,20 @@ def lib() -> ctypes.CDLL:
 def _declare_optional(L: ctypes.CDLL) -> None:
     """Declarations of the batched, backward and allocation-free entry points."""
     vp, sz, i32, i64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int64
+    pp = ctypes.POINTER(vp)
     table = {
-        "radic_batch_plan_create": ([vp, vp, i32, i32, vp, ctypes.POINTER(vp)], i32),
+        "radic_batch_plan_create": ([vp, vp, vp, i32, i32, vp, pp], i32),
         "radic_batch_plan_destroy": ([vp], i32),
         "radic_batch_plan_info": ([vp, ctypes.POINTER(i64)], i32),
         "radic_batch_workspace_bytes": ([vp], sz),
-        "radic_det_batched": ([vp, vp, vp, vp, vp, i32, vp, vp, sz, vp], i32),
-        "radic_batch_graph_create": ([vp, vp, vp, vp, vp, i32, vp, vp, sz, ctypes.POINTER(vp)], i32),
+        "radic_batch_upload": ([vp, vp, sz, vp], i32),
+        "radic_det_batched": ([vp, vp, i32, vp, vp, sz, vp], i32),
+        "radic_batch_graph_create": ([vp, vp, i32, vp, vp, sz, pp], i32),
         "radic_batch_graph_launch": ([vp, vp], i32),
         "radic_batch_graph_destroy": ([vp], i32),
         "radic_backward_workspace_bytes": ([i32, i32, i32], sz),
         "radic_det_backward": ([vp, i32, i32, i32, i64, i64, vp, vp, vp, sz, vp], i32),
+        "radic_det_noalloc": ([vp, i32, i32, i64, i32, vp, vp, vp], i32),
     }
     for name, (args, res) in table.items():
         fn = getattr(L, name, None)

@@ -147,3 +147,121 @@ def det(A, mode="fp64", options=None, stream=None) -> dict:
     if _mode(mode) == L.MODES["exact"]:
         res["value_exact"] = Fraction(res["exact"])
     return res
+
+
+# ---------------------------------------------------------------------------
+# Batches of matrices of uneven shape
+# ---------------------------------------------------------------------------
+
+
+def make_tuning(kind=None, task_cost=None, tol=0.0, growth_threshold=0.0, blocks_per_sm=0) -> "L.RadicBatchTuning":
+    """Batched-path tuning: `kind` and `task_cost` map m to a mapping name and a task size."""
+    t = L.RadicBatchTuning()
+    for m, k in (kind or {}).items():
+        t.kind[int(m)] = L.MAPPINGS[k] if isinstance(k, str) else int(k)
+    for m, c in (task_cost or {}).items():
+        t.task_cost[int(m)] = float(c)
+    t.tol = tol
+    t.growth_threshold = growth_threshold
+    t.blocks_per_sm = blocks_per_sm
+    return t
+
+
+class BatchPlan:
+    """A plan for a batch of matrices (shapes and packing fixed), with its workspace.
+
+    shapes: list of (m, n); matrix b is stored row-major (leading dimension n)
+    at element offset offsets[b] of one packed device buffer.
+    """
+
+    def __init__(self, shapes, offsets=None, mode="mixed", tuning=None, device="cuda", stream=None):
+        shapes = [(int(m), int(n)) for m, n in shapes]
+        if offsets is None:
+            offsets, acc = [], 0
+            for m, n in shapes:
+                offsets.append(acc)
+                acc += m * n
+        self.batch = len(shapes)
+        self.shapes = shapes
+        self.mode = mode
+        self._m = (ctypes.c_int32 * self.batch)(*[m for m, _ in shapes])
+        self._n = (ctypes.c_int32 * self.batch)(*[n for _, n in shapes])
+        self._off = (ctypes.c_int64 * self.batch)(*[int(o) for o in offsets])
+        self._tuning = tuning
+        lib = L.lib()
+        handle = ctypes.c_void_p()
+        rc = lib.radic_batch_plan_create(self._m, self._n, self._off, self.batch, _mode(mode),
+                                         ctypes.byref(tuning) if tuning is not None else None, ctypes.byref(handle))
+        L.check("radic_batch_plan_create", rc)
+        self._plan = handle
+        self.ws_bytes = int(lib.radic_batch_workspace_bytes(self._plan))
+        self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=device)
+        rc = lib.radic_batch_upload(self._plan, self.workspace.data_ptr(), self.workspace.numel(), _stream(stream))
+        L.check("radic_batch_upload", rc)
+        self._graphs = []
+
+    def info(self) -> dict:
+        buf = (ctypes.c_int64 * 8)()
+        L.check("radic_batch_plan_info", L.lib().radic_batch_plan_info(self._plan, buf))
+        keys = ["tasks_fp32", "tasks_fp64", "matrices_fp32", "matrices_fp64", "minors_fp32", "minors_fp64",
+                "blocks_fp32", "blocks_fp64"]
+        return dict(zip(keys, [int(x) for x in buf]))
+
+    def new_results(self) -> torch.Tensor:
+        return torch.empty((self.batch, L.RESULT_WORDS), dtype=torch.int64, device=self.workspace.device)
+
+    def radic_det_batched(self, A: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        if A.dtype not in _TORCH_DTYPES or not A.is_cuda:
+            raise TypeError("A must be a packed CUDA tensor of a supported dtype")
+        if out is None:
+            out = self.new_results()
+        rc = L.lib().radic_det_batched(self._plan, A.data_ptr(), _TORCH_DTYPES[A.dtype], out.data_ptr(),
+                                       self.workspace.data_ptr(), self.workspace.numel(), _stream(stream))
+        L.check("radic_det_batched", rc)
+        return out
+
+    def graph(self, A: torch.Tensor, out: torch.Tensor) -> "BatchGraph":
+        g = BatchGraph(self, A, out)
+        self._graphs.append(g)
+        return g
+
+    def close(self) -> None:
+        for g in self._graphs:
+            g.close()
+        self._graphs = []
+        if self._plan:
+            L.lib().radic_batch_plan_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchGraph:
+    """A captured CUDA graph of one batched call on fixed buffers."""
+
+    def __init__(self, plan: BatchPlan, A: torch.Tensor, out: torch.Tensor):
+        self.plan, self.A, self.out = plan, A, out  # keep the buffers alive
+        handle = ctypes.c_void_p()
+        rc = L.lib().radic_batch_graph_create(plan._plan, A.data_ptr(), _TORCH_DTYPES[A.dtype], out.data_ptr(),
+                                              plan.workspace.data_ptr(), plan.workspace.numel(),
+                                              ctypes.byref(handle))
+        L.check("radic_batch_graph_create", rc)
+        self._g = handle
+
+    def launch(self, stream=None) -> None:
+        L.check("radic_batch_graph_launch", L.lib().radic_batch_graph_launch(self._g, _stream(stream)))
+
+    def close(self) -> None:
+        if self._g:
+            L.lib().radic_batch_graph_destroy(self._g)
+            self._g = None
+
+
+def parse_results(buf: torch.Tensor) -> list:
+    """List of result dictionaries of a (batch, 16) result buffer."""
+    host = buf.detach().to("cpu").contiguous()
+    return [parse_result(host[b]) for b in range(host.shape[0])]

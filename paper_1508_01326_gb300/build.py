@@ -25,6 +25,7 @@ SOURCES = [
     "radic_mixed.cu",
     "radic_modp.cu",
     "radic_noalloc.cu",
+    "radic_batched.cu",
 ]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]

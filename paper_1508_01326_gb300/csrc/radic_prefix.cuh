@@ -160,6 +160,85 @@ struct PrefixAcc<float> {
   }
 };
 
+// Two-entry vector type of T.
+template <typename T>
+struct Pair2 {
+  using type = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+};
+
+// Where per-leaf terms go (terms output of the parity tests); unused otherwise.
+struct TermsSink {
+  double* terms;
+  unsigned long long q0, count, qtot;
+  int escale;
+};
+
+// Processes one prefix c[0..m-3] (last column v): factors it, reduces every
+// later column to its Schur complement, forms the 2 x 2 leaf determinants
+// with the sign of Eq. (1) and adds them to acc.pre (the caller commits or
+// drops them).  `zb` is this lane's slot of the column buffer, `zstride` the
+// distance between consecutive columns.  Returns the growth flag of the mixed
+// mode: largest prefix pivot, or twice the largest Schur entry (a bound for
+// the last two pivots), above `thr`, or a non-finite scale.
+template <typename T, int M, int CS, bool kTerms>
+__device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint64_t* binom, int n, int v,
+                                           const int (&c)[M - 2], typename Pair2<T>::type* zb, int zstride, T thr,
+                                           bool act, PrefixAcc<T>& acc, const TermsSink& ts) {
+  constexpr int P = M - 2;
+  using T2 = typename Pair2<T>::type;
+  const int bs = M + 1;
+  T W[2][P];
+  int idx[M];
+  T prod, gmax;
+  bool neg;
+  prefix_factor<T, M, CS>(As, c, W, idx, prod, gmax, neg);
+  // parity of r = M(M+1)/2, of the prefix columns' share of s, and of the two
+  // leaf columns' "+1" terms; the leaf columns' own parities are folded in below
+  int sp = M * (M + 1) / 2 + 2;
+#pragma unroll
+  for (int j = 0; j < P; ++j) sp += c[j] + 1;
+  const T alpha = ((sp & 1) != neg) ? -prod : prod;
+  unsigned long long rank_prefix = 0;
+  if constexpr (kTerms) {
+#pragma unroll
+    for (int j = 0; j < P; ++j) rank_prefix += rank_part(binom, bs, n, c[j], M - j);
+  }
+  T zmax = T(0);
+  const int k = n - 1 - v;
+  for (int q = 0; q < k; ++q) {
+    const int col = v + 1 + q;
+    T z0, z1;
+    prefix_column<T, M>(As + col * CS, W, idx, z0, z1);
+    zmax = fmax(zmax, fmax(fabs(z0), fabs(z1)));
+    if (col & 1) {
+      z0 = -z0;
+      z1 = -z1;
+    }
+    z0 *= alpha;
+    T colsum = T(0), colabs = T(0);
+    const T2* yp = zb;
+#pragma unroll 4
+    for (int q2 = 0; q2 < q; ++q2, yp += zstride) {
+      const T2 y = *yp;
+      const T d = fma(y.x, z1, -(y.y * z0));
+      if constexpr (kTerms) {
+        const int c2 = v + 1 + q2;
+        const unsigned long long rk =
+            ts.qtot - 1 - (rank_prefix + rank_part(binom, bs, n, c2, 2) + rank_part(binom, bs, n, col, 1));
+        if (act && rk >= ts.q0 && rk < ts.q0 + ts.count) ts.terms[rk - ts.q0] = ldexp(static_cast<double>(d), ts.escale);
+      }
+      colsum += d;
+      colabs += fabs(d);
+    }
+    T2 zz;
+    zz.x = z0;
+    zz.y = z1;
+    zb[q * zstride] = zz;
+    if (act) acc.add_column(colsum, colabs);
+  }
+  return !(gmax <= thr) || !(2 * zmax <= thr) || !(fabs(alpha) <= static_cast<T>(FLT_MAX));
+}
+
 // ---------------------------------------------------------------------------
 // Single-matrix prefix kernel.
 // ---------------------------------------------------------------------------
@@ -180,15 +259,12 @@ __global__ void __launch_bounds__(128) k_fp_prefix(SingleArgs a, PrefixTable tab
   const unsigned long long nwarps = (unsigned long long)gridDim.x * blockDim.x / 32;
   const T thr = static_cast<T>(a.growth);
   const int bs = M + 1;  // binomial table stride
-  // parity of r = M(M+1)/2 plus the two leaf columns' "+1" terms of s
-  const int par_const = (M * (M + 1) / 2 + 2) & 1;
 
   PrefixAcc<T> acc;
   int fcnt = 0;
   unsigned long long* flist = nullptr;
   if constexpr (kMixed && !kTerms) flist = a.flag_ranks + gwarp * (unsigned long long)a.flag_cap;
-  unsigned long long qtot = 0;
-  if constexpr (kTerms) qtot = sm.binom[n * bs + M];
+  TermsSink ts{static_cast<double*>(a.terms), a.q0, a.count, sm.binom[n * bs + M], escale};
 
   for (unsigned long long t = gwarp; t < tab.total_tasks; t += nwarps) {
     int v = tab.v_lo;
@@ -196,7 +272,6 @@ __global__ void __launch_bounds__(128) k_fp_prefix(SingleArgs a, PrefixTable tab
     const unsigned long long runlen = tab.run[v], cnt = tab.count[v];
     const unsigned long long r0 = (t - tab.task_start[v]) * 32ull * runlen + (unsigned long long)lane * runlen;
     const unsigned long long r1 = min(r0 + runlen, cnt);
-    const int k = n - 1 - v;  // candidate columns v+1 .. n-1
     constexpr int H = P > 1 ? P - 1 : 1;
     int head[H];  // first P-1 prefix columns, a (P-1)-subset of {0..v-1}
     if constexpr (P > 1) unrank<P - 1>(r0 < cnt ? r0 : 0ull, v, sm.binom, bs, head);
@@ -206,60 +281,10 @@ __global__ void __launch_bounds__(128) k_fp_prefix(SingleArgs a, PrefixTable tab
 #pragma unroll
       for (int j = 0; j < P - 1; ++j) c[j] = head[j];
       c[P - 1] = v;
-      T W[2][P];
-      int idx[M];
-      T prod, gmax;
-      bool neg;
-      prefix_factor<T, M, CS>(sm.As, c, W, idx, prod, gmax, neg);
-      int sp = par_const;
-#pragma unroll
-      for (int j = 0; j < P; ++j) sp += c[j] + 1;
-      const T alpha = ((sp & 1) != neg) ? -prod : prod;
-      unsigned long long rank_prefix = 0;
-      if constexpr (kTerms) {
-#pragma unroll
-        for (int j = 0; j < P; ++j) rank_prefix += rank_part(sm.binom, bs, n, c[j], M - j);
-      }
-      T zmax = T(0);
-      using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+      using T2 = typename Pair2<T>::type;
       T2* zb = reinterpret_cast<T2*>(zbuf) + threadIdx.x;  // column q at zb[q * blockDim.x]
-      const int zstride = blockDim.x;
-      for (int q = 0; q < k; ++q) {
-        const int col = v + 1 + q;
-        T z0, z1;
-        prefix_column<T, M>(sm.As + col * CS, W, idx, z0, z1);
-        zmax = fmax(zmax, fmax(fabs(z0), fabs(z1)));
-        if (col & 1) {
-          z0 = -z0;
-          z1 = -z1;
-        }
-        z0 *= alpha;
-        T colsum = T(0), colabs = T(0);
-        const T2* yp = zb;
-#pragma unroll 4
-        for (int q2 = 0; q2 < q; ++q2, yp += zstride) {
-          const T2 y = *yp;
-          const T d = fma(y.x, z1, -(y.y * z0));
-          if constexpr (kTerms) {
-            const int c2 = v + 1 + q2;
-            const unsigned long long rk = qtot - 1 - (rank_prefix + rank_part(sm.binom, bs, n, c2, 2) +
-                                                      rank_part(sm.binom, bs, n, col, 1));
-            if (act && rk >= a.q0 && rk < a.q0 + a.count)
-              static_cast<double*>(a.terms)[rk - a.q0] = ldexp(static_cast<double>(d), escale);
-          }
-          colsum += d;
-          colabs += fabs(d);
-        }
-        T2 zz;
-        zz.x = z0;
-        zz.y = z1;
-        zb[q * zstride] = zz;
-        if (act) acc.add_column(colsum, colabs);
-      }
+      const bool flag = prefix_one<T, M, CS, kTerms>(sm.As, sm.binom, n, v, c, zb, blockDim.x, thr, act, acc, ts);
       if constexpr (kMixed && !kTerms) {
-        // growth bound: the pivots of the prefix, and 2 max|z| for the pivots of
-        // the last two elimination steps (multipliers are at most 1 in size)
-        const bool flag = !(gmax <= thr) || !(2 * zmax <= thr) || !(fabs(alpha) <= static_cast<T>(FLT_MAX));
         if (act && flag) acc.drop_prefix();  // its leaves are recomputed in binary64
         const unsigned fm = __ballot_sync(kFull, act && flag);
         if (fm) {

@@ -1,0 +1,167 @@
+"""GPU parity of the batched path: every matrix of a batch against the oracle.
+
+Small batches of uneven shapes are checked against the exact enumeration of
+Eq. (1); the full 4096-matrix workload is checked against the exact values
+of tests/golden/workload_exact.txt (written by the oracle's Pfaffian closed
+form).  Binary64 results must be within 1e-12 * sum|terms|; mixed results
+within 1e-10 * sum|terms| (the target the tier router is built for).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.radic_oracle as orc
+from paper_1508_01326_gb300 import workloads as W
+from tests.conftest import ROOT
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1508_01326_gb300 import build as B
+
+    B.build()
+
+
+def R():
+    import paper_1508_01326_gb300 as R_
+
+    return R_
+
+
+def small_batch(seed, count, max_m=10, max_d=6):
+    rng = np.random.default_rng(seed)
+    mats = []
+    for _ in range(count):
+        m = int(rng.integers(1, max_m + 1))
+        n = int(m + rng.integers(-1, max_d + 1))
+        n = max(n, 1)
+        mats.append(rng.standard_normal((m, n)))
+    return mats
+
+
+def run_batch(mats, mode, dtype=np.float64, tuning=None, graph=False):
+    data, ms, ns, offs = W.pack_batch(mats, dtype)
+    A = torch.from_numpy(data).cuda()
+    plan = R().BatchPlan(list(zip(ms, ns)), offs, mode=mode, tuning=tuning)
+    if graph:
+        out = plan.new_results()
+        g = plan.graph(A, out)
+        g.launch()
+        g.launch()
+    else:
+        out = plan.radic_det_batched(A)
+    torch.cuda.synchronize()
+    res = R().parse_results(out)
+    info = plan.info()
+    plan.close()
+    return res, info
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_small_batch_matches_oracle(mode):
+    mats = small_batch(1, 60)
+    res, info = run_batch(mats, mode)
+    for a, r in zip(mats, res):
+        val, abs_sum = orc.radic_det_exact(a)
+        m, n = a.shape
+        assert r["minors"] == (math.comb(n, m) if m <= n else 0)
+        assert r["status"] == 0
+        if m > n:
+            assert r["value"] == 0.0
+            continue
+        if r["tier"] == 0:  # binary64
+            assert abs(Fraction(r["value"]) - val) <= Fraction(1e-12) * abs_sum
+        else:
+            # small matrices are routed to binary64 by the mixed plan
+            assert abs(float(Fraction(r["value"]) - val)) <= 1e-10 * float(abs_sum)
+    if mode == "fp64":
+        assert info["matrices_fp32"] == 0
+
+
+def test_small_batch_graph_equals_direct_call():
+    mats = small_batch(2, 40)
+    direct, _ = run_batch(mats, "fp64")
+    graphed, _ = run_batch(mats, "fp64", graph=True)
+    assert [r["value"] for r in direct] == [r["value"] for r in graphed]
+
+
+def test_batch_with_per_minor_tuning_and_float32_input():
+    mats = [W.uniform_matrix(s, m, n) for s, (m, n) in enumerate([(3, 9), (5, 11), (8, 13), (2, 12), (1, 7)])]
+    tuning = R().make_tuning(kind={m: "thread" for m in range(1, 9)}, task_cost={m: 2000 for m in range(1, 11)},
+                             tol=1.0)  # tol 1: every matrix in the binary32 tier
+    res, info = run_batch(mats, "mixed", dtype=np.float32, tuning=tuning)
+    assert info["matrices_fp32"] == len(mats)
+    for a, r in zip(mats, res):
+        a32 = a.astype(np.float32)
+        val, abs_sum = orc.radic_det_exact(a32)
+        assert r["tier"] == 1
+        m = a.shape[0]
+        assert abs(float(Fraction(r["value"]) - val)) <= 8 * m * 2.0 ** -24 * float(abs_sum) * 4
+
+
+def test_batch_is_deterministic():
+    mats = small_batch(3, 50, max_d=12)
+    tuning = R().make_tuning(tol=1.0)
+    a, _ = run_batch(mats, "mixed", tuning=tuning)
+    b, _ = run_batch(mats, "mixed", tuning=tuning)
+    assert [r["value"] for r in a] == [r["value"] for r in b]
+
+
+def test_batch_flagged_task_recomputed_in_binary64():
+    # Wilkinson's growth matrix in the leading 9 columns of a 9 x 16 matrix:
+    # the prefixes through those columns flag and their tasks are redone in
+    # binary64 by the second kernel.
+    m = 9
+    w = np.eye(m) - np.tril(np.ones((m, m)), -1)
+    w[:, -1] = 1.0
+    a = np.concatenate([w, W.uniform_matrix(77, m, 7)], axis=1)
+    tuning = R().make_tuning(tol=1.0)
+    res, info = run_batch([a, W.uniform_matrix(78, 4, 10)], "mixed", tuning=tuning)
+    val, abs_sum = orc.radic_det_exact(a)
+    assert res[0]["flagged"] > 0
+    assert abs(float(Fraction(res[0]["value"]) - val)) <= 8 * m * 2.0 ** -24 * float(abs_sum)
+
+
+def _golden(name):
+    vals = {}
+    with open(os.path.join(ROOT, "tests", "golden", "workload_exact.txt")) as f:
+        for line in f:
+            p = line.split()
+            if p and p[0] == name:
+                vals[int(p[1])] = float(p[4])
+    return [vals[i] for i in range(len(vals))]
+
+
+@pytest.mark.parametrize("mode,dtype,golden,tol", [
+    ("mixed", np.float32, "batched_4096_f32", 1e-10),
+    ("mixed", np.float64, "batched_4096_f64", 1e-10),
+    ("mixed", np.float32, "batched_4096_f32", 1e-8),
+    ("fp64", np.float64, "batched_4096_f64", 1e-12),
+])
+def test_full_batched_4096(mode, dtype, golden, tol):
+    mats = W.batched_4096()
+    want = _golden(golden)
+    tuning = R().make_tuning(tol=tol) if mode == "mixed" else None
+    res, info = run_batch(mats, mode, dtype=dtype, tuning=tuning)
+    worst = 0.0
+    for r, w in zip(res, want):
+        assert r["status"] == 0
+        err = abs(r["value"] - w) / r["abs_sum"]
+        worst = max(worst, err)
+    assert worst <= tol, worst
+    assert info["matrices_fp32"] + info["matrices_fp64"] == len(mats)
+    if mode == "mixed":
+        # the router sends a matrix to binary32 only when 2.5e-6 / sqrt(C) meets tol
+        want32 = sum(1 for a in mats if a.shape[0] <= a.shape[1]
+                     and 2.5e-6 / math.sqrt(math.comb(a.shape[1], a.shape[0])) <= tol)
+        assert info["matrices_fp32"] == want32
+        if tol >= 1e-8:
+            assert want32 > 0
