@@ -246,6 +246,24 @@ int radic_batch_graph_create(const radic_batch_plan* plan, const void* A, int dt
 int radic_batch_graph_launch(radic_batch_graph* graph, void* stream);
 int radic_batch_graph_destroy(radic_batch_graph* graph);
 
+/* ---- differentiation ------------------------------------------------------ */
+
+/* Workspace bytes of radic_det_backward (0 for unsupported shapes). */
+size_t radic_backward_workspace_bytes(int batch, int m, int n);
+
+/* Gradient of sum_b grad_out[b] * det_R(A_b) with respect to every A_b, in
+ * binary64.  d det_R / d A[:, J] = (-1)^(r+s) adj(A[:, J])^T for every
+ * column sequence J of Eq. (1): each minor's signed cofactors
+ * det(M) inv(M)^T (from its partial-pivot LU) are scatter-added into the
+ * gradient columns J.  A: device, batch matrices m x n, row-major with
+ * leading dimension lda, matrix b at A + b * stride.  grad_out: device,
+ * batch values.  grad_A: device, same layout as A, overwritten.  1 <= m <= 8
+ * (m > n gives a zero gradient).  Errors: RADIC_EINVAL, RADIC_EUNSUPPORTED
+ * (m > 8), RADIC_EWORKSPACE, RADIC_ECUDA. */
+int radic_det_backward(const double* A, int batch, int m, int n, int64_t lda, int64_t stride,
+                       const double* grad_out, double* grad_A, void* workspace, size_t workspace_bytes,
+                       void* stream);
+
 /* ---- allocation-free variant ------------------------------------------- */
 
 /* Capacity in bytes of the library's own static scratch array. */

@@ -7,6 +7,7 @@ include/radic.h.  This package is the thin Python binding; the shared
 library is loaded on first use and its absence is an error.
 """
 from ._lib import RadicError, make_options  # noqa: F401
+from .autograd import RadicDet, radic_det_autograd, radic_det_backward  # noqa: F401
 from .api import (  # noqa: F401
     BatchGraph,
     BatchPlan,

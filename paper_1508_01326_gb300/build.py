@@ -26,6 +26,7 @@ SOURCES = [
     "radic_modp.cu",
     "radic_noalloc.cu",
     "radic_batched.cu",
+    "radic_backward.cu",
 ]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,0 +1,323 @@
+// Gradient of Radic's determinant with respect to the matrix entries.
+//
+// d det_R / d A[:, J] = sign(J) * adj(A[:, J])^T, the cofactor matrix of each
+// minor, so the gradient of det_R(A) scatter-adds every minor's signed
+// cofactors into the columns J of the gradient.  Per minor (one thread, in
+// registers): partial-pivot LU P M = L U with the row order tracked in
+// idx[], B = U^{-1} L^{-1} = M^{-1} P^T, and cofactor(idx[s], j) =
+// det(M) * B[j][s].  A block owns one run of dictionary ranks of one matrix
+// and adds its cofactors into a shared-memory copy of that matrix's gradient
+// (shared-memory atomics); blocks write their tiles to per-block slots and a
+// second kernel adds a matrix's slots in block order and scales by the
+// incoming gradient.  Binary64 throughout.  A minor with an exactly zero
+// pivot (singular) takes a slow path that forms its cofactors from
+// (m-1) x (m-1) determinants.
+#include <algorithm>
+
+#include "radic_fp_kernels.cuh"
+
+namespace radic {
+namespace {
+
+constexpr int kBwdThreads = 128;
+constexpr int kBwdMaxM = 8;
+
+struct BwdArgs {
+  const double* A;
+  long long lda, stride;  // row stride, matrix stride (elements)
+  int batch, m, n;
+  int chunks;             // blocks per matrix
+  unsigned long long total;
+  double* slots;          // batch x chunks x m x n
+};
+
+// Full partial-pivot LU with multipliers stored below the diagonal; idx[s] is
+// the original row in slot s.  Returns det(M) and whether a pivot was zero.
+template <int M>
+__device__ __forceinline__ double lu_full(double (&a)[M][M], int (&idx)[M], bool& zero_pivot) {
+  double det = 1.0;
+  bool neg = false;
+  zero_pivot = false;
+#pragma unroll
+  for (int i = 0; i < M; ++i) idx[i] = i;
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+#pragma unroll
+    for (int i = k + 1; i < M; ++i) {
+      const bool sw = mag_key(a[i][k]) > mag_key(a[k][k]);
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        const double x = a[k][j], y = a[i][j];
+        a[k][j] = sw ? y : x;
+        a[i][j] = sw ? x : y;
+      }
+      const int ik = idx[k], ii = idx[i];
+      idx[k] = sw ? ii : ik;
+      idx[i] = sw ? ik : ii;
+      neg ^= sw;
+    }
+    const double piv = a[k][k];
+    zero_pivot |= (piv == 0.0);
+    det *= piv;
+    const double r = rcp_f64(piv);
+#pragma unroll
+    for (int i = k + 1; i < M; ++i) {
+      const double l = a[i][k] * r;
+      a[i][k] = l;
+#pragma unroll
+      for (int j = k + 1; j < M; ++j) a[i][j] = fma(-l, a[k][j], a[i][j]);
+    }
+  }
+  return neg ? -det : det;
+}
+
+// X = U^{-1} L^{-1} from the packed factors in a (L unit lower, U upper):
+// first X = L^{-1} column by column (forward substitution), then, in place,
+// X = U^{-1} X (back substitution).
+template <int M>
+__device__ __forceinline__ void inverse_factors(const double (&a)[M][M], double (&X)[M][M]) {
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      if (i < j) X[i][j] = 0.0;
+      else if (i == j) X[i][j] = 1.0;
+      else {
+        double s = -a[i][j];
+#pragma unroll
+        for (int k = j + 1; k < i; ++k) s = fma(-a[i][k], X[k][j], s);
+        X[i][j] = s;
+      }
+    }
+  }
+  double rinv[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) rinv[i] = rcp_f64(a[i][i]);
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+#pragma unroll
+    for (int i = M - 1; i >= 0; --i) {
+      double s = X[i][j];
+#pragma unroll
+      for (int k = i + 1; k < M; ++k) s = fma(-a[i][k], X[k][j], s);
+      X[i][j] = s * rinv[i];
+    }
+  }
+}
+
+// Slow path for a singular minor: cofactor(i, j) = (-1)^(i+j) det of M
+// without row i and column j, by LU of each (m-1) x (m-1) submatrix.
+template <int M>
+__device__ __noinline__ void cofactors_slow(const double* As, int cs, const int (&c)[M], double (&cof)[M][M]) {
+  for (int i = 0; i < M; ++i) {
+    for (int j = 0; j < M; ++j) {
+      double sub[M > 1 ? M - 1 : 1][M > 1 ? M - 1 : 1];
+      int rr = 0;
+      for (int r = 0; r < M; ++r) {
+        if (r == i) continue;
+        int cc = 0;
+        for (int q = 0; q < M; ++q) {
+          if (q == j) continue;
+          sub[rr][cc++] = As[c[q] * cs + r];
+        }
+        ++rr;
+      }
+      double det = 1.0;
+      bool neg = false;
+      const int S = M - 1;
+      for (int k = 0; k < S; ++k) {
+        int p = k;
+        for (int r = k + 1; r < S; ++r)
+          if (fabs(sub[r][k]) > fabs(sub[p][k])) p = r;
+        if (p != k) {
+          for (int q = 0; q < S; ++q) {
+            const double t = sub[k][q];
+            sub[k][q] = sub[p][q];
+            sub[p][q] = t;
+          }
+          neg = !neg;
+        }
+        const double piv = sub[k][k];
+        det *= piv;
+        if (piv == 0.0) break;
+        for (int r = k + 1; r < S; ++r) {
+          const double l = sub[r][k] / piv;
+          for (int q = k + 1; q < S; ++q) sub[r][q] -= l * sub[k][q];
+        }
+      }
+      if (neg) det = -det;
+      cof[i][j] = ((i + j) & 1) ? -det : det;
+    }
+  }
+}
+
+template <int M>
+__global__ void __launch_bounds__(kBwdThreads) k_backward(BwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int CS = ColStride<double, M>::value;
+  const int n = a.n;
+  const int b = blockIdx.y;
+  const int chunk = blockIdx.x;
+  uint64_t* binom = reinterpret_cast<uint64_t*>(smem_raw);
+  size_t off = ((size_t)(n + 1) * (M + 1) * 8 + 15) / 16 * 16;
+  double* As = reinterpret_cast<double*>(smem_raw + off);
+  off += ((size_t)n * CS * 8 + 15) / 16 * 16;
+  double* G = reinterpret_cast<double*>(smem_raw + off);  // M x n gradient tile
+  build_binom(binom, n, M);
+  const double* Ab = a.A + (long long)b * a.stride;
+  for (int idx = threadIdx.x; idx < n * CS; idx += blockDim.x) {
+    const int j = idx / CS, i = idx - j * CS;
+    As[idx] = (i < M) ? Ab[(long long)i * a.lda + j] : 0.0;
+  }
+  for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) G[idx] = 0.0;
+  __syncthreads();
+
+  // this block's run of ranks, split evenly over its threads
+  const unsigned long long per_chunk = (a.total + a.chunks - 1) / a.chunks;
+  const unsigned long long c0 = (unsigned long long)chunk * per_chunk;
+  const unsigned long long c1 = min(c0 + per_chunk, a.total);
+  if (c0 < c1) {
+    const unsigned long long per_thread = (c1 - c0 + blockDim.x - 1) / blockDim.x;
+    const unsigned long long q0 = c0 + threadIdx.x * per_thread;
+    const unsigned long long q1 = min(q0 + per_thread, c1);
+    if (q0 < q1) {
+      int c[M];
+      unrank<M>(q0, n, binom, M + 1, c);
+      for (unsigned long long q = q0; q < q1; ++q) {
+        double mm[M][M];
+        gather<double, M, CS>(As, c, mm);
+        int idx[M];
+        bool zp;
+        const double det = lu_full<M>(mm, idx, zp);
+        const double sgn = sign_negative<M>(c) ? -1.0 : 1.0;
+        if (!zp) {
+          double B[M][M];
+          inverse_factors<M>(mm, B);
+          const double s = sgn * det;
+#pragma unroll
+          for (int sl = 0; sl < M; ++sl) {
+            double* grow = G + idx[sl] * n;
+#pragma unroll
+            for (int j = 0; j < M; ++j) atomicAdd(grow + c[j], s * B[j][sl]);
+          }
+        } else {
+          double cof[M][M];
+          cofactors_slow<M>(As, CS, c, cof);
+          for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) atomicAdd(G + i * n + c[j], sgn * cof[i][j]);
+        }
+        if (q + 1 < q1) successor<M>(c, n);
+      }
+    }
+  }
+  __syncthreads();
+  double* slot = a.slots + ((size_t)b * a.chunks + chunk) * (size_t)M * n;
+  for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) slot[idx] = G[idx];
+}
+
+// grad_A[b] = grad_out[b] * sum over chunks (in order) of the tiles.
+__global__ void k_backward_reduce(const double* slots, int batch, int m, int n, int chunks, const double* grad_out,
+                                  double* grad, long long lda, long long stride) {
+  const long long total = (long long)batch * m * n;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / (m * n));
+    const int e = (int)(t - (long long)b * m * n);
+    const int i = e / n, j = e - i * n;
+    double s = 0.0;
+    for (int k = 0; k < chunks; ++k) s += slots[((size_t)b * chunks + k) * (size_t)m * n + e];
+    grad[(long long)b * stride + (long long)i * lda + j] = s * grad_out[b];
+  }
+}
+
+const void* bwd_kernel(int m) {
+  switch (m) {
+    case 1: return reinterpret_cast<const void*>(&k_backward<1>);
+    case 2: return reinterpret_cast<const void*>(&k_backward<2>);
+    case 3: return reinterpret_cast<const void*>(&k_backward<3>);
+    case 4: return reinterpret_cast<const void*>(&k_backward<4>);
+    case 5: return reinterpret_cast<const void*>(&k_backward<5>);
+    case 6: return reinterpret_cast<const void*>(&k_backward<6>);
+    case 7: return reinterpret_cast<const void*>(&k_backward<7>);
+    case 8: return reinterpret_cast<const void*>(&k_backward<8>);
+    default: return nullptr;
+  }
+}
+
+int bwd_chunks(int batch, unsigned long long total) {
+  const int sms = device_sm_count();
+  const long long want = (long long)(sms > 0 ? sms : 1) * 16;  // about 16 blocks per SM in all
+  long long ch = (want + batch - 1) / batch;
+  const long long by_work = (long long)((total + 4095) / 4096);  // at least ~32 minors per thread
+  if (ch > by_work) ch = by_work;
+  if (ch < 1) ch = 1;
+  if (ch > 65535) ch = 65535;
+  return (int)ch;
+}
+
+size_t bwd_smem(int m, int n) {
+  const int cs = ((m + 1) / 2) * 2;
+  size_t off = ((size_t)(n + 1) * (m + 1) * 8 + 15) / 16 * 16;
+  off += ((size_t)n * cs * 8 + 15) / 16 * 16;
+  off += (size_t)m * n * 8;
+  return off;
+}
+
+}  // namespace
+}  // namespace radic
+
+using namespace radic;
+
+extern "C" {
+
+size_t radic_backward_workspace_bytes(int batch, int m, int n) {
+  if (batch < 1 || m < 1 || m > kBwdMaxM || n < 1 || n > kMaxN) return 0;
+  const unsigned long long total = (m <= n) ? binom_host(n, m) : 0ull;
+  const int chunks = bwd_chunks(batch, total);
+  return align_up((size_t)batch * chunks * m * n * sizeof(double), 256) + 256;
+}
+
+int radic_det_backward(const double* A, int batch, int m, int n, int64_t lda, int64_t stride, const double* grad_out,
+                       double* grad_A, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!A || !grad_out || !grad_A || batch < 1 || m < 1 || n < 1 || n > kMaxN || lda < n || stride < (int64_t)m * lda)
+    return RADIC_EINVAL;
+  if (m > kBwdMaxM) return RADIC_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (m > n) {  // det_R is identically zero: zero gradient
+    for (int b = 0; b < batch; ++b)
+      if (cudaMemset2DAsync(grad_A + (long long)b * stride, lda * sizeof(double), 0, n * sizeof(double), m, s) !=
+          cudaSuccess)
+        return RADIC_ECUDA;
+    return RADIC_OK;
+  }
+  const size_t need = radic_backward_workspace_bytes(batch, m, n);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u) || workspace_bytes < need) return RADIC_EWORKSPACE;
+  BwdArgs a;
+  a.A = A;
+  a.lda = lda;
+  a.stride = stride;
+  a.batch = batch;
+  a.m = m;
+  a.n = n;
+  a.total = binom_host(n, m);
+  a.chunks = bwd_chunks(batch, a.total);
+  a.slots = static_cast<double*>(workspace);
+  const void* k = bwd_kernel(m);
+  const size_t smem = bwd_smem(m, n);
+  if (!allow_smem(k, smem)) return RADIC_EUNSUPPORTED;
+  void* params[] = {&a};
+  if (cudaLaunchKernel(k, dim3(a.chunks, batch), dim3(kBwdThreads), params, smem, s) != cudaSuccess)
+    return RADIC_ECUDA;
+  const long long total = (long long)batch * m * n;
+  const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 65535);
+  const double* slots = a.slots;
+  int bb = batch, mm = m, nn = n, ch = a.chunks;
+  long long l = lda, st = stride;
+  void* rparams[] = {&slots, &bb, &mm, &nn, &ch, &grad_out, &grad_A, &l, &st};
+  if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_backward_reduce), dim3(blocks), dim3(256), rparams, 0, s) !=
+      cudaSuccess)
+    return RADIC_ECUDA;
+  return RADIC_OK;
+}
+
+}  // extern "C"
