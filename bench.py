@@ -191,6 +191,102 @@ def prefix_flops(m: int, n: int) -> int:
     return total
 
 
+def golden_list(name: str) -> list:
+    vals = {}
+    with open(os.path.join(ROOT, "tests", "golden", "workload_exact.txt")) as f:
+        for line in f:
+            p = line.split()
+            if p and p[0] == name:
+                vals[int(p[1])] = (p[2], p[3], float(p[4]))
+    return [vals[i] for i in range(len(vals))]
+
+
+def measure_configs(R, W, torch) -> dict:
+    """The other benchmark configurations (untimed by the headline): exact 3x12
+    latency, exact 12x40 throughput, the 4096-matrix batch (mixed with
+    autotuned tasks, binary64 batched, and one plain binary64 launch per
+    matrix), and forward plus backward of the 256 x 6 x 28 batch."""
+    import numpy as np
+
+    from paper_1508_01326_gb300 import autotune
+
+    stream = torch.cuda.current_stream()
+
+    def ev_time(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    # exact 3 x 12 int32: latency of one call
+    a = torch.from_numpy(W.int_3x12()).cuda()
+    res = R.new_result()
+    ws = torch.empty(R.radic_workspace_bytes(3, 12, "exact"), dtype=torch.uint8, device="cuda")
+    ms = ev_time(lambda: R.radic_det(a, mode="exact", out=res, workspace=ws), reps=50)
+    want = int(golden_list("int_3x12")[0][0])
+    out["int_3x12_exact"] = {"us_per_call": ms * 1e3, "exact_ok": R.parse_result(res)["exact"] == want}
+    # exact 12 x 40 int8: full size
+    a = torch.from_numpy(W.int8_12x40()).cuda()
+    ws = torch.empty(R.radic_workspace_bytes(12, 40, "exact"), dtype=torch.uint8, device="cuda")
+    ms = ev_time(lambda: R.radic_det(a, mode="exact", out=res, workspace=ws))
+    r = R.parse_result(res)
+    out["int8_12x40_exact"] = {"value": r["minors"] / (ms / 1e3), "unit": UNIT, "ms": ms, "n_primes": r["n_primes"],
+                               "exact_ok": r["exact"] == int(golden_list("int8_12x40")[0][0])}
+    # batched 4096
+    mats = W.batched_4096()
+    minors = sum(math.comb(x.shape[1], x.shape[0]) for x in mats if x.shape[0] <= x.shape[1])
+    gold = [g[2] for g in golden_list("batched_4096_f64")]
+    data, ms_, ns_, offs = W.pack_batch(mats, np.float64)
+    A = torch.from_numpy(data).cuda()
+    tuning, table = autotune.autotune(mats, mode="mixed", tol=1e-10)
+    batched = {"minors": minors, "autotune": {m: v["kind"] + "/" + str(int(v["task_cost"])) for m, v in table.items()}}
+    for mode, tun in [("mixed", tuning), ("fp64", None)]:
+        plan = R.BatchPlan(list(zip(ms_, ns_)), offs, mode=mode, tuning=tun)
+        o = plan.new_results()
+        g = plan.graph(A, o)
+        ms = ev_time(g.launch, reps=3)
+        rs = R.parse_results(o)
+        worst = max(abs(x["value"] - w) / x["abs_sum"] for x, w in zip(rs, gold) if x["abs_sum"] > 0)
+        batched[mode] = {"value": minors / (ms / 1e3), "unit": UNIT, "ms": ms, "rel_err_max": worst,
+                         "routing": plan.info()}
+        plan.close()
+    # one plain binary64 per-minor launch per matrix (thread mapping up to m = 8, warp groups above)
+    dev = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in mats]
+    outs = R.new_result().new_empty((len(mats), 16))
+    wss = [torch.empty(max(R.radic_workspace_bytes(x.shape[0], x.shape[1], "fp64",
+                                                   dict(mapping="thread" if x.shape[0] <= 8 else "group")), 256),
+                       dtype=torch.uint8, device="cuda") for x in mats]
+
+    def per_matrix():
+        for i, x in enumerate(dev):
+            R.radic_det(x, mode="fp64", options=dict(mapping="thread" if x.shape[0] <= 8 else "group"),
+                        out=outs[i], workspace=wss[i])
+
+    ms = ev_time(per_matrix)
+    rs = R.parse_results(outs)
+    worst = max(abs(x["value"] - w) / x["abs_sum"] for x, w in zip(rs, gold) if x["abs_sum"] > 0)
+    batched["per_matrix_plain_fp64"] = {"value": minors / (ms / 1e3), "unit": UNIT, "ms": ms, "rel_err_max": worst,
+                                        "launches": 2 * len(mats)}
+    batched["speedup_mixed_over_per_matrix_fp64"] = batched["mixed"]["value"] / batched["per_matrix_plain_fp64"]["value"]
+    out["batched_4096"] = batched
+    # differentiation 256 x 6 x 28: forward (batched binary64) and backward
+    D = torch.from_numpy(W.diff_256x6x28()).cuda()
+    g_out = torch.ones(256, dtype=torch.float64, device="cuda")
+    R.RadicDet.apply(D)
+    fwd = ev_time(lambda: R.RadicDet.apply(D), reps=3)
+    bwd = ev_time(lambda: R.radic_det_backward(D, g_out), reps=3)
+    mn = 256 * math.comb(28, 6)
+    out["diff_256x6x28"] = {"forward_ms": fwd, "backward_ms": bwd, "backward_minors_per_s": mn / (bwd / 1e3),
+                            "forward_minors_per_s": mn / (fwd / 1e3)}
+    return out
+
+
 def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     import ctypes
 
@@ -320,6 +416,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     flops = prefix_flops(M, N)
     achieved = flops / (kern_mean_ms / 1e3) / 1e12
 
+    configs = measure_configs(R, W, torch) if (rank == 0 and not args.headline_only) else None
+
     cpu = None
     if pool is not None:
         sample = 160_000
@@ -346,6 +444,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
                          "flop_per_launch": flops,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (derived)"},
             "clocks": clocks,
+            "configs": configs,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": A.numel() * 8,
                     "d2h_bytes_per_step": 16 * 8},
@@ -364,6 +463,7 @@ def main() -> None:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--settle-seconds", type=float, default=1.0)
+    ap.add_argument("--headline-only", action="store_true", help="skip the other configurations")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
