@@ -172,6 +172,18 @@ def run_reference(args, rank: int, world: int) -> None:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def max_over_ranks(total_ms: float, device=None) -> float:
+    """Slowest rank's timed total (all ranks call it; a no-op without a process group)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_ms
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def prefix_flops(m: int, n: int) -> int:
     """Algorithmic flops (2 per FMA, 1 per add or multiply) of the prefix-sharing path.
 
@@ -371,11 +383,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         torch.distributed.barrier()
     clocks = sampler.stop()
 
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), device="cuda")
     ms_per_step = total_ms / args.steps
     value = world * MINORS / (ms_per_step / 1e3)
     res_head = head.result()
