@@ -257,7 +257,8 @@ def measure_configs(R, W, torch) -> dict:
     data, ms_, ns_, offs = W.pack_batch(mats, np.float64)
     A = torch.from_numpy(data).cuda()
     tuning, table = autotune.autotune(mats, mode="mixed", tol=1e-10)
-    batched = {"minors": minors, "autotune": {m: v["kind"] + "/" + str(int(v["task_cost"])) for m, v in table.items()}}
+    batched = {"minors": minors, "autotune": {m: v["kind"] + (str(v["depth"]) if v.get("depth") else "") + "/" + str(int(v["task_cost"]))
+                                               for m, v in table.items()}}
     for mode, tun in [("mixed", tuning), ("fp64", None)]:
         plan = R.BatchPlan(list(zip(ms_, ns_)), offs, mode=mode, tuning=tun)
         o = plan.new_results()

@@ -79,10 +79,11 @@ enum { RADIC_MODE_FP64 = 0, RADIC_MODE_MIXED = 1, RADIC_MODE_EXACT = 2 };
  *  GROUP  -- a group of `group_width` lanes of one warp (16 or 32) factors
  *            one minor, one row per lane, pivot rows shared by warp shuffles.
  *  PREFIX -- FP64 and MIXED, 3 <= m <= 10 (FP64) or 12 (MIXED): one thread
- *            factors the m x (m-2) matrix of an ascending (m-2)-column
- *            prefix once with partial pivoting; every minor of that
- *            prefix's lexicographic subtree then costs one 2 x 2
- *            determinant of Schur-complement entries.  Same pivots and
+ *            factors the m x (m-D) matrix of an ascending (m-D)-column
+ *            prefix once with partial pivoting (D = 2 or 3, the prefix
+ *            depth); every minor of that prefix's lexicographic subtree
+ *            then costs one D x D determinant of Schur-complement entries
+ *            (for D = 3 a scalar triple product).  Same pivots and
  *            elimination steps as per-minor LU, shared by the subtree.
  *  AUTO   -- FP64/MIXED: PREFIX when 3 <= m within its limit, else THREAD
  *            when m <= 8, else GROUP.  EXACT: THREAD when m <= 12, else
@@ -102,7 +103,11 @@ typedef struct radic_options {
   void* kernel_events;      /* optional: two cudaEvent_t recorded on the
                                stream right before and right after the main
                                per-minor kernel (profiling hook)             */
-  int64_t reserved[3];
+  int32_t prefix_depth;     /* PREFIX mapping: trailing columns per leaf, 2 or
+                               3 (0: 3 when m >= 6 and n - m <= 3m (MIXED)
+                               or 2.5m (FP64), else 2)                       */
+  int32_t pad;
+  int64_t reserved[2];
 } radic_options;
 
 /* Device-resident result of one determinant (16 eight-byte words). */
@@ -199,6 +204,7 @@ typedef struct radic_batch_tuning {
   double tol;              /* MIXED: target |err| / sum|terms| (default 1e-10) */
   double growth_threshold; /* MIXED: growth flag threshold (default 64)         */
   int32_t blocks_per_sm;   /* cap on resident blocks per SM (0: occupancy)     */
+  int32_t prefix_depth[RADIC_MAX_M + 1]; /* 2, 3, or 0 for the default rule */
   int32_t reserved[7];
 } radic_batch_tuning;
 
@@ -210,8 +216,8 @@ typedef struct radic_batch_tuning {
  * expected binary32 error, 2.5e-6 / sqrt(C(n,m)) relative to sum|terms|
  * (an envelope of measured errors on random inputs), meets tuning->tol, and
  * to binary64 otherwise; the result's `tier` field tells which.  The work of every matrix is cut into warp tasks
- * (runs of prefixes or of dictionary ranks, per the tuning) for two
- * persistent kernels with atomic work queues, one per tier, followed by a
+ * (runs of prefixes or of dictionary ranks, per the tuning) for persistent
+ * kernels with atomic work queues, one per tier and m, followed by a
  * per-matrix fixed-order reduction.  Limits: 1 <= m <= 10, n <= 64.
  * The plan is host memory owned by the library until
  * radic_batch_plan_destroy.  Errors: RADIC_EINVAL, RADIC_EUNSUPPORTED

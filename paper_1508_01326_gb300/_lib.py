@@ -28,7 +28,9 @@ class RadicOptions(ctypes.Structure):
         ("flag_capacity", ctypes.c_int32),
         ("growth_threshold", ctypes.c_double),
         ("kernel_events", ctypes.c_void_p),
-        ("reserved", ctypes.c_int64 * 3),
+        ("prefix_depth", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("reserved", ctypes.c_int64 * 2),
     ]
 
 
@@ -42,6 +44,7 @@ class RadicBatchTuning(ctypes.Structure):
         ("tol", ctypes.c_double),
         ("growth_threshold", ctypes.c_double),
         ("blocks_per_sm", ctypes.c_int32),
+        ("prefix_depth", ctypes.c_int32 * (RADIC_MAX_M + 1)),
         ("reserved", ctypes.c_int32 * 7),
     ]
 
@@ -117,7 +120,7 @@ def check(fn: str, code: int) -> None:
 
 def make_options(mapping: str | int = 0, group_width: int = 0, ranks_per_task: int = 0,
                  threads_per_block: int = 0, blocks: int = 0, flag_capacity: int = 0,
-                 growth_threshold: float = 0.0, kernel_events: int = 0) -> RadicOptions:
+                 growth_threshold: float = 0.0, kernel_events: int = 0, prefix_depth: int = 0) -> RadicOptions:
     o = RadicOptions()
     o.mapping = MAPPINGS[mapping] if isinstance(mapping, str) else int(mapping)
     o.group_width = group_width
@@ -127,4 +130,5 @@ def make_options(mapping: str | int = 0, group_width: int = 0, ranks_per_task: i
     o.flag_capacity = flag_capacity
     o.growth_threshold = growth_threshold
     o.kernel_events = kernel_events or None
+    o.prefix_depth = prefix_depth
     return o

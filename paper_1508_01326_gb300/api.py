@@ -154,9 +154,13 @@ def det(A, mode="fp64", options=None, stream=None) -> dict:
 # ---------------------------------------------------------------------------
 
 
-def make_tuning(kind=None, task_cost=None, tol=0.0, growth_threshold=0.0, blocks_per_sm=0) -> "L.RadicBatchTuning":
-    """Batched-path tuning: `kind` and `task_cost` map m to a mapping name and a task size."""
+def make_tuning(kind=None, task_cost=None, tol=0.0, growth_threshold=0.0, blocks_per_sm=0,
+                prefix_depth=None) -> "L.RadicBatchTuning":
+    """Batched-path tuning: `kind`, `task_cost` and `prefix_depth` map m to a mapping name, a task size
+    and a prefix depth (2 or 3)."""
     t = L.RadicBatchTuning()
+    for m, d in (prefix_depth or {}).items():
+        t.prefix_depth[int(m)] = int(d)
     for m, k in (kind or {}).items():
         t.kind[int(m)] = L.MAPPINGS[k] if isinstance(k, str) else int(k)
     for m, c in (task_cost or {}).items():

@@ -1,8 +1,8 @@
-"""Autotuner of the batched path: per m, the minor-to-warp mapping and task size.
+"""Autotuner of the batched path: per m, the minor-to-warp mapping, prefix depth and task size.
 
 For every m present in a batch it times the batched call on the sub-batch of
-matrices with that m under each candidate (mapping, task cost) and keeps the
-fastest.  Results are cached in a JSON file keyed by GPU name, mode, target
+matrices with that m under each candidate (mapping, prefix depth, task cost)
+and keeps the fastest.  Results are cached in a JSON file keyed by GPU name, mode, target
 tolerance and input dtype (default ~/.cache/radic_gb300/autotune.json, or the
 path in RADIC_AUTOTUNE_CACHE).  Host logic only; timing uses CUDA events
 around the library's own launches.
@@ -61,22 +61,25 @@ def _time_plan(mats: List[np.ndarray], mode: str, dtype, tuning, reps: int = 3) 
     return best
 
 
-def candidates(m: int, tier_fp32: bool, costs: Iterable[float]) -> List[Tuple[str, float]]:
+def candidates(m: int, tier_fp32: bool, costs: Iterable[float]) -> List[Tuple[str, int, float]]:
+    """(mapping, prefix depth (0 for the per-minor mapping), task cost) triples to time for this m."""
     kinds = []
     if m >= 3:
-        kinds.append("prefix")
+        kinds.append(("prefix", 2))
+    if m >= 4:
+        kinds.append(("prefix", 3))
     if m <= 2 or (tier_fp32 and m <= 8):
-        kinds.append("thread")
-    return [(k, c) for k in kinds for c in costs]
+        kinds.append(("thread", 0))
+    return [(k, d, c) for k, d in kinds for c in costs]
 
 
 def autotune(mats: List[np.ndarray], mode: str = "mixed", tol: float = 1e-10, dtype=np.float64,
              costs: Iterable[float] = DEFAULT_COSTS, path: Optional[str] = None, force: bool = False,
              reps: int = 3) -> Tuple["api.L.RadicBatchTuning", dict]:
-    """Returns (tuning struct, table {m: {"kind", "task_cost", "ms"}}) for this batch."""
+    """Returns (tuning struct, table {m: {"kind", "depth", "task_cost", "ms"}}) for this batch."""
     path = path or cache_path()
     dev = torch.cuda.get_device_name()
-    key = f"{dev}|{mode}|{tol:g}|{np.dtype(dtype).name}"
+    key = f"{dev}|{mode}|{tol:g}|{np.dtype(dtype).name}|v2"
     cache = _load(path)
     table: Dict[str, dict] = dict(cache.get(key, {}))
     by_m: Dict[int, List[np.ndarray]] = {}
@@ -93,16 +96,17 @@ def autotune(mats: List[np.ndarray], mode: str = "mixed", tol: float = 1e-10, dt
             a.shape[0] <= a.shape[1] and 2.5e-6 / math.sqrt(math.comb(a.shape[1], a.shape[0])) <= tol
             for a in group)
         best = None
-        for kind, cost in candidates(m, tier_fp32, costs):
-            tun = api.make_tuning(kind={m: kind}, task_cost={m: cost}, tol=tol)
+        for kind, depth, cost in candidates(m, tier_fp32, costs):
+            tun = api.make_tuning(kind={m: kind}, task_cost={m: cost}, prefix_depth={m: depth}, tol=tol)
             ms = _time_plan(group, mode, dtype, tun, reps)
             if best is None or ms < best["ms"]:
-                best = {"kind": kind, "task_cost": cost, "ms": ms}
+                best = {"kind": kind, "depth": depth, "task_cost": cost, "ms": ms}
         table[str(m)] = best
         changed = True
     if changed:
         cache[key] = table
         _store(path, cache)
     tun = api.make_tuning(kind={int(m): v["kind"] for m, v in table.items()},
-                          task_cost={int(m): v["task_cost"] for m, v in table.items()}, tol=tol)
+                          task_cost={int(m): v["task_cost"] for m, v in table.items()},
+                          prefix_depth={int(m): v.get("depth", 0) for m, v in table.items()}, tol=tol)
     return tun, table

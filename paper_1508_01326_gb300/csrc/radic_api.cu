@@ -49,21 +49,17 @@ size_t smem_of(const SinglePlan& p) {
 
 void layout_workspace(SinglePlan& pl);
 
-// Prefix mapping: groups v (last prefix column) with C(v, m-3) prefixes each;
-// runs per lane sized so that warp tasks cost about the same.  Cost model per
-// prefix: factorisation ~ m (m-2)^2, each candidate column ~ 3m, each leaf 6.
 int plan_prefix(SinglePlan pl, const radic_options& d, int sms, int per_sm, unsigned long long units,
                 SinglePlan* out) {
-  const int m = pl.m, n = pl.n, P = m - 2;
+  const int m = pl.m, n = pl.n, D = pl.depth, P = m - D;
   PrefixTable& t = pl.ptab;
   t.v_lo = P - 1;
-  t.v_hi = n - 3;
+  t.v_hi = n - 1 - D;
   double total_cost = 0.0;
   double cost[kMaxN] = {0};
   for (int v = t.v_lo; v <= t.v_hi; ++v) {
-    const int k = n - 1 - v;
     t.count[v] = binom_host(v, P - 1);
-    cost[v] = (double)m * P * P + 3.0 * m * k + 6.0 * k * (k - 1) / 2.0;
+    cost[v] = prefix_cost(m, D, n - 1 - v);
     total_cost += cost[v] * (double)t.count[v];
   }
   const unsigned long long lanes = (unsigned long long)sms * per_sm * pl.threads;
@@ -80,6 +76,7 @@ int plan_prefix(SinglePlan pl, const radic_options& d, int sms, int per_sm, unsi
     start += (t.count[v] + 32 * run - 1) / (32 * run);
   }
   if (t.v_hi + 1 < kMaxN) t.task_start[t.v_hi + 1] = start;
+  if (t.v_hi < t.v_lo) start = 0;
   t.total_tasks = start;
   const unsigned long long warps_per_block = pl.threads / 32;
   const unsigned long long need = (start + warps_per_block - 1) / warps_per_block;
@@ -123,6 +120,11 @@ int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long
   if (mapping == RADIC_MAP_THREAD && m > thread_limit(mode)) return RADIC_EUNSUPPORTED;
   if (mapping == RADIC_MAP_PREFIX && (m < 3 || m > prefix_limit || m > n)) return RADIC_EUNSUPPORTED;
   pl.mapping = mapping;
+  if (mapping == RADIC_MAP_PREFIX) {
+    if (d.prefix_depth != 0 && d.prefix_depth != 2 && d.prefix_depth != 3) return RADIC_EINVAL;
+    if (d.prefix_depth == 3 && m < 4) return RADIC_EUNSUPPORTED;
+    pl.depth = d.prefix_depth ? d.prefix_depth : prefix_auto_depth(m, n, mode == RADIC_MODE_FP64 ? 8 : 4);
+  }
   if (mapping == RADIC_MAP_GROUP) {
     const int gw = d.group_width ? d.group_width : (m <= 16 ? 16 : 32);
     if ((gw != 16 && gw != 32) || gw < m) return RADIC_EINVAL;
@@ -354,7 +356,7 @@ int radic_det(const void* A, int m, int n, int64_t lda, int dtype, int mode, con
   a.tasks = p.tasks;
   a.growth = p.growth;
   a.flag_cap = p.flag_cap;
-  a.flag_prefix = (p.mapping == RADIC_MAP_PREFIX) ? m - 2 : 0;
+  a.flag_prefix = (p.mapping == RADIC_MAP_PREFIX) ? m - p.depth : 0;
   a.n_warps = p.blocks * p.threads / 32;
   a.hdr = reinterpret_cast<WsHeader*>(ws);
   a.partials = reinterpret_cast<FpPartial*>(ws + p.off_partials);

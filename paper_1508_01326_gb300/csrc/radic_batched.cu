@@ -26,7 +26,7 @@ namespace {
 
 constexpr int kBatchMaxM = 10;      // prefix mapping covers 3..10, per-minor 1..8
 constexpr int kBatchThreads = 128;  // four warps per block
-constexpr int kKindMinor = 0, kKindPrefix = 1;
+constexpr int kKindMinor = 0;       // otherwise: prefix depth (2 or 3)
 constexpr double kBinary32ErrorK = 2.5e-6;  // error model constant of the router
 
 struct BatchTask {
@@ -35,28 +35,31 @@ struct BatchTask {
   unsigned long long run;   // prefixes or ranks per lane
   unsigned long long lim;   // prefixes in the group, or C(n,m): end of the range
   int b, m, n, v;           // matrix, shape, prefix group
-  int kind, tier;
+  int kind, tier;           // kKindMinor or the prefix depth; kModeMixed or kModeFp64
 };
 
 struct BatchHeader {
-  unsigned int q32, q64;    // work-queue counters of the two tiers
-  unsigned int nflag;       // binary32 tasks sent to binary64
+  unsigned int q32[kBatchMaxM + 1];    // work-queue counters, binary32 tier, per m
+  unsigned int q64[kBatchMaxM + 1];    // work-queue counters, binary64 tier, per m
+  unsigned int nflag[kBatchMaxM + 1];  // binary32 tasks of each m sent to binary64
   int status;
 };
+static_assert(sizeof(BatchHeader) <= 256, "header slot");
 
 struct BatchArgs {
   const void* A;
   int dtype;
-  int n_tasks32, n_tasks64;
+  int begin32, end32;       // this m's binary32 tasks [begin32, end32)
+  int begin64, end64;       // this m's binary64 tasks
+  int n_tasks32;            // slot index of the first binary64 task
   const BatchTask* tasks32;
   const BatchTask* tasks64;
   FpPartial* slots;         // n_tasks32 + n_tasks64
-  int* flagged;             // n_tasks32
+  int* flagged;             // ids of flagged binary32 tasks, in this m's range
   int* escale;              // per matrix
   BatchHeader* hdr;
   double growth;
   int slice_bytes;          // shared memory per warp
-  int max_n;
 };
 
 struct ReduceArgs {
@@ -74,10 +77,10 @@ template <typename T>
 struct WarpSlice {
   uint64_t* binom;
   T* As;
-  typename Pair2<T>::type* zbuf;
+  unsigned char* zbuf;
 };
 
-// Per-warp slice layout: binom (n+1)(m+1) | As n x cs | zbuf k x 32 pairs.
+// Per-warp slice layout: binom (n+1)(m+1) | As n x cs | column buffer.
 template <typename T>
 __device__ WarpSlice<T> carve_slice(unsigned char* base, int n, int m, int cs) {
   WarpSlice<T> w;
@@ -85,8 +88,8 @@ __device__ WarpSlice<T> carve_slice(unsigned char* base, int n, int m, int cs) {
   w.binom = reinterpret_cast<uint64_t*>(base);
   off = ((size_t)(n + 1) * (m + 1) * 8 + 15) / 16 * 16;
   w.As = reinterpret_cast<T*>(base + off);
-  off += ((size_t)n * cs * sizeof(T) + 15) / 16 * 16;
-  w.zbuf = reinterpret_cast<typename Pair2<T>::type*>(base + off);
+  off += ((size_t)n * cs * sizeof(T) + 31) / 32 * 32;
+  w.zbuf = base + off;
   return w;
 }
 
@@ -138,6 +141,35 @@ struct TaskAcc<float> {
   }
 };
 
+template <typename T, int M, int D, bool kFlag>
+__device__ bool run_prefix(const BatchArgs& a, const BatchTask& t, const WarpSlice<T>& w, TaskAcc<T>& acc,
+                           unsigned long long first, unsigned long long last) {
+  constexpr int CS = ColStride<T, M>::value;
+  constexpr int P = M - D;
+  constexpr int H = P > 1 ? P - 1 : 1;
+  const int lane = threadIdx.x & 31;
+  const T thr = static_cast<T>(a.growth);
+  bool flagged = false;
+  int head[H];
+  if constexpr (P > 1) unrank<P - 1>(first < t.lim ? first : 0ull, t.v, w.binom, M + 1, head);
+  TermsSink ts{nullptr, 0, 0, 0, 0};
+  const ZBuf<T, D> zb(w.zbuf, lane, 32, t.n - M + D);
+  for (unsigned long long it = 0; it < t.run; ++it) {
+    const bool act = first + it < last;
+    int c[P];
+#pragma unroll
+    for (int j = 0; j < P - 1; ++j) c[j] = head[j];
+    c[P - 1] = t.v;
+    const bool f = prefix_one<T, M, D, CS, false>(w.As, w.binom, t.n, t.v, c, zb, thr, act, acc.p, ts);
+    if (kFlag && act && f) flagged = true;
+    acc.p.end_prefix();
+    if constexpr (P > 1) {
+      if (first + it + 1 < last) successor<P - 1>(head, t.v);
+    }
+  }
+  return flagged;
+}
+
 // Works one task in the warp; returns (in every lane) whether a lane flagged.
 template <typename T, int M, bool kFlag>
 __device__ bool run_task(const BatchArgs& a, const BatchTask& t, const WarpSlice<T>& w, TaskAcc<T>& acc) {
@@ -147,27 +179,10 @@ __device__ bool run_task(const BatchArgs& a, const BatchTask& t, const WarpSlice
   bool flagged = false;
   const unsigned long long first = t.r0 + (unsigned long long)lane * t.run;
   const unsigned long long last = min(first + t.run, t.lim);
-  if (t.kind == kKindPrefix) {
-    if constexpr (M >= 3) {
-      constexpr int P = M - 2;
-      constexpr int H = P > 1 ? P - 1 : 1;
-      int head[H];
-      if constexpr (P > 1) unrank<P - 1>(first < t.lim ? first : 0ull, t.v, w.binom, M + 1, head);
-      TermsSink ts{nullptr, 0, 0, 0, 0};
-      for (unsigned long long it = 0; it < t.run; ++it) {
-        const bool act = first + it < last;
-        int c[P];
-#pragma unroll
-        for (int j = 0; j < P - 1; ++j) c[j] = head[j];
-        c[P - 1] = t.v;
-        const bool f = prefix_one<T, M, CS, false>(w.As, w.binom, t.n, t.v, c, w.zbuf + lane, 32, thr, act, acc.p, ts);
-        if (kFlag && act && f) flagged = true;
-        acc.p.end_prefix();
-        if constexpr (P > 1) {
-          if (first + it + 1 < last) successor<P - 1>(head, t.v);
-        }
-      }
-    }
+  if (t.kind == 2) {
+    if constexpr (M >= 3) flagged = run_prefix<T, M, 2, kFlag>(a, t, w, acc, first, last);
+  } else if (t.kind == 3) {
+    if constexpr (M >= 4) flagged = run_prefix<T, M, 3, kFlag>(a, t, w, acc, first, last);
   } else {
     // per-minor mapping: binary32 up to m = 8, binary64 only for m <= 2
     if constexpr (M <= (sizeof(T) == 8 ? 2 : 8)) {
@@ -204,35 +219,14 @@ __device__ __forceinline__ void warp_sum(TaskAcc<T>& acc, Dd& d, double& ab) {
   }
 }
 
-template <typename T, bool kFlag>
-__device__ void dispatch(const BatchArgs& a, const BatchTask& t, unsigned char* slice, int task_id, int slot_id) {
+template <typename T, int M, bool kFlag>
+__device__ void do_task(const BatchArgs& a, const BatchTask& t, unsigned char* slice, int task_id, int slot_id) {
+  constexpr int CS = ColStride<T, M>::value;
   const int lane = threadIdx.x & 31;
-  bool flagged = false;
   TaskAcc<T> acc;
-  int esc = 0;
-  switch (t.m) {
-#define RADIC_BATCH_CASE(MM)                                                        \
-  case MM: {                                                                        \
-    constexpr int CS = ColStride<T, MM>::value;                                     \
-    const WarpSlice<T> w = carve_slice<T>(slice, t.n, MM, CS);                      \
-    esc = stage_warp<T>(a, t, CS, w);                                               \
-    flagged = run_task<T, MM, kFlag>(a, t, w, acc);                                 \
-    break;                                                                          \
-  }
-    RADIC_BATCH_CASE(1)
-    RADIC_BATCH_CASE(2)
-    RADIC_BATCH_CASE(3)
-    RADIC_BATCH_CASE(4)
-    RADIC_BATCH_CASE(5)
-    RADIC_BATCH_CASE(6)
-    RADIC_BATCH_CASE(7)
-    RADIC_BATCH_CASE(8)
-    RADIC_BATCH_CASE(9)
-    RADIC_BATCH_CASE(10)
-#undef RADIC_BATCH_CASE
-    default:
-      break;
-  }
+  const WarpSlice<T> w = carve_slice<T>(slice, t.n, M, CS);
+  const int esc = stage_warp<T>(a, t, CS, w);
+  const bool flagged = run_task<T, M, kFlag>(a, t, w, acc);
   Dd d;
   double ab;
   warp_sum<T>(acc, d, ab);
@@ -240,43 +234,48 @@ __device__ void dispatch(const BatchArgs& a, const BatchTask& t, unsigned char* 
   if (lane == 0) {
     a.escale[t.b] = esc;
     if (kFlag && flagged) {
-      const unsigned int pos = atomicAdd(&a.hdr->nflag, 1u);
-      a.flagged[pos] = task_id;
+      const unsigned int pos = atomicAdd(&a.hdr->nflag[M], 1u);
+      a.flagged[a.begin32 + pos] = task_id;
     } else {
       // count: minors of a binary32 task that was recomputed here in binary64
       long long redone = 0;
       if (!kFlag && t.tier == kModeMixed) {
         const unsigned long long units = min(32ull * t.run, t.lim - t.r0);
-        redone = (long long)(t.kind == kKindPrefix ? units * c_binom.v[t.n - 1 - t.v][2] : units);
+        const int D = t.kind;
+        redone = (long long)(D == kKindMinor ? units : units * c_binom.v[t.n - 1 - t.v][D]);
       }
       a.slots[slot_id] = FpPartial{d.hi, d.lo, ab, redone};
     }
   }
 }
 
-// Persistent kernel of one tier.  Binary32 tier: queue over tasks32.
-// Binary64 tier: queue over tasks64, then over the binary32 tasks that were
-// flagged (their slots are overwritten with binary64 sums).
-template <typename T, bool kMixedTier>
+// Persistent kernel of one tier and one m.  Binary32 tier: queue over this
+// m's binary32 tasks.  Binary64 tier: queue over this m's binary64 tasks, then
+// over this m's binary32 tasks that were flagged (their slots are
+// overwritten with binary64 sums).
+template <typename T, bool kMixedTier, int M>
 __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* slice = smem_raw + (size_t)warp * a.slice_bytes;
-  const int total = kMixedTier ? a.n_tasks32 : a.n_tasks64 + (int)__ldcg(&a.hdr->nflag);
-  unsigned int* counter = kMixedTier ? &a.hdr->q32 : &a.hdr->q64;
+  const int own = kMixedTier ? a.end32 - a.begin32 : a.end64 - a.begin64;
+  const int total = kMixedTier ? own : own + (int)__ldcg(&a.hdr->nflag[M]);
+  unsigned int* counter = kMixedTier ? &a.hdr->q32[M] : &a.hdr->q64[M];
   for (;;) {
     unsigned int i = 0;
     if (lane == 0) i = atomicAdd(counter, 1u);
     i = __shfl_sync(kFull, i, 0);
     if ((int)i >= total) break;
     if (kMixedTier) {
-      dispatch<T, true>(a, a.tasks32[i], slice, (int)i, (int)i);
-    } else if ((int)i < a.n_tasks64) {
-      dispatch<T, false>(a, a.tasks64[i], slice, (int)i, a.n_tasks32 + (int)i);
+      const int id = a.begin32 + (int)i;
+      do_task<T, M, true>(a, a.tasks32[id], slice, id, id);
+    } else if ((int)i < own) {
+      const int id = a.begin64 + (int)i;
+      do_task<T, M, false>(a, a.tasks64[id], slice, id, a.n_tasks32 + id);
     } else {
-      const int id = __ldcg(&a.flagged[i - a.n_tasks64]);
+      const int id = __ldcg(&a.flagged[a.begin32 + (int)i - own]);
       BatchTask t = a.tasks32[id];
-      dispatch<T, false>(a, t, slice, id, id);
+      do_task<T, M, false>(a, t, slice, id, id);
     }
   }
 }
@@ -320,6 +319,23 @@ __global__ void __launch_bounds__(128) k_batch_reduce(ReduceArgs r) {
   }
 }
 
+template <typename T, bool kMixed>
+const void* batch_kernel(int m) {
+  switch (m) {
+    case 1: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 1>);
+    case 2: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 2>);
+    case 3: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 3>);
+    case 4: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 4>);
+    case 5: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 5>);
+    case 6: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 6>);
+    case 7: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 7>);
+    case 8: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 8>);
+    case 9: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 9>);
+    case 10: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 10>);
+    default: return nullptr;
+  }
+}
+
 }  // namespace
 }  // namespace radic
 
@@ -333,12 +349,12 @@ struct radic_batch_plan {
   std::vector<int> shape;            // m, n per matrix
   std::vector<long long> offset;
   std::vector<int> tier;
-  std::vector<BatchTask> t32, t64;
+  std::vector<BatchTask> t32, t64;   // sorted by m, then by cost (largest first)
+  int begin32[kBatchMaxM + 2] = {0}, begin64[kBatchMaxM + 2] = {0};  // task ranges per m
   std::vector<int> csr_ptr, csr_idx;
-  std::vector<int> kind_of_m;        // resolved mapping per m
   int max_n = 1, max_m = 1;
-  int blocks32 = 0, blocks64 = 0;
-  int slice32 = 0, slice64 = 0;
+  int blocks32[kBatchMaxM + 1] = {0}, blocks64[kBatchMaxM + 1] = {0};
+  int slice32[kBatchMaxM + 1] = {0}, slice64[kBatchMaxM + 1] = {0};  // shared memory per warp
   double tol = 1e-10, growth = 64.0;
   // workspace layout
   size_t off_t32 = 0, off_t64 = 0, off_slots = 0, off_flagged = 0, off_escale = 0, off_csr_ptr = 0,
@@ -354,19 +370,18 @@ struct radic_batch_graph {
 
 namespace {
 
-double cost_prefix(int m, int k) {
-  const int P = m - 2;
-  return (double)m * P * P + 3.0 * m * k + 6.0 * k * (k - 1) / 2.0;
-}
 double cost_minor(int m) { return 10.0 * m * m * m / 3.0 + 40.0; }
 
 int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* tun) {
   const int m = pl.shape[2 * b], n = pl.shape[2 * b + 1];
   std::vector<BatchTask>& out = (tier == kModeMixed) ? pl.t32 : pl.t64;
   if (m > n) return RADIC_OK;
-  int kind = (m >= 3) ? kKindPrefix : kKindMinor;
+  const int elem = (tier == kModeMixed) ? 4 : 8;
+  int kind = (m >= 3) ? prefix_auto_depth(m, n, elem) : kKindMinor;
   if (tun && tun->kind[m] == RADIC_MAP_THREAD && m <= 8 && tier == kModeMixed) kind = kKindMinor;
-  if (tun && tun->kind[m] == RADIC_MAP_PREFIX && m >= 3) kind = kKindPrefix;
+  if (tun && tun->kind[m] == RADIC_MAP_PREFIX && m >= 3) kind = prefix_auto_depth(m, n, elem);
+  if (kind != kKindMinor && tun && (tun->prefix_depth[m] == 2 || (tun->prefix_depth[m] == 3 && m >= 4)))
+    kind = tun->prefix_depth[m];
   const double lane_cost = (tun && tun->task_cost[m] > 0.0) ? tun->task_cost[m] : 30000.0;
   BatchTask t;
   std::memset(&t, 0, sizeof(t));
@@ -376,11 +391,11 @@ int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* 
   t.n = n;
   t.kind = kind;
   t.tier = tier;
-  if (kind == kKindPrefix) {
-    const int P = m - 2;
-    for (int v = P - 1; v <= n - 3; ++v) {
+  if (kind != kKindMinor) {
+    const int D = kind, P = m - D;
+    for (int v = P - 1; v <= n - 1 - D; ++v) {
       const unsigned long long cnt = binom_host(v, P - 1);
-      const double c = cost_prefix(m, n - 1 - v);
+      const double c = prefix_cost(m, D, n - 1 - v);
       unsigned long long run = (unsigned long long)std::max(1.0, std::floor(lane_cost / c));
       run = std::min(run, (cnt + 31) / 32);
       if (run < 1) run = 1;
@@ -409,15 +424,15 @@ int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* 
 }
 
 double task_cost(const BatchTask& t) {
-  if (t.kind == kKindPrefix) return (double)t.run * cost_prefix(t.m, t.n - 1 - t.v);
+  if (t.kind != kKindMinor) return (double)t.run * prefix_cost(t.m, t.kind, t.n - 1 - t.v);
   return (double)t.run * cost_minor(t.m);
 }
 
 template <typename T, bool kMixed>
-int persistent_blocks(int slice_bytes, int sms) {
-  const void* k = reinterpret_cast<const void*>(&k_batch<T, kMixed>);
+int persistent_blocks(int m, int slice_bytes, int sms) {
+  const void* k = batch_kernel<T, kMixed>(m);
   const size_t smem = (size_t)slice_bytes * (kBatchThreads / 32);
-  if (!allow_smem(k, smem)) return 0;
+  if (!k || !allow_smem(k, smem)) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBatchThreads, smem) != cudaSuccess) return 0;
   return nb * sms;
@@ -431,7 +446,6 @@ int enqueue(const radic_batch_plan* pl, const void* A, int dtype, radic_result* 
   a.A = A;
   a.dtype = dtype;
   a.n_tasks32 = (int)pl->t32.size();
-  a.n_tasks64 = (int)pl->t64.size();
   a.tasks32 = reinterpret_cast<const BatchTask*>(ws + pl->off_t32);
   a.tasks64 = reinterpret_cast<const BatchTask*>(ws + pl->off_t64);
   a.slots = reinterpret_cast<FpPartial*>(ws + pl->off_slots);
@@ -439,20 +453,33 @@ int enqueue(const radic_batch_plan* pl, const void* A, int dtype, radic_result* 
   a.escale = reinterpret_cast<int*>(ws + pl->off_escale);
   a.hdr = reinterpret_cast<BatchHeader*>(ws);
   a.growth = pl->growth;
-  a.max_n = pl->max_n;
-  if (a.n_tasks32 > 0) {
-    a.slice_bytes = pl->slice32;
-    void* params[] = {&a};
-    if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_batch<float, true>), dim3(pl->blocks32),
-                         dim3(kBatchThreads), params, (size_t)pl->slice32 * (kBatchThreads / 32), s) != cudaSuccess)
-      return RADIC_ECUDA;
+  // binary32 tier, one persistent kernel per m present
+  for (int m = 1; m <= kBatchMaxM; ++m) {
+    a.begin32 = pl->begin32[m];
+    a.end32 = pl->begin32[m + 1];
+    a.begin64 = pl->begin64[m];
+    a.end64 = pl->begin64[m + 1];
+    if (a.end32 > a.begin32) {
+      a.slice_bytes = pl->slice32[m];
+      void* params[] = {&a};
+      if (cudaLaunchKernel(batch_kernel<float, true>(m), dim3(pl->blocks32[m]), dim3(kBatchThreads), params,
+                           (size_t)pl->slice32[m] * (kBatchThreads / 32), s) != cudaSuccess)
+        return RADIC_ECUDA;
+    }
   }
-  if (a.n_tasks64 > 0 || a.n_tasks32 > 0) {
-    a.slice_bytes = pl->slice64;
-    void* params[] = {&a};
-    if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_batch<double, false>), dim3(pl->blocks64),
-                         dim3(kBatchThreads), params, (size_t)pl->slice64 * (kBatchThreads / 32), s) != cudaSuccess)
-      return RADIC_ECUDA;
+  // binary64 tier (and the flagged binary32 tasks), one kernel per m present
+  for (int m = 1; m <= kBatchMaxM; ++m) {
+    a.begin32 = pl->begin32[m];
+    a.end32 = pl->begin32[m + 1];
+    a.begin64 = pl->begin64[m];
+    a.end64 = pl->begin64[m + 1];
+    if (a.end64 > a.begin64 || a.end32 > a.begin32) {
+      a.slice_bytes = pl->slice64[m];
+      void* params[] = {&a};
+      if (cudaLaunchKernel(batch_kernel<double, false>(m), dim3(pl->blocks64[m]), dim3(kBatchThreads), params,
+                           (size_t)pl->slice64[m] * (kBatchThreads / 32), s) != cudaSuccess)
+        return RADIC_ECUDA;
+    }
   }
   ReduceArgs r;
   r.csr_ptr = reinterpret_cast<const int*>(ws + pl->off_csr_ptr);
@@ -517,10 +544,21 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
     }
     make_tasks(*pl, b, tier, tuning);
   }
-  // largest tasks first (longest-processing-time order for the work queues)
-  auto by_cost = [](const BatchTask& x, const BatchTask& y) { return task_cost(x) > task_cost(y); };
-  std::stable_sort(pl->t32.begin(), pl->t32.end(), by_cost);
-  std::stable_sort(pl->t64.begin(), pl->t64.end(), by_cost);
+  // per m, largest tasks first (longest-processing-time order for each queue)
+  auto order = [](const BatchTask& x, const BatchTask& y) {
+    if (x.m != y.m) return x.m < y.m;
+    return task_cost(x) > task_cost(y);
+  };
+  std::stable_sort(pl->t32.begin(), pl->t32.end(), order);
+  std::stable_sort(pl->t64.begin(), pl->t64.end(), order);
+  for (int m = 0; m <= kBatchMaxM + 1; ++m) {
+    pl->begin32[m] = (int)(std::lower_bound(pl->t32.begin(), pl->t32.end(), m,
+                                            [](const BatchTask& t, int mm) { return t.m < mm; }) -
+                           pl->t32.begin());
+    pl->begin64[m] = (int)(std::lower_bound(pl->t64.begin(), pl->t64.end(), m,
+                                            [](const BatchTask& t, int mm) { return t.m < mm; }) -
+                           pl->t64.begin());
+  }
   // per-matrix task lists in task order (fixed summation order)
   std::vector<std::vector<int>> per(batch);
   for (size_t i = 0; i < pl->t32.size(); ++i) per[pl->t32[i].b].push_back((int)i);
@@ -531,31 +569,58 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
     for (int id : per[b]) pl->csr_idx.push_back(id);
   }
   if (pl->csr_idx.empty()) pl->csr_idx.push_back(0);
-  // per-warp shared-memory slices: binomial table and staged matrix for the
-  // largest m and n, column buffer for the most candidate columns (m = 3)
-  auto slice = [&](int cs, int elem) {
-    size_t b = ((size_t)(pl->max_n + 1) * (pl->max_m + 1) * 8 + 15) / 16 * 16;
-    b += ((size_t)pl->max_n * cs * elem + 15) / 16 * 16;
-    b += (size_t)(pl->max_n + 2) * 32 * 2 * elem;
-    return (int)align_up(b, 16);
-  };
-  pl->slice32 = slice(((pl->max_m + 3) / 4) * 4, 4);
-  pl->slice64 = slice(((pl->max_m + 1) / 2) * 2, 8);
+  // per-warp shared-memory slices of each m's kernels: binomial table and
+  // staged matrix for the largest n of that m, column buffer for the most
+  // candidate columns and the deepest prefix among that kernel's tasks (the
+  // binary64 kernel of m also redoes flagged binary32 tasks of m)
+  {
+    int n32[kBatchMaxM + 1] = {0}, d32[kBatchMaxM + 1] = {0}, n64[kBatchMaxM + 1] = {0}, d64[kBatchMaxM + 1] = {0};
+    for (const BatchTask& t : pl->t32) {
+      n32[t.m] = std::max(n32[t.m], t.n);
+      if (t.kind != kKindMinor) d32[t.m] = std::max(d32[t.m], t.kind);
+    }
+    for (const BatchTask& t : pl->t64) {
+      n64[t.m] = std::max(n64[t.m], t.n);
+      if (t.kind != kKindMinor) d64[t.m] = std::max(d64[t.m], t.kind);
+    }
+    auto slice = [](int m, int n, int depth, int cs, int elem) {
+      size_t b = ((size_t)(n + 1) * (m + 1) * 8 + 15) / 16 * 16;
+      b += ((size_t)n * cs * elem + 31) / 32 * 32;
+      if (depth > 0) b += zbuf_bytes(n - m + depth, 32, depth, elem);
+      return (int)align_up(b, 32);
+    };
+    for (int m = 1; m <= kBatchMaxM; ++m) {
+      n64[m] = std::max(n64[m], n32[m]);
+      d64[m] = std::max(d64[m], d32[m]);
+      if (n32[m] > 0) pl->slice32[m] = slice(m, n32[m], d32[m], ((m + 3) / 4) * 4, 4);
+      if (n64[m] > 0) pl->slice64[m] = slice(m, n64[m], d64[m], ((m + 1) / 2) * 2, 8);
+    }
+  }
   const int sms = device_sm_count();
   if (sms <= 0) {
     delete pl;
     return RADIC_ECUDA;
   }
-  int occ = (tuning && tuning->blocks_per_sm > 0) ? tuning->blocks_per_sm : 0;
-  pl->blocks32 = persistent_blocks<float, true>(pl->slice32, sms);
-  pl->blocks64 = persistent_blocks<double, false>(pl->slice64, sms);
-  if (occ > 0) {
-    pl->blocks32 = std::min(pl->blocks32, occ * sms);
-    pl->blocks64 = std::min(pl->blocks64, occ * sms);
-  }
-  if (pl->blocks32 <= 0 || pl->blocks64 <= 0) {
-    delete pl;
-    return RADIC_EUNSUPPORTED;
+  const int occ = (tuning && tuning->blocks_per_sm > 0) ? tuning->blocks_per_sm : 0;
+  for (int m = 1; m <= kBatchMaxM; ++m) {
+    const bool has32 = pl->begin32[m + 1] > pl->begin32[m];
+    const bool has64 = pl->begin64[m + 1] > pl->begin64[m] || has32;
+    if (has32) {
+      pl->blocks32[m] = persistent_blocks<float, true>(m, pl->slice32[m], sms);
+      if (occ > 0) pl->blocks32[m] = std::min(pl->blocks32[m], occ * sms);
+      if (pl->blocks32[m] <= 0) {
+        delete pl;
+        return RADIC_EUNSUPPORTED;
+      }
+    }
+    if (has64) {
+      pl->blocks64[m] = persistent_blocks<double, false>(m, pl->slice64[m], sms);
+      if (occ > 0) pl->blocks64[m] = std::min(pl->blocks64[m], occ * sms);
+      if (pl->blocks64[m] <= 0) {
+        delete pl;
+        return RADIC_EUNSUPPORTED;
+      }
+    }
   }
   // workspace layout
   size_t off = 256;
@@ -593,8 +658,13 @@ int radic_batch_plan_info(const radic_batch_plan* plan, int64_t* info) {
   info[3] = plan->n_fp64_matrices;
   info[4] = (int64_t)plan->minors32;
   info[5] = (int64_t)plan->minors64;
-  info[6] = plan->blocks32;
-  info[7] = plan->blocks64;
+  int64_t b32 = 0, b64 = 0;
+  for (int m = 1; m <= kBatchMaxM; ++m) {
+    b32 = std::max<int64_t>(b32, plan->blocks32[m]);
+    b64 = std::max<int64_t>(b64, plan->blocks64[m]);
+  }
+  info[6] = b32;
+  info[7] = b64;
   return RADIC_OK;
 }
 

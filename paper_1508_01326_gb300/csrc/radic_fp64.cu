@@ -18,23 +18,23 @@ const void* group_kernel(bool terms) {
                : reinterpret_cast<const void*>(&k_fp_group<double, G, false, false>);
 }
 
-template <int M>
+template <int M, int D>
 const void* prefix_kernel(bool terms) {
-  return terms ? reinterpret_cast<const void*>(&k_fp_prefix<double, M, false, true>)
-               : reinterpret_cast<const void*>(&k_fp_prefix<double, M, false, false>);
+  return terms ? reinterpret_cast<const void*>(&k_fp_prefix<double, M, D, false, true>)
+               : reinterpret_cast<const void*>(&k_fp_prefix<double, M, D, false, false>);
 }
 
 const void* pick(const SinglePlan& p, bool terms) {
   if (p.mapping == RADIC_MAP_PREFIX) {
     switch (p.m) {
-      case 3: return prefix_kernel<3>(terms);
-      case 4: return prefix_kernel<4>(terms);
-      case 5: return prefix_kernel<5>(terms);
-      case 6: return prefix_kernel<6>(terms);
-      case 7: return prefix_kernel<7>(terms);
-      case 8: return prefix_kernel<8>(terms);
-      case 9: return prefix_kernel<9>(terms);
-      case 10: return prefix_kernel<10>(terms);
+      case 3: return p.depth == 2 ? prefix_kernel<3, 2>(terms) : nullptr;
+      case 4: return p.depth == 3 ? prefix_kernel<4, 3>(terms) : prefix_kernel<4, 2>(terms);
+      case 5: return p.depth == 3 ? prefix_kernel<5, 3>(terms) : prefix_kernel<5, 2>(terms);
+      case 6: return p.depth == 3 ? prefix_kernel<6, 3>(terms) : prefix_kernel<6, 2>(terms);
+      case 7: return p.depth == 3 ? prefix_kernel<7, 3>(terms) : prefix_kernel<7, 2>(terms);
+      case 8: return p.depth == 3 ? prefix_kernel<8, 3>(terms) : prefix_kernel<8, 2>(terms);
+      case 9: return p.depth == 3 ? prefix_kernel<9, 3>(terms) : prefix_kernel<9, 2>(terms);
+      case 10: return p.depth == 3 ? prefix_kernel<10, 3>(terms) : prefix_kernel<10, 2>(terms);
       default: return nullptr;
     }
   }
@@ -60,7 +60,7 @@ const void* pick(const SinglePlan& p, bool terms) {
 
 size_t smem_fp64(const SinglePlan& p) {
   const int cs = (p.mapping != RADIC_MAP_GROUP) ? ((p.m + 1) / 2) * 2 : p.m;
-  if (p.mapping == RADIC_MAP_PREFIX) return prefix_smem_bytes(p.n, p.m, cs, 8, p.threads);
+  if (p.mapping == RADIC_MAP_PREFIX) return prefix_smem_bytes(p.n, p.m, cs, 8, p.threads, p.depth);
   return fp_smem_bytes(p.n, p.m, cs, 8, p.threads);
 }
 

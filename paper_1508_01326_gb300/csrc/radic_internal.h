@@ -64,6 +64,7 @@ struct SinglePlan {
   int mapping = RADIC_MAP_THREAD;  // resolved mapping
   int group = 0;                   // lanes per minor for the group mapping
   PrefixTable ptab{};              // prefix mapping only
+  int depth = 2;                   // prefix mapping: trailing columns per leaf
   int threads = 128;
   int blocks = 1;
   unsigned long long ranks_per_task = 64;
@@ -120,6 +121,33 @@ int blocks_per_sm_modp(const SinglePlan& p);
 size_t smem_fp64(const SinglePlan& p);
 size_t smem_mixed(const SinglePlan& p);
 size_t smem_modp(const SinglePlan& p);
+
+// Cost model of the prefix mapping (instruction units): P = m - D prefix
+// columns, D = 2 or 3 trailing columns per leaf; a prefix with k candidate
+// columns costs its factorisation m P^2, m + 2 D P per candidate column,
+// 8 per column pair (D = 3) and 6 per leaf.  Group v (last prefix column)
+// holds C(v, P-1) prefixes with k = n-1-v.
+inline double prefix_cost(int m, int D, int k) {
+  const int P = m - D;
+  double c = (double)m * P * P + (double)k * (m + 2.0 * D * P) + 6.0 * (double)binom_host(k, D);
+  if (D == 3) c += 8.0 * (double)binom_host(k, 2);
+  return c;
+}
+
+// Default prefix depth for an m x n matrix whose elimination uses elements
+// of `elem` bytes.  Depth 3 divides the number of prefix factorisations by
+// about (n - m + 3) / (m - 2) but holds three Schur-complement entries per
+// candidate column, up to n - m + 3 columns per lane, in shared memory; with
+// many candidate columns that buffer cuts occupancy and the leaves' longer
+// chains are no longer hidden.  Measured on GB300 (single 8x32, 6x40, 10x30,
+// 12x28, 5x60 matrices and the batched m = 3..10 sets): depth 3 wins from
+// m = 6 on while n - m <= 3m with binary32 elements, n - m <= 2.5m with
+// binary64 elements (twice the bytes per entry), and loses below m = 6.
+inline int prefix_auto_depth(int m, int n, int elem) {
+  if (m < 6) return 2;
+  const int extra = n - m;
+  return (elem <= 4 ? extra <= 3 * m : 2 * extra <= 5 * m) ? 3 : 2;
+}
 
 inline int ceil_div(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

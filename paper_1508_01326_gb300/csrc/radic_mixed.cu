@@ -64,25 +64,27 @@ template <int MC>
 __device__ long long prefix_leaves_f64(const FpSmem<double>& sm, int n, int m, int P, unsigned long long rp, Dd& acc,
                                        double& abs_sum) {
   long long cnt = 0;
-  int pre[MC];
-  // the binomial table is built for k <= m, which covers P = m - 2
-  unrank_dyn<MC>(rp, n, P, sm.binom, m + 1, pre);
-  const int v = pre[P - 1];
-  for (int c1 = v + 1; c1 < n; ++c1) {
-    for (int c2 = c1 + 1; c2 < n; ++c2) {
-      int cols[MC];
-      for (int j = 0; j < P; ++j) cols[j] = pre[j];
-      cols[P] = c1;
-      cols[P + 1] = c2;
-      double a[MC * MC];
-      for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) a[i * MC + j] = sm.As[cols[j] * m + i];
-      double det = lu_det_local<MC>(a, m);
-      if (sign_negative_dyn<MC>(cols, m)) det = -det;
-      acc.add(det);
-      abs_sum += fabs(det);
-      ++cnt;
-    }
+  int cols[MC];
+  // the binomial table is built for k <= m, which covers P
+  unrank_dyn<MC>(rp, n, P, sm.binom, m + 1, cols);
+  const int v = cols[P - 1], D = m - P;
+  // every D-subset of {v+1 .. n-1}, in dictionary order
+  for (int d = 0; d < D; ++d) cols[P + d] = v + 1 + d;
+  if (cols[m - 1] >= n) return 0;
+  for (;;) {
+    double a[MC * MC];
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) a[i * MC + j] = sm.As[cols[j] * m + i];
+    double det = lu_det_local<MC>(a, m);
+    if (sign_negative_dyn<MC>(cols, m)) det = -det;
+    acc.add(det);
+    abs_sum += fabs(det);
+    ++cnt;
+    int pos = m - 1;
+    while (pos >= P && cols[pos] == n - m + pos) --pos;
+    if (pos < P) break;
+    ++cols[pos];
+    for (int j = pos + 1; j < m; ++j) cols[j] = cols[j - 1] + 1;
   }
   return cnt;
 }
@@ -190,25 +192,25 @@ const void* group_kernel(bool terms) {
                : reinterpret_cast<const void*>(&k_fp_group<float, G, true, false>);
 }
 
-template <int M>
+template <int M, int D>
 const void* prefix_kernel(bool terms) {
-  return terms ? reinterpret_cast<const void*>(&k_fp_prefix<float, M, true, true>)
-               : reinterpret_cast<const void*>(&k_fp_prefix<float, M, true, false>);
+  return terms ? reinterpret_cast<const void*>(&k_fp_prefix<float, M, D, true, true>)
+               : reinterpret_cast<const void*>(&k_fp_prefix<float, M, D, true, false>);
 }
 
 const void* pick(const SinglePlan& p, bool terms) {
   if (p.mapping == RADIC_MAP_PREFIX) {
     switch (p.m) {
-      case 3: return prefix_kernel<3>(terms);
-      case 4: return prefix_kernel<4>(terms);
-      case 5: return prefix_kernel<5>(terms);
-      case 6: return prefix_kernel<6>(terms);
-      case 7: return prefix_kernel<7>(terms);
-      case 8: return prefix_kernel<8>(terms);
-      case 9: return prefix_kernel<9>(terms);
-      case 10: return prefix_kernel<10>(terms);
-      case 11: return prefix_kernel<11>(terms);
-      case 12: return prefix_kernel<12>(terms);
+      case 3: return p.depth == 2 ? prefix_kernel<3, 2>(terms) : nullptr;
+      case 4: return p.depth == 3 ? prefix_kernel<4, 3>(terms) : prefix_kernel<4, 2>(terms);
+      case 5: return p.depth == 3 ? prefix_kernel<5, 3>(terms) : prefix_kernel<5, 2>(terms);
+      case 6: return p.depth == 3 ? prefix_kernel<6, 3>(terms) : prefix_kernel<6, 2>(terms);
+      case 7: return p.depth == 3 ? prefix_kernel<7, 3>(terms) : prefix_kernel<7, 2>(terms);
+      case 8: return p.depth == 3 ? prefix_kernel<8, 3>(terms) : prefix_kernel<8, 2>(terms);
+      case 9: return p.depth == 3 ? prefix_kernel<9, 3>(terms) : prefix_kernel<9, 2>(terms);
+      case 10: return p.depth == 3 ? prefix_kernel<10, 3>(terms) : prefix_kernel<10, 2>(terms);
+      case 11: return p.depth == 3 ? prefix_kernel<11, 3>(terms) : prefix_kernel<11, 2>(terms);
+      case 12: return p.depth == 3 ? prefix_kernel<12, 3>(terms) : prefix_kernel<12, 2>(terms);
       default: return nullptr;
     }
   }
@@ -244,7 +246,7 @@ const void* pick_fixup(int m) {
 
 size_t smem_mixed(const SinglePlan& p) {
   const int cs = (p.mapping != RADIC_MAP_GROUP) ? ((p.m + 3) / 4) * 4 : p.m;
-  if (p.mapping == RADIC_MAP_PREFIX) return prefix_smem_bytes(p.n, p.m, cs, 4, p.threads);
+  if (p.mapping == RADIC_MAP_PREFIX) return prefix_smem_bytes(p.n, p.m, cs, 4, p.threads, p.depth);
   return fp_smem_bytes(p.n, p.m, cs, 4, p.threads);
 }
 

@@ -24,11 +24,59 @@
 
 namespace radic {
 
-__host__ __device__ inline size_t prefix_smem_bytes(int n, int m, int cs, int elem, int threads) {
-  const int kmax = n - m + 2;  // largest number of candidate columns
-  size_t off = fp_smem_bytes(n, m, cs, elem, threads);
-  off += (size_t)kmax * threads * 2 * elem;
-  return off;
+// A lane's column buffer of the leaf phase: entry q holds the D
+// Schur-complement entries of candidate column q.  Entries of one lane are
+// `stride` elements apart (lanes interleaved, so a warp's accesses to the
+// same q are contiguous).  D = 2 stores one 2-vector per entry; D = 3 stores
+// three planes `plane` elements apart (12 or 24 bytes per entry, no padding).
+template <typename T, int D>
+struct ZBuf;
+template <typename T>
+struct ZBuf<T, 2> {
+  using V = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+  V* p;
+  int stride;
+  __device__ ZBuf(void* base, int lane, int stride_, int /*kcap*/) : p(static_cast<V*>(base) + lane), stride(stride_) {}
+  __device__ __forceinline__ void get(int q, T (&y)[2]) const {
+    const V v = p[q * stride];
+    y[0] = v.x;
+    y[1] = v.y;
+  }
+  __device__ __forceinline__ void put(int q, const T (&z)[2]) const {
+    V v;
+    v.x = z[0];
+    v.y = z[1];
+    p[q * stride] = v;
+  }
+};
+template <typename T>
+struct ZBuf<T, 3> {
+  T* p;
+  int stride, plane;
+  __device__ ZBuf(void* base, int lane, int stride_, int kcap)
+      : p(static_cast<T*>(base) + lane), stride(stride_), plane(kcap * stride_) {}
+  __device__ __forceinline__ void get(int q, T (&y)[3]) const {
+    const T* e = p + q * stride;
+    y[0] = e[0];
+    y[1] = e[plane];
+    y[2] = e[2 * plane];
+  }
+  __device__ __forceinline__ void put(int q, const T (&z)[3]) const {
+    T* e = p + q * stride;
+    e[0] = z[0];
+    e[plane] = z[1];
+    e[2 * plane] = z[2];
+  }
+};
+
+// Bytes of the column buffer for `lanes` lanes with up to kcap entries each.
+__host__ __device__ inline size_t zbuf_bytes(int kcap, int lanes, int depth, int elem) {
+  return (size_t)kcap * lanes * depth * elem;
+}
+
+__host__ __device__ inline size_t prefix_smem_bytes(int n, int m, int cs, int elem, int threads, int depth) {
+  const int kmax = n - m + depth;  // largest number of candidate columns
+  return fp_smem_bytes(n, m, cs, elem, threads) + zbuf_bytes(kmax, threads, depth, elem);
 }
 
 // Rank of an ascending 0-based combination in dictionary order (the inverse of
@@ -37,13 +85,13 @@ __device__ __forceinline__ unsigned long long rank_part(const uint64_t* binom, i
   return binom[(n - 1 - c) * bstride + k];
 }
 
-// Factor the m x (m-2) prefix with partial pivoting.  Outputs the row order
-// idx[], W (2 x (m-2)), the product of pivots, the largest pivot magnitude and
-// the parity of the row permutation.
-template <typename T, int M, int CS>
-__device__ __forceinline__ void prefix_factor(const T* __restrict__ As, const int (&c)[M - 2], T (&W)[2][M - 2],
+// Factor the m x P prefix (P = m - D) with partial pivoting.  Outputs the row
+// order idx[], W = -L21 L11^{-1} (D x P), the product of pivots, the largest
+// pivot magnitude and the parity of the row permutation.
+template <typename T, int M, int D, int CS>
+__device__ __forceinline__ void prefix_factor(const T* __restrict__ As, const int (&c)[M - D], T (&W)[D][M - D],
                                               int (&idx)[M], T& prod, T& gmax, bool& neg) {
-  constexpr int P = M - 2;
+  constexpr int P = M - D;
   T a[M][P];
 #pragma unroll
   for (int j = 0; j < P; ++j) {
@@ -88,7 +136,7 @@ __device__ __forceinline__ void prefix_factor(const T* __restrict__ As, const in
   }
   // W = -L21 L11^{-1}: w_j = -l21_j - sum_{i > j} w_i L11[i][j], j descending.
 #pragma unroll
-  for (int rr = 0; rr < 2; ++rr) {
+  for (int rr = 0; rr < D; ++rr) {
 #pragma unroll
     for (int j = P - 1; j >= 0; --j) {
       T s = -a[P + rr][j];
@@ -99,20 +147,20 @@ __device__ __forceinline__ void prefix_factor(const T* __restrict__ As, const in
   }
 }
 
-// Schur complement of column `col` (rows read in the pivoted order idx[]).
-template <typename T, int M>
-__device__ __forceinline__ void prefix_column(const T* __restrict__ col, const T (&W)[2][M - 2], const int (&idx)[M],
-                                              T& z0, T& z1) {
-  constexpr int P = M - 2;
+// Schur complement (D entries) of column `col`, rows read in the order idx[].
+template <typename T, int M, int D>
+__device__ __forceinline__ void prefix_column(const T* __restrict__ col, const T (&W)[D][M - D], const int (&idx)[M],
+                                              T (&z)[D]) {
+  constexpr int P = M - D;
   T x[M];
 #pragma unroll
   for (int s = 0; s < M; ++s) x[s] = col[idx[s]];
-  z0 = x[P];
-  z1 = x[P + 1];
+#pragma unroll
+  for (int d = 0; d < D; ++d) z[d] = x[P + d];
 #pragma unroll
   for (int j = 0; j < P; ++j) {
-    z0 = fma(W[0][j], x[j], z0);
-    z1 = fma(W[1][j], x[j], z1);
+#pragma unroll
+    for (int d = 0; d < D; ++d) z[d] = fma(W[d][j], x[j], z[d]);
   }
 }
 
@@ -160,12 +208,6 @@ struct PrefixAcc<float> {
   }
 };
 
-// Two-entry vector type of T.
-template <typename T>
-struct Pair2 {
-  using type = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
-};
-
 // Where per-leaf terms go (terms output of the parity tests); unused otherwise.
 struct TermsSink {
   double* terms;
@@ -173,84 +215,252 @@ struct TermsSink {
   int escale;
 };
 
-// Processes one prefix c[0..m-3] (last column v): factors it, reduces every
-// later column to its Schur complement, forms the 2 x 2 leaf determinants
-// with the sign of Eq. (1) and adds them to acc.pre (the caller commits or
-// drops them).  `zb` is this lane's slot of the column buffer, `zstride` the
-// distance between consecutive columns.  Returns the growth flag of the mixed
-// mode: largest prefix pivot, or twice the largest Schur entry (a bound for
-// the last two pivots), above `thr`, or a non-finite scale.
-template <typename T, int M, int CS, bool kTerms>
-__device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint64_t* binom, int n, int v,
-                                           const int (&c)[M - 2], typename Pair2<T>::type* zb, int zstride, T thr,
-                                           bool act, PrefixAcc<T>& acc, const TermsSink& ts) {
-  constexpr int P = M - 2;
-  using T2 = typename Pair2<T>::type;
+// Columns per step of the blocked leaf phase: every buffer entry loaded from
+// shared memory serves kLeafBlock leaves (fewer loads per leaf, kLeafBlock
+// independent sums in flight).  Binary64 keeps one column per step: its
+// leaves are bound by the binary64 pipe, and wider blocks only cost registers.
+#ifndef RADIC_LEAF_BLOCK_F32
+#define RADIC_LEAF_BLOCK_F32 4
+#endif
+#ifndef RADIC_LEAF_BLOCK_F64
+#define RADIC_LEAF_BLOCK_F64 1
+#endif
+template <typename T>
+__host__ __device__ constexpr int leaf_block() {
+  return sizeof(T) == 4 ? RADIC_LEAF_BLOCK_F32 : RADIC_LEAF_BLOCK_F64;
+}
+
+template <typename T>
+__device__ __forceinline__ void leaf_add(T d, T& s, T& a) {
+  s += d;
+  a += fabs(d);
+}
+
+// 2 x 2 and 3 x 3 leaf determinants of Schur-complement columns.
+template <typename T>
+__device__ __forceinline__ T det2(const T (&x)[2], const T (&y)[2]) {
+  return fma(x[0], y[1], -(x[1] * y[0]));
+}
+template <typename T>
+__device__ __forceinline__ void cross3(const T (&x)[3], const T (&y)[3], T (&w)[3]) {
+  w[0] = fma(x[1], y[2], -(x[2] * y[1]));
+  w[1] = fma(x[2], y[0], -(x[0] * y[2]));
+  w[2] = fma(x[0], y[1], -(x[1] * y[0]));
+}
+template <typename T>
+__device__ __forceinline__ T dot3(const T (&x)[3], const T (&w)[3]) {
+  return fma(x[0], w[0], fma(x[1], w[1], x[2] * w[2]));
+}
+
+// Schur complement of candidate column `col`, with the sign of its index
+// parity and (first entry) the prefix scale alpha folded in; updates zmax.
+template <typename T, int M, int D, int CS>
+__device__ __forceinline__ void leaf_column(const T* __restrict__ As, int col, const T (&W)[D][M - D],
+                                            const int (&idx)[M], T alpha, T (&z)[D], T& zmax) {
+  prefix_column<T, M, D>(As + col * CS, W, idx, z);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    zmax = fmax(zmax, fabs(z[d]));
+    if (col & 1) z[d] = -z[d];
+  }
+  z[0] *= alpha;
+}
+
+// Leaf phase of one prefix without per-leaf output: the k later columns are
+// taken LB at a time (q, q+1, ...).  For each block, the leaves whose other
+// D-1 columns lie before the block read those columns' z from the buffer
+// once for the whole block; leaves with two or three columns inside the
+// block are formed from registers.  Leaf sums are kept per column and added
+// to acc in column order.  Columns past k in the last block are zero and
+// their sums are discarded.
+template <typename T, int M, int D, int CS>
+__device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, int v, int k, const T (&W)[D][M - D],
+                                                      const int (&idx)[M], T alpha, const ZBuf<T, D>& zb, bool act,
+                                                      PrefixAcc<T>& acc, T& zmax) {
+  constexpr int LB = leaf_block<T>();
+  for (int q = 0; q < k; q += LB) {
+    T z[LB][D];
+#pragma unroll
+    for (int b = 0; b < LB; ++b) {
+      if (q + b < k) {  // the same k in every lane of a warp
+        leaf_column<T, M, D, CS>(As, v + 1 + q + b, W, idx, alpha, z[b], zmax);
+      } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) z[b][d] = T(0);
+      }
+    }
+    T cs[LB], ca[LB];
+#pragma unroll
+    for (int b = 0; b < LB; ++b) cs[b] = ca[b] = T(0);
+    if constexpr (D == 2) {
+      // (q2, q + b), q2 < q
+#pragma unroll 2
+      for (int q2 = 0; q2 < q; ++q2) {
+        T y[2];
+        zb.get(q2, y);
+#pragma unroll
+        for (int b = 0; b < LB; ++b) leaf_add(det2(y, z[b]), cs[b], ca[b]);
+      }
+      // (q + b2, q + b), b2 < b
+#pragma unroll
+      for (int b = 1; b < LB; ++b) {
+#pragma unroll
+        for (int b2 = 0; b2 < b; ++b2) leaf_add(det2(z[b2], z[b]), cs[b], ca[b]);
+      }
+    } else {
+      // (q1, q2, q + b), q1 < q2 < q: y1 . (y2 x z_b)
+      for (int q2 = 0; q2 < q; ++q2) {
+        T y2[3];
+        zb.get(q2, y2);
+        T w[LB][3];
+#pragma unroll
+        for (int b = 0; b < LB; ++b) cross3(y2, z[b], w[b]);
+#pragma unroll 2
+        for (int q1 = 0; q1 < q2; ++q1) {
+          T y1[3];
+          zb.get(q1, y1);
+#pragma unroll
+          for (int b = 0; b < LB; ++b) leaf_add(dot3(y1, w[b]), cs[b], ca[b]);
+        }
+      }
+      if constexpr (LB > 1) {
+        // (q1, q + b2, q + b), q1 < q, b2 < b: y1 . (z_b2 x z_b); pair
+        // (b2, b) is entry b(b-1)/2 + b2 of w
+        T w[LB * (LB - 1) / 2][3];
+#pragma unroll
+        for (int b = 1; b < LB; ++b) {
+#pragma unroll
+          for (int b2 = 0; b2 < b; ++b2) cross3(z[b2], z[b], w[b * (b - 1) / 2 + b2]);
+        }
+#pragma unroll 2
+        for (int q1 = 0; q1 < q; ++q1) {
+          T y1[3];
+          zb.get(q1, y1);
+#pragma unroll
+          for (int b = 1; b < LB; ++b) {
+#pragma unroll
+            for (int b2 = 0; b2 < b; ++b2) leaf_add(dot3(y1, w[b * (b - 1) / 2 + b2]), cs[b], ca[b]);
+          }
+        }
+        // (q + b1, q + b2, q + b), b1 < b2 < b
+#pragma unroll
+        for (int b = 2; b < LB; ++b) {
+#pragma unroll
+          for (int b2 = 1; b2 < b; ++b2) {
+#pragma unroll
+            for (int b1 = 0; b1 < b2; ++b1) leaf_add(dot3(z[b1], w[b * (b - 1) / 2 + b2]), cs[b], ca[b]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < LB; ++b) {
+      if (q + b < k) {
+        zb.put(q + b, z[b]);
+        if (act) acc.add_column(cs[b], ca[b]);
+      }
+    }
+  }
+}
+
+// Leaf phase with per-leaf output (terms of the parity tests): one column at
+// a time, every leaf's dictionary-order rank computed and its term stored
+// when it falls in the requested window.
+template <typename T, int M, int D, int CS>
+__device__ __forceinline__ void prefix_leaves_terms(const T* __restrict__ As, const uint64_t* binom, int n, int v,
+                                                    int k, const T (&W)[D][M - D], const int (&idx)[M], T alpha,
+                                                    unsigned long long rank_prefix, const ZBuf<T, D>& zb, bool act,
+                                                    PrefixAcc<T>& acc, T& zmax, const TermsSink& ts) {
   const int bs = M + 1;
-  T W[2][P];
+  auto emit = [&](T d, unsigned long long rk) {
+    rk = ts.qtot - 1 - rk;
+    if (act && rk >= ts.q0 && rk < ts.q0 + ts.count) ts.terms[rk - ts.q0] = ldexp(static_cast<double>(d), ts.escale);
+  };
+  for (int q = 0; q < k; ++q) {
+    const int col = v + 1 + q;
+    T z[D];
+    leaf_column<T, M, D, CS>(As, col, W, idx, alpha, z, zmax);
+    const unsigned long long rk_col = rank_prefix + rank_part(binom, bs, n, col, 1);
+    T colsum = T(0), colabs = T(0);
+    if constexpr (D == 2) {
+      for (int q2 = 0; q2 < q; ++q2) {
+        T y[2];
+        zb.get(q2, y);
+        const T d = det2(y, z);
+        emit(d, rk_col + rank_part(binom, bs, n, v + 1 + q2, 2));
+        leaf_add(d, colsum, colabs);
+      }
+    } else {
+      for (int q2 = 0; q2 < q; ++q2) {
+        T y2[3], w[3];
+        zb.get(q2, y2);
+        cross3(y2, z, w);
+        const unsigned long long rk2 = rk_col + rank_part(binom, bs, n, v + 1 + q2, 2);
+        for (int q1 = 0; q1 < q2; ++q1) {
+          T y1[3];
+          zb.get(q1, y1);
+          const T d = dot3(y1, w);
+          emit(d, rk2 + rank_part(binom, bs, n, v + 1 + q1, 3));
+          leaf_add(d, colsum, colabs);
+        }
+      }
+    }
+    zb.put(q, z);
+    if (act) acc.add_column(colsum, colabs);
+  }
+}
+
+// Processes one prefix c[0..m-D-1] (last column v): factors it, reduces every
+// later column to its D-entry Schur complement and forms the D x D leaf
+// determinants with the sign of Eq. (1), adding them to acc.pre (the caller
+// commits or drops them).  D = 2: det = z1[0] z2[1] - z1[1] z2[0].  D = 3:
+// det = z1 . (z2 x z3), the cross product formed once per pair (c2, c3).
+// `zb` is this lane's column buffer.  Returns the growth flag of the mixed
+// mode: largest prefix pivot, or 2^(D-1) max|z| (a bound for the last D
+// pivots under partial pivoting), above `thr`, or a non-finite scale.
+template <typename T, int M, int D, int CS, bool kTerms>
+__device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint64_t* binom, int n, int v,
+                                           const int (&c)[M - D], const ZBuf<T, D>& zb, T thr, bool act,
+                                           PrefixAcc<T>& acc, const TermsSink& ts) {
+  constexpr int P = M - D;
+  T W[D][P];
   int idx[M];
   T prod, gmax;
   bool neg;
-  prefix_factor<T, M, CS>(As, c, W, idx, prod, gmax, neg);
-  // parity of r = M(M+1)/2, of the prefix columns' share of s, and of the two
-  // leaf columns' "+1" terms; the leaf columns' own parities are folded in below
-  int sp = M * (M + 1) / 2 + 2;
+  prefix_factor<T, M, D, CS>(As, c, W, idx, prod, gmax, neg);
+  // parity of r = M(M+1)/2, of the prefix columns' share of s, and of the D
+  // leaf columns' "+1" terms; the leaf columns' own parities are folded in
+  // per column
+  int sp = M * (M + 1) / 2 + D;
 #pragma unroll
   for (int j = 0; j < P; ++j) sp += c[j] + 1;
   const T alpha = ((sp & 1) != neg) ? -prod : prod;
-  unsigned long long rank_prefix = 0;
-  if constexpr (kTerms) {
-#pragma unroll
-    for (int j = 0; j < P; ++j) rank_prefix += rank_part(binom, bs, n, c[j], M - j);
-  }
   T zmax = T(0);
   const int k = n - 1 - v;
-  for (int q = 0; q < k; ++q) {
-    const int col = v + 1 + q;
-    T z0, z1;
-    prefix_column<T, M>(As + col * CS, W, idx, z0, z1);
-    zmax = fmax(zmax, fmax(fabs(z0), fabs(z1)));
-    if (col & 1) {
-      z0 = -z0;
-      z1 = -z1;
-    }
-    z0 *= alpha;
-    T colsum = T(0), colabs = T(0);
-    const T2* yp = zb;
-#pragma unroll 4
-    for (int q2 = 0; q2 < q; ++q2, yp += zstride) {
-      const T2 y = *yp;
-      const T d = fma(y.x, z1, -(y.y * z0));
-      if constexpr (kTerms) {
-        const int c2 = v + 1 + q2;
-        const unsigned long long rk =
-            ts.qtot - 1 - (rank_prefix + rank_part(binom, bs, n, c2, 2) + rank_part(binom, bs, n, col, 1));
-        if (act && rk >= ts.q0 && rk < ts.q0 + ts.count) ts.terms[rk - ts.q0] = ldexp(static_cast<double>(d), ts.escale);
-      }
-      colsum += d;
-      colabs += fabs(d);
-    }
-    T2 zz;
-    zz.x = z0;
-    zz.y = z1;
-    zb[q * zstride] = zz;
-    if (act) acc.add_column(colsum, colabs);
+  if constexpr (kTerms) {
+    unsigned long long rank_prefix = 0;
+#pragma unroll
+    for (int j = 0; j < P; ++j) rank_prefix += rank_part(binom, M + 1, n, c[j], M - j);
+    prefix_leaves_terms<T, M, D, CS>(As, binom, n, v, k, W, idx, alpha, rank_prefix, zb, act, acc, zmax, ts);
+  } else {
+    prefix_leaves_blocked<T, M, D, CS>(As, v, k, W, idx, alpha, zb, act, acc, zmax);
   }
-  return !(gmax <= thr) || !(2 * zmax <= thr) || !(fabs(alpha) <= static_cast<T>(FLT_MAX));
+  const T growth_bound = (D == 2 ? T(2) : T(4)) * zmax;
+  return !(gmax <= thr) || !(growth_bound <= thr) || !(fabs(alpha) <= static_cast<T>(FLT_MAX));
 }
 
 // ---------------------------------------------------------------------------
 // Single-matrix prefix kernel.
 // ---------------------------------------------------------------------------
-template <typename T, int M, bool kMixed, bool kTerms>
+template <typename T, int M, int D, bool kMixed, bool kTerms>
 __global__ void __launch_bounds__(128) k_fp_prefix(SingleArgs a, PrefixTable tab) {
-  static_assert(M >= 3, "prefix sharing needs m >= 3");
-  constexpr int P = M - 2;
+  static_assert(M > D, "the prefix needs at least one column");
+  constexpr int P = M - D;
   constexpr int CS = ColStride<T, M>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.n;
   FpSmem<T> sm(smem_raw, n, M, CS);
-  T* zbuf = reinterpret_cast<T*>(smem_raw + fp_smem_bytes(n, M, CS, sizeof(T), blockDim.x));
+  const ZBuf<T, D> zb(smem_raw + fp_smem_bytes(n, M, CS, sizeof(T), blockDim.x), threadIdx.x, blockDim.x, n - M + D);
   build_binom(sm.binom, n, M);
   const int escale = stage_scaled<T>(a.A, a.dtype, M, n, a.lda, sm.As, CS, sm.row_exp);
 
@@ -281,16 +491,14 @@ __global__ void __launch_bounds__(128) k_fp_prefix(SingleArgs a, PrefixTable tab
 #pragma unroll
       for (int j = 0; j < P - 1; ++j) c[j] = head[j];
       c[P - 1] = v;
-      using T2 = typename Pair2<T>::type;
-      T2* zb = reinterpret_cast<T2*>(zbuf) + threadIdx.x;  // column q at zb[q * blockDim.x]
-      const bool flag = prefix_one<T, M, CS, kTerms>(sm.As, sm.binom, n, v, c, zb, blockDim.x, thr, act, acc, ts);
+      const bool flag = prefix_one<T, M, D, CS, kTerms>(sm.As, sm.binom, n, v, c, zb, thr, act, acc, ts);
       if constexpr (kMixed && !kTerms) {
         if (act && flag) acc.drop_prefix();  // its leaves are recomputed in binary64
         const unsigned fm = __ballot_sync(kFull, act && flag);
         if (fm) {
           if (act && flag) {
             const int pos = fcnt + __popc(fm & ((1u << lane) - 1u));
-            // record the prefix by its rank among all (m-2)-subsets of {0..n-1}
+            // record the prefix by its rank among all P-subsets of {0..n-1}
             unsigned long long rp = sm.binom[n * bs + P] - 1;
 #pragma unroll
             for (int j = 0; j < P; ++j) rp -= rank_part(sm.binom, bs, n, c[j], P - j);

@@ -107,6 +107,16 @@ def test_batch_with_per_minor_tuning_and_float32_input():
         assert abs(float(Fraction(r["value"]) - val)) <= 8 * m * 2.0 ** -24 * float(abs_sum) * 4
 
 
+@pytest.mark.parametrize("depth", [2, 3])
+def test_batch_prefix_depths_match_oracle(depth):
+    mats = small_batch(4, 40, max_m=10, max_d=8)
+    tuning = R().make_tuning(prefix_depth={m: depth for m in range(3, 11)}, task_cost={m: 3000 for m in range(1, 11)})
+    res, _ = run_batch(mats, "fp64", tuning=tuning)
+    for a, r in zip(mats, res):
+        val, abs_sum = orc.radic_det_exact(a)
+        assert abs(Fraction(r["value"]) - val) <= Fraction(1e-12) * abs_sum
+
+
 def test_batch_is_deterministic():
     mats = small_batch(3, 50, max_d=12)
     tuning = R().make_tuning(tol=1.0)

@@ -64,10 +64,15 @@ OPTS = {
     "g32": dict(mapping="group", group_width=32, ranks_per_task=7),
     "prefix": dict(mapping=3),
     "prefix_r1": dict(mapping=3, ranks_per_task=1, threads_per_block=64),
+    "prefix2": dict(mapping=3, prefix_depth=2),
+    "prefix3": dict(mapping=3, prefix_depth=3),
+    "prefix3_r1": dict(mapping=3, prefix_depth=3, ranks_per_task=1, threads_per_block=64),
 }
 
-FP64_LIMIT = {"thread": 8, "thread_l13": 8, "prefix": 10, "prefix_r1": 10}
-MIXED_LIMIT = {"thread": 12, "thread_l13": 12, "prefix": 12, "prefix_r1": 12}
+FP64_LIMIT = {"thread": 8, "thread_l13": 8, "prefix": 10, "prefix_r1": 10, "prefix2": 10, "prefix3": 10,
+              "prefix3_r1": 10}
+MIXED_LIMIT = {"thread": 12, "thread_l13": 12, "prefix": 12, "prefix_r1": 12, "prefix2": 12, "prefix3": 12,
+               "prefix3_r1": 12}
 
 
 # ---------------------------------------------------------------------------
@@ -129,6 +134,12 @@ TERM_CASES = [
     (8, 13, np.float32, "prefix_r1"),
     (10, 14, np.float64, "prefix"),
     (12, 15, np.float64, "prefix"),
+    (4, 11, np.float64, "prefix3"),
+    (5, 14, np.int32, "prefix3_r1"),
+    (8, 14, np.float64, "prefix3"),
+    (8, 13, np.float32, "prefix2"),
+    (10, 15, np.float64, "prefix3"),
+    (12, 16, np.float64, "prefix3"),
 ]
 
 
@@ -221,31 +232,37 @@ def _mapping_ok(mapping, m, n, limits):
         return m <= 32
     if mapping == "prefix":
         return 3 <= m <= limits["prefix"] and m <= n
+    if mapping == "prefix3":
+        return 4 <= m <= limits["prefix"] and m <= n
     return m <= limits["thread"]
 
 
-@pytest.mark.parametrize("mapping", ["auto", "thread", "group", "prefix"])
+def _det_opts(mapping):
+    return dict(mapping=3, prefix_depth=3) if mapping == "prefix3" else dict(mapping=mapping)
+
+
+@pytest.mark.parametrize("mapping", ["auto", "thread", "group", "prefix", "prefix3"])
 @pytest.mark.parametrize("m,n,dtype", DET_CASES)
 def test_det_fp64_small(m, n, dtype, mapping):
     if not _mapping_ok(mapping, m, n, FP64_LIMIT):
         pytest.skip("mapping does not cover this shape")
     a = _matrix(m, n, dtype, 400 + m * n)
     val, abs_sum = _exact(a)
-    res = R().det(a, mode="fp64", options=dict(mapping=mapping))
+    res = R().det(a, mode="fp64", options=_det_opts(mapping))
     assert res["minors"] == (math.comb(n, m) if m <= n else 0)
     assert abs(Fraction(res["value"]) - val) <= Fraction(1e-12) * abs_sum
     if abs_sum:
         assert abs(res["abs_sum"] - float(abs_sum)) <= 1e-12 * float(abs_sum)
 
 
-@pytest.mark.parametrize("mapping", ["auto", "thread", "group", "prefix"])
+@pytest.mark.parametrize("mapping", ["auto", "thread", "group", "prefix", "prefix3"])
 @pytest.mark.parametrize("m,n,dtype", DET_CASES)
 def test_det_mixed_small(m, n, dtype, mapping):
     if not _mapping_ok(mapping, m, n, MIXED_LIMIT):
         pytest.skip("mapping does not cover this shape")
     a = _matrix(m, n, dtype, 500 + m * n)
     val, abs_sum = _exact(a)
-    res = R().det(a, mode="mixed", options=dict(mapping=mapping))
+    res = R().det(a, mode="mixed", options=_det_opts(mapping))
     if m > n:
         assert res["value"] == 0.0 and res["minors"] == 0
         return
@@ -296,7 +313,7 @@ def test_det_is_deterministic():
         assert v1 == v2
 
 
-@pytest.mark.parametrize("key", ["thread", "g16", "prefix"])
+@pytest.mark.parametrize("key", ["thread", "g16", "prefix2", "prefix3"])
 def test_mixed_growth_flag_recomputes_in_binary64(key):
     # Partial pivoting grows the last column of this minor to 2^(m-1) times
     # its entries (Wilkinson's example), above the default threshold 64.
@@ -311,11 +328,13 @@ def test_mixed_growth_flag_recomputes_in_binary64(key):
     assert abs(res["value"] - float(val)) <= 8 * m * U32 * h
 
 
-@pytest.mark.parametrize("mapping", ["thread", "prefix"])
+@pytest.mark.parametrize("mapping", ["thread", "prefix", "prefix3"])
 def test_mixed_flag_list_overflow_falls_back_to_binary64(mapping):
     a = W.uniform_matrix(12, 6, 14)
     val, abs_sum = _exact(a)
-    res = R().det(a, mode="mixed", options=dict(mapping=mapping, flag_capacity=1, growth_threshold=1e-30))
+    opts = _det_opts(mapping)
+    opts.update(flag_capacity=1, growth_threshold=1e-30)
+    res = R().det(a, mode="mixed", options=opts)
     assert res["flagged"] == math.comb(14, 6)
     assert abs(res["value"] - float(val)) <= 1e-12 * float(abs_sum)
 
@@ -360,10 +379,10 @@ def fp64_8x32():
     return a, orc.radic_det_pfaffian(a)
 
 
-@pytest.mark.parametrize("mapping", ["auto", "thread"])
+@pytest.mark.parametrize("mapping", ["auto", "thread", "prefix", "prefix3"])
 def test_full_fp64_8x32_binary64(fp64_8x32, mapping):
     a, exact = fp64_8x32
-    res = R().det(a, mode="fp64", options=dict(mapping=mapping))
+    res = R().det(a, mode="fp64", options=_det_opts(mapping))
     assert res["minors"] == 10_518_300
     assert abs(Fraction(res["value"]) - exact) <= Fraction(1e-12) * Fraction(res["abs_sum"])
     # sum|terms| against a seeded sample of exact minors (unbiased estimate)
@@ -376,7 +395,7 @@ def test_full_fp64_8x32_binary64(fp64_8x32, mapping):
 @pytest.mark.parametrize("mapping", ["auto", "thread"])
 def test_full_fp64_8x32_mixed(fp64_8x32, mapping):
     a, exact = fp64_8x32
-    res = R().det(a, mode="mixed", options=dict(mapping=mapping))
+    res = R().det(a, mode="mixed", options=_det_opts(mapping))
     rel = abs(float(Fraction(res["value"]) - exact)) / res["abs_sum"]
     assert rel <= 1e-10, rel
 
