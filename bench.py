@@ -3,10 +3,11 @@
 
 One step = one det_R call over the 8 x 32 binary64 workload (C(32,8) =
 10,518,300 signed minors): stage A and the binomial table, unrank, successor,
-gather, binary32 partial-pivot LU, sign, compensated accumulation, binary64
-recompute of flagged minors, fixed-order reduction.  The headline `value` is
-signed minors per second of this mixed path, beside the plain binary64 kernel
-on the same input, the relative error of each against the exact value
+gather, binary32 partial-pivot LU (shared per column prefix), sign,
+compensated accumulation, binary64 recompute of flagged minors, fixed-order
+reduction.  The headline `value` is signed minors per second of this mixed
+path, beside the plain binary64 kernel and the pair (float-float) path on the
+same input, the relative error of each against the exact value
 (|err| / sum|terms|), and the fraction of the binary32 FMA roofline.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -184,23 +185,45 @@ def max_over_ranks(total_ms: float, device=None) -> float:
     return float(t.item())
 
 
-def prefix_flops(m: int, n: int) -> int:
-    """Algorithmic flops (2 per FMA, 1 per add or multiply) of the prefix-sharing path.
+def prefix_ops(m: int, n: int, D: int) -> dict:
+    """Operation counts of the prefix-sharing path with depth D (2 or 3).
 
-    Per (m-2)-column prefix: the partial-pivot elimination of its m x (m-2)
-    matrix, the product of pivots and W = -L21 L11^-1; per candidate column:
-    its two Schur-complement entries and the scale; per leaf minor: the 2 x 2
-    determinant (one multiply, one FMA) and two additions into the sums.
+    Per (m-D)-column prefix: the partial-pivot elimination of its m x (m-D)
+    matrix (multipliers and FMA updates), the product of pivots and
+    W = -L21 L11^-1 (FMAs); per candidate column: its D Schur-complement
+    entries (FMAs) and the scale (a multiply); per column pair (D = 3): a cross
+    product (three multiplies, three FMAs); per leaf minor: the D x D
+    determinant (D = 2: a multiply and an FMA; D = 3: a multiply and two
+    FMAs) and two additions into the sums (signed and absolute).
     """
-    P = m - 2
-    f_pre = sum((m - k - 1) + 2 * (m - k - 1) * (P - k - 1) for k in range(P)) + P + 2 * P * (P - 1)
-    f_col = 4 * P + 1
-    f_leaf = 5
-    total = 0
-    for v in range(P - 1, n - 2):
+    P = m - D
+    pre = {"fma": sum((m - k - 1) * (P - k - 1) for k in range(P)) + D * P * (P - 1) // 2,
+           "mul": sum(m - k - 1 for k in range(P)) + P, "add": 0}
+    col = {"fma": D * P, "mul": 1, "add": 0}
+    pair = {"fma": 3, "mul": 3, "add": 0} if D == 3 else {"fma": 0, "mul": 0, "add": 0}
+    leaf = {"fma": D - 1, "mul": 1, "add": 2}
+    tot = {"fma": 0, "mul": 0, "add": 0}
+    for v in range(P - 1, n - D):
         k = n - 1 - v
-        total += math.comb(v, P - 1) * (f_pre + k * f_col + math.comb(k, 2) * f_leaf)
-    return total
+        cnt = math.comb(v, P - 1)
+        for key in tot:
+            tot[key] += cnt * (pre[key] + k * col[key] + math.comb(k, 2) * pair[key] + math.comb(k, D) * leaf[key])
+    return tot
+
+
+def prefix_flops(m: int, n: int, D: int) -> int:
+    """Algorithmic binary32 (or binary64) flops of the prefix path: 2 per FMA, 1 per add or multiply."""
+    c = prefix_ops(m, n, D)
+    return 2 * c["fma"] + c["mul"] + c["add"]
+
+
+def pair_flops(m: int, n: int, D: int) -> int:
+    """The same operations in pairs of binary32, counted in binary32 flops of the pair
+    algorithms: multiply-add 18 (exact product 7, TwoSum 6, low parts 2, Fast2Sum 3),
+    multiply 10, addition 11; the absolute-value sum stays one binary32 add per leaf."""
+    c = prefix_ops(m, n, D)
+    leaves = c["add"] // 2
+    return 18 * c["fma"] + 10 * c["mul"] + 11 * leaves + leaves
 
 
 def golden_list(name: str) -> list:
@@ -366,6 +389,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     per_minor = Path("mixed", "thread")
     fp64_plain = Path("fp64", "thread")
     fp64_prefix = Path("fp64", "auto")
+    pair_prefix = Path("pair", "auto")
+    depth = {p.mode: R.radic_plan_info(M, N, p.mode, p.opts)["prefix_depth"] for p in (head, fp64_prefix, pair_prefix)}
 
     sampler = ClockSampler(local_rank)
     head.timed(args.warmup, kernel_events=False)
@@ -392,7 +417,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     side = {}
     for name, path, steps in [("per_minor_mixed", per_minor, max(5, args.steps // 2)),
                               ("fp64_plain", fp64_plain, max(3, args.steps // 5)),
-                              ("fp64_prefix", fp64_prefix, max(5, args.steps // 2))]:
+                              ("fp64_prefix", fp64_prefix, max(5, args.steps // 2)),
+                              ("pair_prefix", pair_prefix, max(5, args.steps // 2))]:
         path.timed(2, kernel_events=False)
         s_ms, k_ms = path.timed(steps)
         res = path.result()
@@ -400,6 +426,11 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
                       "kernel_ms": statistics.mean(k_ms), "flagged": res["flagged"]}
     pm = side["per_minor_mixed"]
     pm["fma_frac"] = FLOP_PER_MINOR * MINORS / (pm["kernel_ms"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS
+    pp = side["pair_prefix"]
+    pp["prefix_depth"] = depth["pair"]
+    pp["fma_frac"] = pair_flops(M, N, depth["pair"]) / (pp["kernel_ms"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS
+    pp["speedup_over_fp64_prefix"] = pp["value"] / side["fp64_prefix"]["value"]
+    side["fp64_prefix"]["prefix_depth"] = depth["fp64"]
     side["fp64_plain"]["speedup_of_headline"] = value / world / side["fp64_plain"]["value"]
 
     # end to end through the public API from pinned host memory
@@ -422,7 +453,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     e2e_rate = world * MINORS / (statistics.mean(e2e_ms) / 1e3)
 
     kern_mean_ms = statistics.mean(kern_ms)
-    flops = prefix_flops(M, N)
+    flops = prefix_flops(M, N, depth["mixed"])
     achieved = flops / (kern_mean_ms / 1e3) / 1e12
 
     configs = measure_configs(R, W, torch) if (rank == 0 and not args.headline_only) else None
@@ -442,14 +473,15 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "m": M, "n": N, "minors": MINORS, "mode": "mixed",
-                       "mapping": "prefix (binary32 elimination shared per 6-column prefix, binary64 sums)",
+                       "mapping": f"prefix depth {depth['mixed']} (binary32 elimination shared per "
+                                  f"{M - depth['mixed']}-column prefix, binary64 sums)",
                        "l2": "flushed between timed iterations (256 MB write, untimed)",
                        "parallelism": f"replicas{world}"},
             "rel_err": res_head["rel_err"], "flagged": res_head["flagged"],
             **side,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "k_fp_prefix<float,8,mixed>", "kernel_ms": kern_mean_ms,
+                         "kernel": f"k_fp_prefix<float,8,{depth['mixed']},mixed>", "kernel_ms": kern_mean_ms,
                          "flop_per_launch": flops,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (derived)"},
             "clocks": clocks,

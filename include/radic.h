@@ -70,8 +70,13 @@ enum { RADIC_I8 = 0, RADIC_I32 = 1, RADIC_F32 = 2, RADIC_F64 = 3 };
  *           run of ranks, then binary64 two-sum across runs and blocks).
  *  EXACT -- integer inputs only: LU modulo 31-bit primes (as many as a
  *           Hadamard bound needs, at most RADIC_MAX_PRIMES) and Chinese
- *           remaindering to a signed 128-bit integer, bit-exact. */
-enum { RADIC_MODE_FP64 = 0, RADIC_MODE_MIXED = 1, RADIC_MODE_EXACT = 2 };
+ *           remaindering to a signed 128-bit integer, bit-exact.
+ *  PAIR  -- the MIXED scheme with the elimination carried out in pairs of
+ *           binary32 numbers (hi + lo, about 48 significant bits, on the
+ *           binary32 pipe): PREFIX mapping, 3 <= m <= 10; flagged prefixes
+ *           are recomputed in binary64.  Also the value of a batched
+ *           result's `tier` field for matrices routed to pairs. */
+enum { RADIC_MODE_FP64 = 0, RADIC_MODE_MIXED = 1, RADIC_MODE_EXACT = 2, RADIC_MODE_PAIR = 3 };
 
 /* Minor-to-thread mapping.
  *  THREAD -- one thread factors one minor in registers (m <= 8 for FP64,
@@ -145,6 +150,16 @@ int radic_primes(uint32_t* primes, int max_count);
  * for invalid arguments. */
 size_t radic_workspace_bytes(int m, int n, int mode, const radic_options* opts);
 
+/* The launch plan radic_det would use for this shape, mode and options,
+ * written to the first `count` (<= RADIC_PLAN_INFO_COUNT) entries of host
+ * array info: [0] mapping (RADIC_MAP_THREAD, _GROUP or _PREFIX), [1] prefix
+ * depth (0 unless PREFIX), [2] group width (0 unless GROUP), [3] threads per
+ * block, [4] blocks of the main kernel, [5] ranks per processor run (THREAD,
+ * GROUP) or warp tasks (PREFIX), [6] dynamic shared memory bytes of the main
+ * kernel, [7] workspace bytes.  Same errors as radic_det's planning. */
+#define RADIC_PLAN_INFO_COUNT 8
+int radic_plan_info(int m, int n, int mode, const radic_options* opts, int64_t* info, int count);
+
 /* det_R(A) of one m x n matrix (Eq. (1)).
  * A:        device, m x n, row-major with leading dimension lda, type dtype.
  * out:      device, one radic_result, fully overwritten.
@@ -205,17 +220,22 @@ typedef struct radic_batch_tuning {
   double growth_threshold; /* MIXED: growth flag threshold (default 64)         */
   int32_t blocks_per_sm;   /* cap on resident blocks per SM (0: occupancy)     */
   int32_t prefix_depth[RADIC_MAX_M + 1]; /* 2, 3, or 0 for the default rule */
-  int32_t reserved[7];
+  int32_t tiers;           /* MIXED: allowed low tiers, bit 0 binary32, bit 1
+                              pairs (0: both); binary64 is always allowed  */
+  int32_t reserved[6];
 } radic_batch_tuning;
 
 /* Builds the plan of `batch` matrices: matrix b is m[b] x n[b], row-major
  * with leading dimension n[b], starting offsets[b] elements into one packed
  * buffer (all three arrays are host memory).  mode is RADIC_MODE_FP64 or
- * RADIC_MODE_MIXED.  In MIXED mode each matrix is routed to binary32
- * elimination (binary64 sums, binary64 recompute of flagged tasks) when the
- * expected binary32 error, 2.5e-6 / sqrt(C(n,m)) relative to sum|terms|
- * (an envelope of measured errors on random inputs), meets tuning->tol, and
- * to binary64 otherwise; the result's `tier` field tells which.  The work of every matrix is cut into warp tasks
+ * RADIC_MODE_MIXED.  In MIXED mode each matrix is routed to the cheapest
+ * allowed tier whose expected error relative to sum|terms| meets
+ * tuning->tol: binary32 elimination when 2.5e-6 / sqrt(C(n,m)) meets it,
+ * else pairs of binary32 (m >= 3) when 1e-11 / sqrt(C(n,m)) meets it, else
+ * binary64 (the constants are envelopes of measured errors on random
+ * inputs).  Binary32 and pair tasks that meet a growth flag are redone in
+ * binary64.  The result's `tier` field holds RADIC_MODE_MIXED (binary32),
+ * RADIC_MODE_PAIR or RADIC_MODE_FP64.  The work of every matrix is cut into warp tasks
  * (runs of prefixes or of dictionary ranks, per the tuning) for persistent
  * kernels with atomic work queues, one per tier and m, followed by a
  * per-matrix fixed-order reduction.  Limits: 1 <= m <= 10, n <= 64.
@@ -229,9 +249,15 @@ int radic_batch_plan_destroy(radic_batch_plan* plan);
 /* Workspace bytes the plan needs (256-byte aligned device memory). */
 size_t radic_batch_workspace_bytes(const radic_batch_plan* plan);
 
-/* info (host, 8 entries): tasks of the binary32 and binary64 tiers,
- * matrices routed to each tier, minors in each tier, persistent grid sizes. */
-int radic_batch_plan_info(const radic_batch_plan* plan, int64_t* info);
+/* Writes the first `count` (<= RADIC_BATCH_INFO_COUNT) entries of the plan
+ * summary to host array info: [0] tasks binary32, [1] tasks binary64,
+ * [2] matrices binary32, [3] matrices binary64, [4] minors binary32,
+ * [5] minors binary64, [6] largest persistent grid binary32, [7] same for
+ * binary64, [8] tasks pairs, [9] matrices pairs, [10] minors pairs,
+ * [11] largest persistent grid pairs.  RADIC_EINVAL on a null pointer or a
+ * count outside 0..RADIC_BATCH_INFO_COUNT. */
+#define RADIC_BATCH_INFO_COUNT 12
+int radic_batch_plan_info(const radic_batch_plan* plan, int64_t* info, int count);
 
 /* Copies the plan's task tables into `workspace` (once per workspace, before
  * the first batched call or graph capture).  Waits for the copies. */

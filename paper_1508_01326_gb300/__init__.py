@@ -17,6 +17,7 @@ from .api import (  # noqa: F401
     new_result,
     parse_result,
     radic_det,
+    radic_plan_info,
     radic_primes,
     radic_status_string,
     radic_terms,

@@ -14,7 +14,7 @@ RADIC_MAX_PRIMES = 4
 STATUS = {0: "RADIC_OK", 1: "RADIC_EINVAL", 2: "RADIC_EOVERFLOW", 3: "RADIC_ECUDA", 4: "RADIC_ETIMEOUT",
           5: "RADIC_EWORKSPACE", 6: "RADIC_EUNSUPPORTED"}
 DTYPES = {"int8": 0, "int32": 1, "float32": 2, "float64": 3}
-MODES = {"fp64": 0, "mixed": 1, "exact": 2}
+MODES = {"fp64": 0, "mixed": 1, "exact": 2, "pair": 3}
 MAPPINGS = {"auto": 0, "thread": 1, "group": 2, "prefix": 3}
 
 
@@ -45,7 +45,8 @@ class RadicBatchTuning(ctypes.Structure):
         ("growth_threshold", ctypes.c_double),
         ("blocks_per_sm", ctypes.c_int32),
         ("prefix_depth", ctypes.c_int32 * (RADIC_MAX_M + 1)),
-        ("reserved", ctypes.c_int32 * 7),
+        ("tiers", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 _lib = None
@@ -95,7 +96,8 @@ def _declare_optional(L: ctypes.CDLL) -> None:
     table = {
         "radic_batch_plan_create": ([vp, vp, vp, i32, i32, vp, pp], i32),
         "radic_batch_plan_destroy": ([vp], i32),
-        "radic_batch_plan_info": ([vp, ctypes.POINTER(i64)], i32),
+        "radic_batch_plan_info": ([vp, ctypes.POINTER(i64), i32], i32),
+        "radic_plan_info": ([i32, i32, i32, ctypes.POINTER(RadicOptions), ctypes.POINTER(i64), i32], i32),
         "radic_batch_workspace_bytes": ([vp], sz),
         "radic_batch_upload": ([vp, vp, sz, vp], i32),
         "radic_det_batched": ([vp, vp, i32, vp, vp, sz, vp], i32),

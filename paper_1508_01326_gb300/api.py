@@ -63,6 +63,21 @@ def radic_workspace_bytes(m: int, n: int, mode="fp64", options=None) -> int:
     return int(L.lib().radic_workspace_bytes(int(m), int(n), _mode(mode), _opts(options)))
 
 
+PLAN_INFO_KEYS = ["mapping", "prefix_depth", "group_width", "threads", "blocks", "run_or_tasks", "smem_bytes",
+                  "workspace_bytes"]
+MAPPING_NAMES = {1: "thread", 2: "group", 3: "prefix"}
+
+
+def radic_plan_info(m: int, n: int, mode="fp64", options=None) -> dict:
+    """The launch plan radic_det would use (host only, no launch)."""
+    buf = (ctypes.c_int64 * len(PLAN_INFO_KEYS))()
+    opts = _opts(options)
+    L.check("radic_plan_info", L.lib().radic_plan_info(int(m), int(n), _mode(mode), opts, buf, len(buf)))
+    info = dict(zip(PLAN_INFO_KEYS, [int(x) for x in buf]))
+    info["mapping"] = MAPPING_NAMES.get(info["mapping"], info["mapping"])
+    return info
+
+
 def new_result(device=None) -> torch.Tensor:
     """Device buffer for one radic_result (sixteen int64 words)."""
     return torch.empty(L.RESULT_WORDS, dtype=torch.int64, device=device or "cuda")
@@ -154,11 +169,22 @@ def det(A, mode="fp64", options=None, stream=None) -> dict:
 # ---------------------------------------------------------------------------
 
 
+TIERS = {"fp32": 1, "pair": 2}
+
+
 def make_tuning(kind=None, task_cost=None, tol=0.0, growth_threshold=0.0, blocks_per_sm=0,
-                prefix_depth=None) -> "L.RadicBatchTuning":
+                prefix_depth=None, tiers=None) -> "L.RadicBatchTuning":
     """Batched-path tuning: `kind`, `task_cost` and `prefix_depth` map m to a mapping name, a task size
-    and a prefix depth (2 or 3)."""
+    and a prefix depth (2 or 3); `tiers` lists the low tiers the mixed router may use ("fp32",
+    "pair"; default both; binary64 is always available)."""
     t = L.RadicBatchTuning()
+    if tiers is not None:
+        mask = 0
+        for name in tiers:
+            mask |= TIERS[name]
+        if mask == 0:
+            raise ValueError("tiers must name at least one of " + ", ".join(TIERS))
+        t.tiers = mask
     for m, d in (prefix_depth or {}).items():
         t.prefix_depth[int(m)] = int(d)
     for m, k in (kind or {}).items():
@@ -204,12 +230,13 @@ class BatchPlan:
         L.check("radic_batch_upload", rc)
         self._graphs = []
 
+    INFO_KEYS = ["tasks_fp32", "tasks_fp64", "matrices_fp32", "matrices_fp64", "minors_fp32", "minors_fp64",
+                 "blocks_fp32", "blocks_fp64", "tasks_pair", "matrices_pair", "minors_pair", "blocks_pair"]
+
     def info(self) -> dict:
-        buf = (ctypes.c_int64 * 8)()
-        L.check("radic_batch_plan_info", L.lib().radic_batch_plan_info(self._plan, buf))
-        keys = ["tasks_fp32", "tasks_fp64", "matrices_fp32", "matrices_fp64", "minors_fp32", "minors_fp64",
-                "blocks_fp32", "blocks_fp64"]
-        return dict(zip(keys, [int(x) for x in buf]))
+        buf = (ctypes.c_int64 * len(self.INFO_KEYS))()
+        L.check("radic_batch_plan_info", L.lib().radic_batch_plan_info(self._plan, buf, len(self.INFO_KEYS)))
+        return dict(zip(self.INFO_KEYS, [int(x) for x in buf]))
 
     def new_results(self) -> torch.Tensor:
         return torch.empty((self.batch, L.RESULT_WORDS), dtype=torch.int64, device=self.workspace.device)

@@ -23,6 +23,7 @@ SOURCES = [
     "radic_api.cu",
     "radic_fp64.cu",
     "radic_mixed.cu",
+    "radic_pair.cu",
     "radic_modp.cu",
     "radic_noalloc.cu",
     "radic_batched.cu",

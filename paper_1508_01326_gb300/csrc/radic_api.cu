@@ -25,9 +25,10 @@ int device_sm_count() {
 namespace {
 
 bool valid_dtype(int d) { return d == kI8 || d == kI32 || d == kF32 || d == kF64; }
-bool valid_mode(int md) { return md == kModeFp64 || md == kModeMixed || md == kModeExact; }
+bool valid_mode(int md) { return md == kModeFp64 || md == kModeMixed || md == kModeExact || md == kModePair; }
 
 int thread_limit(int mode) {
+  if (mode == kModePair) return 0;  // prefix mapping only
   return mode == kModeFp64 ? kThreadMaxMFp64 : (mode == kModeMixed ? kThreadMaxMFp32 : kThreadMaxMModp);
 }
 
@@ -35,6 +36,7 @@ int blocks_per_sm(const SinglePlan& p) {
   switch (p.mode) {
     case kModeFp64: return blocks_per_sm_fp64(p);
     case kModeMixed: return blocks_per_sm_mixed(p);
+    case kModePair: return blocks_per_sm_pair(p);
     default: return blocks_per_sm_modp(p);
   }
 }
@@ -43,6 +45,7 @@ size_t smem_of(const SinglePlan& p) {
   switch (p.mode) {
     case kModeFp64: return smem_fp64(p);
     case kModeMixed: return smem_mixed(p);
+    case kModePair: return smem_pair(p);
     default: return smem_modp(p);
   }
 }
@@ -110,20 +113,24 @@ int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long
   pl.n = n;
   pl.total = (m <= n) ? binom_host(n, m) : 0ull;
   const int auto_limit = (mode == kModeExact) ? kThreadMaxMModp : 8;
-  const int prefix_limit = (mode == kModeFp64) ? kPrefixMaxMFp64 : (mode == kModeMixed ? kPrefixMaxMFp32 : 0);
+  const int prefix_limit = (mode == kModeFp64)    ? kPrefixMaxMFp64
+                           : (mode == kModeMixed) ? kPrefixMaxMFp32
+                           : (mode == kModePair)  ? kPrefixMaxMPair
+                                                  : 0;
   int mapping = d.mapping;
   if (mapping == RADIC_MAP_AUTO) {
     if (m >= 3 && m <= prefix_limit && m <= n) mapping = RADIC_MAP_PREFIX;
     else mapping = (m <= auto_limit ? RADIC_MAP_THREAD : RADIC_MAP_GROUP);
   }
   if (mapping != RADIC_MAP_THREAD && mapping != RADIC_MAP_GROUP && mapping != RADIC_MAP_PREFIX) return RADIC_EINVAL;
+  if (mode == kModePair && mapping != RADIC_MAP_PREFIX) return RADIC_EUNSUPPORTED;
   if (mapping == RADIC_MAP_THREAD && m > thread_limit(mode)) return RADIC_EUNSUPPORTED;
   if (mapping == RADIC_MAP_PREFIX && (m < 3 || m > prefix_limit || m > n)) return RADIC_EUNSUPPORTED;
   pl.mapping = mapping;
   if (mapping == RADIC_MAP_PREFIX) {
     if (d.prefix_depth != 0 && d.prefix_depth != 2 && d.prefix_depth != 3) return RADIC_EINVAL;
     if (d.prefix_depth == 3 && m < 4) return RADIC_EUNSUPPORTED;
-    pl.depth = d.prefix_depth ? d.prefix_depth : prefix_auto_depth(m, n, mode == RADIC_MODE_FP64 ? 8 : 4);
+    pl.depth = d.prefix_depth ? d.prefix_depth : prefix_auto_depth(m, n, mode == kModeMixed ? 4 : 8);
   }
   if (mapping == RADIC_MAP_GROUP) {
     const int gw = d.group_width ? d.group_width : (m <= 16 ? 16 : 32);
@@ -178,7 +185,7 @@ void layout_workspace(SinglePlan& pl) {
   size_t off = 256;
   pl.off_partials = off;
   off = align_up(off + (size_t)pl.blocks * sizeof(FpPartial), 256);
-  if (mode == kModeMixed) {
+  if (mode == kModeMixed || mode == kModePair) {
     pl.off_partials2 = off;
     off = align_up(off + (size_t)pl.blocks2 * sizeof(FpPartial), 256);
     pl.off_flag_count = off;
@@ -327,6 +334,25 @@ size_t radic_workspace_bytes(int m, int n, int mode, const radic_options* opts) 
   return p.ws_bytes;
 }
 
+int radic_plan_info(int m, int n, int mode, const radic_options* opts, int64_t* info, int count) {
+  if ((!info && count > 0) || count < 0 || count > RADIC_PLAN_INFO_COUNT) return RADIC_EINVAL;
+  SinglePlan p;
+  const int rc =
+      make_plan(m, n, mode, opts, (m <= n && n <= kMaxN && m >= 1 && n >= 1) ? binom_host(n, m) : 0ull, &p);
+  if (rc != RADIC_OK) return rc;
+  int64_t v[RADIC_PLAN_INFO_COUNT];
+  v[0] = p.mapping;
+  v[1] = (p.mapping == RADIC_MAP_PREFIX) ? p.depth : 0;
+  v[2] = (p.mapping == RADIC_MAP_GROUP) ? p.group : 0;
+  v[3] = p.threads;
+  v[4] = p.blocks;
+  v[5] = (p.mapping == RADIC_MAP_PREFIX) ? (int64_t)p.ptab.total_tasks : (int64_t)p.ranks_per_task;
+  v[6] = (int64_t)p.smem;
+  v[7] = (int64_t)p.ws_bytes;
+  for (int i = 0; i < count; ++i) info[i] = v[i];
+  return RADIC_OK;
+}
+
 int radic_det(const void* A, int m, int n, int64_t lda, int dtype, int mode, const radic_options* opts,
               radic_result* out, void* workspace, size_t workspace_bytes, void* stream) {
   if (!A || !out || lda < n || !valid_dtype(dtype)) return RADIC_EINVAL;
@@ -369,6 +395,7 @@ int radic_det(const void* A, int m, int n, int64_t lda, int dtype, int mode, con
   switch (mode) {
     case kModeFp64: r = launch_fp64(p, a, s); break;
     case kModeMixed: r = launch_mixed(p, a, s); break;
+    case kModePair: r = launch_pair(p, a, s); break;
     default: r = launch_modp(p, a, s); break;
   }
   return r;
@@ -404,6 +431,7 @@ int radic_terms(const void* A, int m, int n, int64_t lda, int dtype, int mode, c
   switch (mode) {
     case kModeFp64: return launch_fp64(p, a, s);
     case kModeMixed: return launch_mixed(p, a, s);
+    case kModePair: return launch_pair(p, a, s);
     default: return launch_modp(p, a, s);
   }
 }

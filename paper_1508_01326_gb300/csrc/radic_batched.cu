@@ -1,17 +1,18 @@
 // Batched Radic determinants: many matrices of uneven m and n in one pass.
 //
 // The host plan routes every matrix to a tier (binary32 elimination with
-// binary64 sums, or binary64) and cuts its work into warp tasks: runs of
+// binary64 sums, elimination in pairs of binary32 with binary64 sums, or
+// binary64) and cuts its work into warp tasks: runs of
 // (m-2)-column prefixes of one group (prefix mapping) or runs of dictionary
 // ranks (per-minor mapping), each with about the same estimated cost.  Tasks
 // are sorted by cost, largest first.  One persistent kernel per tier pulls
 // tasks from an atomic work queue; a warp stages its task's matrix and
 // binomial table in its own slice of shared memory, works the task (every
 // lane one contiguous run, as in the split of Section 5) and writes the
-// task's partial sum into the task's own slot.  Binary32 tasks that meet a
-// flag are appended to a list and recomputed in binary64 by the second
-// kernel into the same slot, so the result does not depend on which warp ran
-// which task.  A last kernel adds each matrix's slots in task order.
+// task's partial sum into the task's own slot.  Binary32 and pair tasks that
+// meet a flag are appended to a list and recomputed in binary64 by the
+// binary64 kernel into the same slot, so the result does not depend on which
+// warp ran which task.  A last kernel adds each matrix's slots in task order.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -27,7 +28,8 @@ namespace {
 constexpr int kBatchMaxM = 10;      // prefix mapping covers 3..10, per-minor 1..8
 constexpr int kBatchThreads = 128;  // four warps per block
 constexpr int kKindMinor = 0;       // otherwise: prefix depth (2 or 3)
-constexpr double kBinary32ErrorK = 2.5e-6;  // error model constant of the router
+constexpr double kBinary32ErrorK = 2.5e-6;  // error model constants of the router
+constexpr double kPairErrorK = 1e-11;
 
 struct BatchTask {
   long long offset;         // element offset of the matrix in the packed buffer
@@ -35,13 +37,14 @@ struct BatchTask {
   unsigned long long run;   // prefixes or ranks per lane
   unsigned long long lim;   // prefixes in the group, or C(n,m): end of the range
   int b, m, n, v;           // matrix, shape, prefix group
-  int kind, tier;           // kKindMinor or the prefix depth; kModeMixed or kModeFp64
+  int kind, tier;           // kKindMinor or the prefix depth; kModeMixed, kModePair or kModeFp64
 };
 
 struct BatchHeader {
   unsigned int q32[kBatchMaxM + 1];    // work-queue counters, binary32 tier, per m
+  unsigned int qpair[kBatchMaxM + 1];  // work-queue counters, pair tier, per m
   unsigned int q64[kBatchMaxM + 1];    // work-queue counters, binary64 tier, per m
-  unsigned int nflag[kBatchMaxM + 1];  // binary32 tasks of each m sent to binary64
+  unsigned int nflag[kBatchMaxM + 1];  // binary32 and pair tasks of each m sent to binary64
   int status;
 };
 static_assert(sizeof(BatchHeader) <= 256, "header slot");
@@ -49,13 +52,14 @@ static_assert(sizeof(BatchHeader) <= 256, "header slot");
 struct BatchArgs {
   const void* A;
   int dtype;
-  int begin32, end32;       // this m's binary32 tasks [begin32, end32)
+  int begin32, end32;       // low-tier launch: its tasks [begin32, end32) of tasks32
   int begin64, end64;       // this m's binary64 tasks
+  int flag_base;            // first entry of this m's region of `flagged`
   int n_tasks32;            // slot index of the first binary64 task
-  const BatchTask* tasks32;
+  const BatchTask* tasks32; // binary32 and pair tasks (per m: binary32 first)
   const BatchTask* tasks64;
   FpPartial* slots;         // n_tasks32 + n_tasks64
-  int* flagged;             // ids of flagged binary32 tasks, in this m's range
+  int* flagged;             // ids of flagged binary32 and pair tasks, per m
   int* escale;              // per matrix
   BatchHeader* hdr;
   double growth;
@@ -65,7 +69,7 @@ struct BatchArgs {
 struct ReduceArgs {
   const int* csr_ptr;       // batch + 1
   const int* csr_idx;       // task ids (binary32 ids first, then binary64 ids)
-  const int* tier;          // per matrix: kModeMixed or kModeFp64
+  const int* tier;          // per matrix: kModeMixed, kModePair or kModeFp64
   const int* shape;         // per matrix: m, n
   const FpPartial* slots;
   const int* escale;
@@ -114,7 +118,7 @@ __device__ int stage_warp(const BatchArgs& a, const BatchTask& t, int cs, const 
     if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
     esum += e;
     for (int j = lane; j < n; j += 32)
-      w.As[j * cs + i] = static_cast<T>(ldexp(load_elem(A, a.dtype, t.offset + (long long)i * n + j), -e));
+      w.As[j * cs + i] = to_elem<T>(ldexp(load_elem(A, a.dtype, t.offset + (long long)i * n + j), -e));
   }
   for (int idx = lane; idx < (cs - m) * n; idx += 32) {
     const int j = idx / (cs - m), i = m + (idx - j * (cs - m));
@@ -139,6 +143,11 @@ struct TaskAcc<float> {
     p.add_column(d, fabsf(d));
     p.end_prefix();
   }
+};
+
+template <>
+struct TaskAcc<ff> {  // pair tasks are prefix tasks only
+  PrefixAcc<ff> p;
 };
 
 template <typename T, int M, int D, bool kFlag>
@@ -184,8 +193,9 @@ __device__ bool run_task(const BatchArgs& a, const BatchTask& t, const WarpSlice
   } else if (t.kind == 3) {
     if constexpr (M >= 4) flagged = run_prefix<T, M, 3, kFlag>(a, t, w, acc, first, last);
   } else {
-    // per-minor mapping: binary32 up to m = 8, binary64 only for m <= 2
-    if constexpr (M <= (sizeof(T) == 8 ? 2 : 8)) {
+    // per-minor mapping, m <= 8: binary32 tasks, binary64 tasks of m <= 2 and
+    // the binary64 redo of flagged binary32 tasks; never pairs
+    if constexpr (!std::is_same<T, ff>::value && M <= 8) {
       int c[M];
       unrank<M>(first < t.lim ? first : 0ull, t.n, w.binom, M + 1, c);
       for (unsigned long long it = 0; it < t.run; ++it) {
@@ -235,11 +245,11 @@ __device__ void do_task(const BatchArgs& a, const BatchTask& t, unsigned char* s
     a.escale[t.b] = esc;
     if (kFlag && flagged) {
       const unsigned int pos = atomicAdd(&a.hdr->nflag[M], 1u);
-      a.flagged[a.begin32 + pos] = task_id;
+      a.flagged[a.flag_base + pos] = task_id;
     } else {
-      // count: minors of a binary32 task that was recomputed here in binary64
+      // count: minors of a binary32 or pair task recomputed here in binary64
       long long redone = 0;
-      if (!kFlag && t.tier == kModeMixed) {
+      if (!kFlag && t.tier != kModeFp64) {
         const unsigned long long units = min(32ull * t.run, t.lim - t.r0);
         const int D = t.kind;
         redone = (long long)(D == kKindMinor ? units : units * c_binom.v[t.n - 1 - t.v][D]);
@@ -249,10 +259,10 @@ __device__ void do_task(const BatchArgs& a, const BatchTask& t, unsigned char* s
   }
 }
 
-// Persistent kernel of one tier and one m.  Binary32 tier: queue over this
-// m's binary32 tasks.  Binary64 tier: queue over this m's binary64 tasks, then
-// over this m's binary32 tasks that were flagged (their slots are
-// overwritten with binary64 sums).
+// Persistent kernel of one tier and one m.  Binary32 (T = float) and pair
+// (T = ff) tiers: queue over this m's tasks of that tier.  Binary64 tier:
+// queue over this m's binary64 tasks, then over this m's binary32 and pair
+// tasks that were flagged (their slots are overwritten with binary64 sums).
 template <typename T, bool kMixedTier, int M>
 __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -260,7 +270,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a) {
   unsigned char* slice = smem_raw + (size_t)warp * a.slice_bytes;
   const int own = kMixedTier ? a.end32 - a.begin32 : a.end64 - a.begin64;
   const int total = kMixedTier ? own : own + (int)__ldcg(&a.hdr->nflag[M]);
-  unsigned int* counter = kMixedTier ? &a.hdr->q32[M] : &a.hdr->q64[M];
+  unsigned int* counter =
+      kMixedTier ? (std::is_same<T, ff>::value ? &a.hdr->qpair[M] : &a.hdr->q32[M]) : &a.hdr->q64[M];
   for (;;) {
     unsigned int i = 0;
     if (lane == 0) i = atomicAdd(counter, 1u);
@@ -273,7 +284,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs a) {
       const int id = a.begin64 + (int)i;
       do_task<T, M, false>(a, a.tasks64[id], slice, id, a.n_tasks32 + id);
     } else {
-      const int id = __ldcg(&a.flagged[a.begin32 + (int)i - own]);
+      const int id = __ldcg(&a.flagged[a.flag_base + (int)i - own]);
       BatchTask t = a.tasks32[id];
       do_task<T, M, false>(a, t, slice, id, id);
     }
@@ -319,19 +330,25 @@ __global__ void __launch_bounds__(128) k_batch_reduce(ReduceArgs r) {
   }
 }
 
+template <typename T, bool kMixed, int M>
+const void* batch_kernel_m() {
+  if constexpr (std::is_same<T, ff>::value && M < 3) return nullptr;  // pairs: prefix tasks, m >= 3
+  else return reinterpret_cast<const void*>(&k_batch<T, kMixed, M>);
+}
+
 template <typename T, bool kMixed>
 const void* batch_kernel(int m) {
   switch (m) {
-    case 1: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 1>);
-    case 2: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 2>);
-    case 3: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 3>);
-    case 4: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 4>);
-    case 5: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 5>);
-    case 6: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 6>);
-    case 7: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 7>);
-    case 8: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 8>);
-    case 9: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 9>);
-    case 10: return reinterpret_cast<const void*>(&k_batch<T, kMixed, 10>);
+    case 1: return batch_kernel_m<T, kMixed, 1>();
+    case 2: return batch_kernel_m<T, kMixed, 2>();
+    case 3: return batch_kernel_m<T, kMixed, 3>();
+    case 4: return batch_kernel_m<T, kMixed, 4>();
+    case 5: return batch_kernel_m<T, kMixed, 5>();
+    case 6: return batch_kernel_m<T, kMixed, 6>();
+    case 7: return batch_kernel_m<T, kMixed, 7>();
+    case 8: return batch_kernel_m<T, kMixed, 8>();
+    case 9: return batch_kernel_m<T, kMixed, 9>();
+    case 10: return batch_kernel_m<T, kMixed, 10>();
     default: return nullptr;
   }
 }
@@ -349,18 +366,21 @@ struct radic_batch_plan {
   std::vector<int> shape;            // m, n per matrix
   std::vector<long long> offset;
   std::vector<int> tier;
-  std::vector<BatchTask> t32, t64;   // sorted by m, then by cost (largest first)
+  std::vector<BatchTask> t32, t64;   // t32: binary32 and pair tasks; sorted by m, tier, cost (largest first)
   int begin32[kBatchMaxM + 2] = {0}, begin64[kBatchMaxM + 2] = {0};  // task ranges per m
+  int pair32[kBatchMaxM + 1] = {0};  // first pair task of m in t32 (binary32 tasks of m before it)
   std::vector<int> csr_ptr, csr_idx;
   int max_n = 1, max_m = 1;
-  int blocks32[kBatchMaxM + 1] = {0}, blocks64[kBatchMaxM + 1] = {0};
-  int slice32[kBatchMaxM + 1] = {0}, slice64[kBatchMaxM + 1] = {0};  // shared memory per warp
+  int blocks32[kBatchMaxM + 1] = {0}, blocks64[kBatchMaxM + 1] = {0}, blocksp[kBatchMaxM + 1] = {0};
+  int slice32[kBatchMaxM + 1] = {0}, slice64[kBatchMaxM + 1] = {0}, slicep[kBatchMaxM + 1] = {0};  // per warp
   double tol = 1e-10, growth = 64.0;
+  int tiers = 3;  // allowed low tiers: bit 0 binary32, bit 1 pairs
   // workspace layout
   size_t off_t32 = 0, off_t64 = 0, off_slots = 0, off_flagged = 0, off_escale = 0, off_csr_ptr = 0,
          off_csr_idx = 0, off_tier = 0, off_shape = 0, ws_bytes = 0;
-  long long n_fp32_matrices = 0, n_fp64_matrices = 0;
-  unsigned long long minors32 = 0, minors64 = 0;
+  long long n_fp32_matrices = 0, n_fp64_matrices = 0, n_pair_matrices = 0;
+  unsigned long long minors32 = 0, minors64 = 0, minors_pair = 0;
+  int tasks_pair = 0;
 };
 
 struct radic_batch_graph {
@@ -374,9 +394,9 @@ double cost_minor(int m) { return 10.0 * m * m * m / 3.0 + 40.0; }
 
 int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* tun) {
   const int m = pl.shape[2 * b], n = pl.shape[2 * b + 1];
-  std::vector<BatchTask>& out = (tier == kModeMixed) ? pl.t32 : pl.t64;
+  std::vector<BatchTask>& out = (tier == kModeFp64) ? pl.t64 : pl.t32;
   if (m > n) return RADIC_OK;
-  const int elem = (tier == kModeMixed) ? 4 : 8;
+  const int elem = (tier == kModeMixed) ? 4 : 8;  // pairs are 8 bytes like binary64
   int kind = (m >= 3) ? prefix_auto_depth(m, n, elem) : kKindMinor;
   if (tun && tun->kind[m] == RADIC_MAP_THREAD && m <= 8 && tier == kModeMixed) kind = kKindMinor;
   if (tun && tun->kind[m] == RADIC_MAP_PREFIX && m >= 3) kind = prefix_auto_depth(m, n, elem);
@@ -453,12 +473,13 @@ int enqueue(const radic_batch_plan* pl, const void* A, int dtype, radic_result* 
   a.escale = reinterpret_cast<int*>(ws + pl->off_escale);
   a.hdr = reinterpret_cast<BatchHeader*>(ws);
   a.growth = pl->growth;
-  // binary32 tier, one persistent kernel per m present
+  // binary32 and pair tiers, one persistent kernel per tier and m present
   for (int m = 1; m <= kBatchMaxM; ++m) {
-    a.begin32 = pl->begin32[m];
-    a.end32 = pl->begin32[m + 1];
+    a.flag_base = pl->begin32[m];
     a.begin64 = pl->begin64[m];
     a.end64 = pl->begin64[m + 1];
+    a.begin32 = pl->begin32[m];
+    a.end32 = pl->pair32[m];
     if (a.end32 > a.begin32) {
       a.slice_bytes = pl->slice32[m];
       void* params[] = {&a};
@@ -466,9 +487,19 @@ int enqueue(const radic_batch_plan* pl, const void* A, int dtype, radic_result* 
                            (size_t)pl->slice32[m] * (kBatchThreads / 32), s) != cudaSuccess)
         return RADIC_ECUDA;
     }
+    a.begin32 = pl->pair32[m];
+    a.end32 = pl->begin32[m + 1];
+    if (a.end32 > a.begin32) {
+      a.slice_bytes = pl->slicep[m];
+      void* params[] = {&a};
+      if (cudaLaunchKernel(batch_kernel<ff, true>(m), dim3(pl->blocksp[m]), dim3(kBatchThreads), params,
+                           (size_t)pl->slicep[m] * (kBatchThreads / 32), s) != cudaSuccess)
+        return RADIC_ECUDA;
+    }
   }
-  // binary64 tier (and the flagged binary32 tasks), one kernel per m present
+  // binary64 tier (and the flagged binary32 and pair tasks), one kernel per m present
   for (int m = 1; m <= kBatchMaxM; ++m) {
+    a.flag_base = pl->begin32[m];
     a.begin32 = pl->begin32[m];
     a.end32 = pl->begin32[m + 1];
     a.begin64 = pl->begin64[m];
@@ -513,6 +544,7 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
   pl->mode = mode;
   if (tuning && tuning->tol > 0.0) pl->tol = tuning->tol;
   if (tuning && tuning->growth_threshold > 0.0) pl->growth = tuning->growth_threshold;
+  if (tuning && tuning->tiers != 0) pl->tiers = tuning->tiers & 3;
   pl->shape.resize(2 * (size_t)batch);
   pl->offset.resize(batch);
   pl->tier.resize(batch);
@@ -527,26 +559,36 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
     pl->max_n = std::max(pl->max_n, (int)n[b]);
     pl->max_m = std::max(pl->max_m, (int)m[b]);
     const unsigned long long c = (m[b] <= n[b]) ? binom_host(n[b], m[b]) : 0ull;
-    // Routing: binary32 elimination errors behave like independent rounding
-    // per minor, so the error relative to sum|terms| falls like K / sqrt(C(n,m)).
+    // Routing: elimination errors behave like independent rounding per
+    // minor, so the error relative to sum|terms| falls like K / sqrt(C(n,m)).
     // Over 4096 random N(0,1) matrices (m 2..10, n-m 1..20) K stayed below
-    // 2.1e-6 (median 1.2e-7); a matrix goes to the binary32 tier only when
-    // K = 2.5e-6 meets the target.
+    // 2.1e-6 for binary32 elimination (median 1.2e-7); a matrix goes to the
+    // binary32 tier only when K = 2.5e-6 meets the target, else to pairs
+    // when K = 1e-11 does, else to binary64.
     int tier = kModeFp64;
-    if (mode == RADIC_MODE_MIXED && c > 0 && kBinary32ErrorK / std::sqrt((double)c) <= pl->tol) tier = kModeMixed;
+    if (mode == RADIC_MODE_MIXED && c > 0) {
+      const double rs = 1.0 / std::sqrt((double)c);
+      if ((pl->tiers & 1) && kBinary32ErrorK * rs <= pl->tol) tier = kModeMixed;
+      else if ((pl->tiers & 2) && m[b] >= 3 && kPairErrorK * rs <= pl->tol) tier = kModePair;
+    }
     pl->tier[b] = tier;
     if (tier == kModeMixed) {
       pl->n_fp32_matrices++;
       pl->minors32 += c;
+    } else if (tier == kModePair) {
+      pl->n_pair_matrices++;
+      pl->minors_pair += c;
     } else {
       pl->n_fp64_matrices++;
       pl->minors64 += c;
     }
     make_tasks(*pl, b, tier, tuning);
   }
-  // per m, largest tasks first (longest-processing-time order for each queue)
+  // per m and tier (binary32 before pairs), largest tasks first
+  // (longest-processing-time order for each queue)
   auto order = [](const BatchTask& x, const BatchTask& y) {
     if (x.m != y.m) return x.m < y.m;
+    if (x.tier != y.tier) return x.tier == kModeMixed;
     return task_cost(x) > task_cost(y);
   };
   std::stable_sort(pl->t32.begin(), pl->t32.end(), order);
@@ -559,6 +601,12 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
                                             [](const BatchTask& t, int mm) { return t.m < mm; }) -
                            pl->t64.begin());
   }
+  for (int m = 0; m <= kBatchMaxM; ++m) {
+    int i = pl->begin32[m];
+    while (i < pl->begin32[m + 1] && pl->t32[i].tier == kModeMixed) ++i;
+    pl->pair32[m] = i;
+  }
+  for (const BatchTask& t : pl->t32) pl->tasks_pair += (t.tier == kModePair);
   // per-matrix task lists in task order (fixed summation order)
   std::vector<std::vector<int>> per(batch);
   for (size_t i = 0; i < pl->t32.size(); ++i) per[pl->t32[i].b].push_back((int)i);
@@ -575,9 +623,12 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
   // binary64 kernel of m also redoes flagged binary32 tasks of m)
   {
     int n32[kBatchMaxM + 1] = {0}, d32[kBatchMaxM + 1] = {0}, n64[kBatchMaxM + 1] = {0}, d64[kBatchMaxM + 1] = {0};
+    int np[kBatchMaxM + 1] = {0}, dp[kBatchMaxM + 1] = {0};
     for (const BatchTask& t : pl->t32) {
-      n32[t.m] = std::max(n32[t.m], t.n);
-      if (t.kind != kKindMinor) d32[t.m] = std::max(d32[t.m], t.kind);
+      int* nn = (t.tier == kModePair) ? np : n32;
+      int* dd = (t.tier == kModePair) ? dp : d32;
+      nn[t.m] = std::max(nn[t.m], t.n);
+      if (t.kind != kKindMinor) dd[t.m] = std::max(dd[t.m], t.kind);
     }
     for (const BatchTask& t : pl->t64) {
       n64[t.m] = std::max(n64[t.m], t.n);
@@ -590,9 +641,10 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
       return (int)align_up(b, 32);
     };
     for (int m = 1; m <= kBatchMaxM; ++m) {
-      n64[m] = std::max(n64[m], n32[m]);
-      d64[m] = std::max(d64[m], d32[m]);
+      n64[m] = std::max(n64[m], std::max(n32[m], np[m]));
+      d64[m] = std::max(d64[m], std::max(d32[m], dp[m]));
       if (n32[m] > 0) pl->slice32[m] = slice(m, n32[m], d32[m], ((m + 3) / 4) * 4, 4);
+      if (np[m] > 0) pl->slicep[m] = slice(m, np[m], dp[m], ((m + 1) / 2) * 2, 8);
       if (n64[m] > 0) pl->slice64[m] = slice(m, n64[m], d64[m], ((m + 1) / 2) * 2, 8);
     }
   }
@@ -603,8 +655,17 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
   }
   const int occ = (tuning && tuning->blocks_per_sm > 0) ? tuning->blocks_per_sm : 0;
   for (int m = 1; m <= kBatchMaxM; ++m) {
-    const bool has32 = pl->begin32[m + 1] > pl->begin32[m];
-    const bool has64 = pl->begin64[m + 1] > pl->begin64[m] || has32;
+    const bool has32 = pl->pair32[m] > pl->begin32[m];
+    const bool hasp = pl->begin32[m + 1] > pl->pair32[m];
+    const bool has64 = pl->begin64[m + 1] > pl->begin64[m] || has32 || hasp;
+    if (hasp) {
+      pl->blocksp[m] = persistent_blocks<ff, true>(m, pl->slicep[m], sms);
+      if (occ > 0) pl->blocksp[m] = std::min(pl->blocksp[m], occ * sms);
+      if (pl->blocksp[m] <= 0) {
+        delete pl;
+        return RADIC_EUNSUPPORTED;
+      }
+    }
     if (has32) {
       pl->blocks32[m] = persistent_blocks<float, true>(m, pl->slice32[m], sms);
       if (occ > 0) pl->blocks32[m] = std::min(pl->blocks32[m], occ * sms);
@@ -650,21 +711,28 @@ int radic_batch_plan_destroy(radic_batch_plan* plan) {
 
 size_t radic_batch_workspace_bytes(const radic_batch_plan* plan) { return plan ? plan->ws_bytes : 0; }
 
-int radic_batch_plan_info(const radic_batch_plan* plan, int64_t* info) {
-  if (!plan || !info) return RADIC_EINVAL;
-  info[0] = (int64_t)plan->t32.size();
-  info[1] = (int64_t)plan->t64.size();
-  info[2] = plan->n_fp32_matrices;
-  info[3] = plan->n_fp64_matrices;
-  info[4] = (int64_t)plan->minors32;
-  info[5] = (int64_t)plan->minors64;
-  int64_t b32 = 0, b64 = 0;
+int radic_batch_plan_info(const radic_batch_plan* plan, int64_t* info, int count) {
+  if (!plan || (!info && count > 0) || count < 0 || count > RADIC_BATCH_INFO_COUNT) return RADIC_EINVAL;
+  int64_t v[RADIC_BATCH_INFO_COUNT];
+  v[0] = (int64_t)plan->t32.size() - plan->tasks_pair;
+  v[1] = (int64_t)plan->t64.size();
+  v[2] = plan->n_fp32_matrices;
+  v[3] = plan->n_fp64_matrices;
+  v[4] = (int64_t)plan->minors32;
+  v[5] = (int64_t)plan->minors64;
+  int64_t b32 = 0, b64 = 0, bp = 0;
   for (int m = 1; m <= kBatchMaxM; ++m) {
     b32 = std::max<int64_t>(b32, plan->blocks32[m]);
     b64 = std::max<int64_t>(b64, plan->blocks64[m]);
+    bp = std::max<int64_t>(bp, plan->blocksp[m]);
   }
-  info[6] = b32;
-  info[7] = b64;
+  v[6] = b32;
+  v[7] = b64;
+  v[8] = plan->tasks_pair;
+  v[9] = plan->n_pair_matrices;
+  v[10] = (int64_t)plan->minors_pair;
+  v[11] = bp;
+  for (int i = 0; i < count; ++i) info[i] = v[i];
   return RADIC_OK;
 }
 

@@ -9,7 +9,10 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "radic_internal.h"
+#include "radic_ff.cuh"
 
 namespace radic {
 
@@ -163,6 +166,9 @@ __device__ __forceinline__ double rcp_f64(double d) {
   r = fma(r, e, r);
   return d == 0.0 ? 0.0 : r;
 }
+
+__device__ __forceinline__ float rcp_t(float d) { return rcp_f32(d); }
+__device__ __forceinline__ double rcp_t(double d) { return rcp_f64(d); }
 
 // Magnitude keys for pivot comparisons that stay off the FP64 pipe: the high
 // word of |x| orders binary64 magnitudes up to ties within 2^-20.
@@ -367,7 +373,7 @@ __device__ inline int stage_scaled(const void* A, int dtype, int m, int n, long 
   //    column-major shared copy, padding rows zeroed for vector loads
   for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
-    As[j * cs + i] = static_cast<T>(ldexp(load_elem(A, dtype, (long long)i * lda + j), -row_exp[i]));
+    As[j * cs + i] = to_elem<T>(ldexp(load_elem(A, dtype, (long long)i * lda + j), -row_exp[i]));
   }
   for (int idx = threadIdx.x; idx < (cs - m) * n; idx += blockDim.x) {
     const int j = idx / (cs - m), i = m + (idx - j * (cs - m));

@@ -61,7 +61,9 @@ __device__ __forceinline__ bool mixed_flag(T det, T gmax, T thr) {
 // Writes the final radic_result from block-ordered partial sums.
 __device__ inline void write_fp_result(radic_result* out, const Dd& t, double abs_sum, int escale, int m,
                                        unsigned long long total, long long flagged, int status, int tier) {
-  const double u = (tier == kModeFp64) ? 0x1p-53 : 0x1p-24;
+  // unit roundoff of the elimination: binary64, pairs of binary32 (about
+  // 2^-46 per operation, 2^-44 allows for the renormalisations), binary32
+  const double u = (tier == kModeFp64) ? 0x1p-53 : (tier == kModePair ? 0x1p-44 : 0x1p-24);
   out->value = ldexp(t.hi + t.lo, escale);
   out->abs_sum = ldexp(abs_sum, escale);
   out->err_est = static_cast<double>(m) * u * out->abs_sum;
@@ -79,8 +81,15 @@ __device__ inline void write_fp_result(radic_result* out, const Dd& t, double ab
 // and writes the result.  In the mixed mode it also leaves the totals and the
 // number of flagged entries in the workspace header for the fix-up kernel,
 // which rewrites the result only when something was flagged.
+// Tier (mode) that produced a floating-point result: binary64, binary32
+// elimination (MIXED) or pairs of binary32 (PAIR).
+template <typename T, bool kMixed>
+__host__ __device__ constexpr int tier_of() {
+  return !kMixed ? kModeFp64 : (std::is_same<T, ff>::value ? kModePair : kModeMixed);
+}
+
 template <bool kMixed>
-__device__ inline void finish_fp_main(const SingleArgs& a, double* scratch, int escale, int m) {
+__device__ inline void finish_fp_main(const SingleArgs& a, double* scratch, int escale, int m, int tier) {
   if (!last_block(&a.hdr->ticket[0])) return;
   Dd t;
   double ab = 0.0;
@@ -102,7 +111,7 @@ __device__ inline void finish_fp_main(const SingleArgs& a, double* scratch, int 
       a.hdr->flag_total = fl;
       a.hdr->escale = escale;
     }
-    write_fp_result(a.out, t, ab, escale, m, a.total, 0, a.hdr->status, kMixed ? kModeMixed : kModeFp64);
+    write_fp_result(a.out, t, ab, escale, m, a.total, 0, a.hdr->status, tier);
   }
 }
 
@@ -203,7 +212,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
     }
     block_reduce_dd(acc, abs_sum, cnt, sm.scratch);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, cnt};
-    finish_fp_main<kMixed>(a, sm.scratch, escale, M);
+    finish_fp_main<kMixed>(a, sm.scratch, escale, M, tier_of<T, kMixed>());
   }
 }
 
@@ -345,7 +354,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
     }
     block_reduce_dd(acc, abs_sum, cnt, sm.scratch);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, cnt};
-    finish_fp_main<kMixed>(a, sm.scratch, escale, m);
+    finish_fp_main<kMixed>(a, sm.scratch, escale, m, tier_of<T, kMixed>());
   }
 }
 

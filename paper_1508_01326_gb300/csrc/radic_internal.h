@@ -11,7 +11,12 @@ namespace radic {
 
 // dtype / mode / mapping codes (same values as the C enums)
 enum : int { kI8 = RADIC_I8, kI32 = RADIC_I32, kF32 = RADIC_F32, kF64 = RADIC_F64 };
-enum : int { kModeFp64 = RADIC_MODE_FP64, kModeMixed = RADIC_MODE_MIXED, kModeExact = RADIC_MODE_EXACT };
+enum : int {
+  kModeFp64 = RADIC_MODE_FP64,
+  kModeMixed = RADIC_MODE_MIXED,
+  kModeExact = RADIC_MODE_EXACT,
+  kModePair = RADIC_MODE_PAIR
+};
 
 constexpr int kMaxM = RADIC_MAX_M;
 constexpr int kMaxN = RADIC_MAX_N;
@@ -21,6 +26,7 @@ constexpr int kThreadMaxMFp32 = 12;
 constexpr int kThreadMaxMModp = 12;
 constexpr int kPrefixMaxMFp64 = 10;  // prefix mapping limits
 constexpr int kPrefixMaxMFp32 = 12;
+constexpr int kPrefixMaxMPair = 10;
 
 // 31-bit primes of the exact mode (largest primes below 2^31).
 constexpr uint32_t kPrime0 = 2147483647u, kPrime1 = 2147483629u, kPrime2 = 2147483587u, kPrime3 = 2147483579u;
@@ -110,6 +116,7 @@ int device_sm_count();
 // kernel writes per-rank terms instead of reducing.
 int launch_fp64(const SinglePlan& p, const SingleArgs& a, cudaStream_t s);
 int launch_mixed(const SinglePlan& p, const SingleArgs& a, cudaStream_t s);
+int launch_pair(const SinglePlan& p, const SingleArgs& a, cudaStream_t s);
 int launch_modp(const SinglePlan& p, const SingleArgs& a, cudaStream_t s);
 int launch_unrank(int n, int m, unsigned long long q0, unsigned long long count, uint8_t* cols,
                   int ranks_per_task, cudaStream_t s);
@@ -117,10 +124,17 @@ int launch_unrank(int n, int m, unsigned long long q0, unsigned long long count,
 // Occupancy helpers filled in by the arithmetic files.
 int blocks_per_sm_fp64(const SinglePlan& p);
 int blocks_per_sm_mixed(const SinglePlan& p);
+int blocks_per_sm_pair(const SinglePlan& p);
 int blocks_per_sm_modp(const SinglePlan& p);
 size_t smem_fp64(const SinglePlan& p);
 size_t smem_mixed(const SinglePlan& p);
+size_t smem_pair(const SinglePlan& p);
 size_t smem_modp(const SinglePlan& p);
+
+// Binary64 fix-up kernel of the MIXED and PAIR modes (arguments: SingleArgs,
+// int main_blocks, int tier) and its dynamic shared memory.
+const void* mixed_fixup_kernel(int m);
+size_t mixed_fixup_smem(const SinglePlan& p);
 
 // Cost model of the prefix mapping (instruction units): P = m - D prefix
 // columns, D = 2 or 3 trailing columns per leaf; a prefix with k candidate

@@ -96,7 +96,7 @@ __device__ long long prefix_leaves_f64(const FpSmem<double>& sm, int n, int m, i
 // main kernel, and the last block adds the recomputed sums to the main totals
 // kept in the workspace header and rewrites the result.
 template <int MC>
-__global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_blocks) {
+__global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_blocks, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int has_work;
   const bool overflow = __ldcg(&a.hdr->overflow) != 0;
@@ -174,8 +174,7 @@ __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_bloc
         t.merge(mainsum);
         ab += __ldcg(&a.hdr->main_abs);
       }
-      write_fp_result(a.out, t, ab, __ldcg(&a.hdr->escale), m, a.total, flagged, __ldcg(&a.hdr->status),
-                      kModeMixed);
+      write_fp_result(a.out, t, ab, __ldcg(&a.hdr->escale), m, a.total, flagged, __ldcg(&a.hdr->status), tier);
     }
   }
 }
@@ -236,21 +235,21 @@ const void* pick(const SinglePlan& p, bool terms) {
   return nullptr;
 }
 
-const void* pick_fixup(int m) {
+}  // namespace
+
+const void* mixed_fixup_kernel(int m) {
   if (m <= 8) return reinterpret_cast<const void*>(&k_mixed_fixup<8>);
   if (m <= 16) return reinterpret_cast<const void*>(&k_mixed_fixup<16>);
   return reinterpret_cast<const void*>(&k_mixed_fixup<32>);
 }
 
-}  // namespace
+size_t mixed_fixup_smem(const SinglePlan& p) { return fp_smem_bytes(p.n, p.m, p.m, 8, 128); }
 
 size_t smem_mixed(const SinglePlan& p) {
   const int cs = (p.mapping != RADIC_MAP_GROUP) ? ((p.m + 3) / 4) * 4 : p.m;
   if (p.mapping == RADIC_MAP_PREFIX) return prefix_smem_bytes(p.n, p.m, cs, 4, p.threads, p.depth);
   return fp_smem_bytes(p.n, p.m, cs, 4, p.threads);
 }
-
-static size_t smem_fixup(const SinglePlan& p) { return fp_smem_bytes(p.n, p.m, p.m, 8, 128); }
 
 int blocks_per_sm_mixed(const SinglePlan& p) {
   const void* k = pick(p, false);
@@ -275,9 +274,10 @@ int launch_mixed(const SinglePlan& p, const SingleArgs& a, cudaStream_t s) {
     return RADIC_ECUDA;
   if (ev && cudaEventRecord(ev[1], s) != cudaSuccess) return RADIC_ECUDA;
   if (terms) return RADIC_OK;
-  int main_blocks = p.blocks;
-  void* params2[] = {&args, &main_blocks};
-  if (cudaLaunchKernel(pick_fixup(p.m), dim3(p.blocks2), dim3(128), params2, smem_fixup(p), s) != cudaSuccess)
+  int main_blocks = p.blocks, tier = kModeMixed;
+  void* params2[] = {&args, &main_blocks, &tier};
+  if (cudaLaunchKernel(mixed_fixup_kernel(p.m), dim3(p.blocks2), dim3(128), params2, mixed_fixup_smem(p), s) !=
+      cudaSuccess)
     return RADIC_ECUDA;
   return RADIC_OK;
 }

@@ -20,6 +20,7 @@
 
 #include <type_traits>
 
+#include "radic_ff.cuh"
 #include "radic_fp_kernels.cuh"
 
 namespace radic {
@@ -47,6 +48,21 @@ struct ZBuf<T, 2> {
     v.x = z[0];
     v.y = z[1];
     p[q * stride] = v;
+  }
+};
+template <>
+struct ZBuf<ff, 2> {  // (x.hi, x.lo, y.hi, y.lo) in one 16-byte vector
+  float4* p;
+  int stride;
+  __device__ ZBuf(void* base, int lane, int stride_, int /*kcap*/)
+      : p(static_cast<float4*>(base) + lane), stride(stride_) {}
+  __device__ __forceinline__ void get(int q, ff (&y)[2]) const {
+    const float4 v = p[q * stride];
+    y[0] = ff(v.x, v.y);
+    y[1] = ff(v.z, v.w);
+  }
+  __device__ __forceinline__ void put(int q, const ff (&z)[2]) const {
+    p[q * stride] = make_float4(z[0].hi, z[0].lo, z[1].hi, z[1].lo);
   }
 };
 template <typename T>
@@ -121,9 +137,7 @@ __device__ __forceinline__ void prefix_factor(const T* __restrict__ As, const in
       neg ^= sw;
     }
     const T piv = a[k][k];
-    T r;
-    if constexpr (sizeof(T) == 8) r = rcp_f64(piv);
-    else r = rcp_f32(piv);
+    const T r = rcp_t(piv);
     prod *= piv;
     gmax = fmax(gmax, fabs(piv));
 #pragma unroll
@@ -208,6 +222,35 @@ struct PrefixAcc<float> {
   }
 };
 
+template <>
+struct PrefixAcc<ff> {
+  // per prefix: pair sums; per thread: binary64 two-sum of the prefix sums
+  // (one flush per prefix, off the leaf loop), binary32 pairs for |terms|
+  ff pre = ff(0.0f, 0.0f);
+  float pre_abs = 0.0f;
+  Ff tot_abs;
+  Dd acc;
+  double abs_sum = 0.0;
+  __device__ __forceinline__ void add_column(ff s, ff a) {
+    pre += s;
+    pre_abs += a.hi;
+  }
+  __device__ __forceinline__ void end_prefix() {
+    acc.add(static_cast<double>(pre.hi));
+    acc.add(static_cast<double>(pre.lo));
+    tot_abs.add(pre_abs);
+    pre = ff(0.0f, 0.0f);
+    pre_abs = 0.0f;
+  }
+  __device__ __forceinline__ void drop_prefix() {
+    pre = ff(0.0f, 0.0f);
+    pre_abs = 0.0f;
+  }
+  __device__ __forceinline__ void finish() {
+    abs_sum = static_cast<double>(tot_abs.hi) + static_cast<double>(tot_abs.lo);
+  }
+};
+
 // Where per-leaf terms go (terms output of the parity tests); unused otherwise.
 struct TermsSink {
   double* terms;
@@ -225,15 +268,24 @@ struct TermsSink {
 #ifndef RADIC_LEAF_BLOCK_F64
 #define RADIC_LEAF_BLOCK_F64 1
 #endif
+#ifndef RADIC_LEAF_BLOCK_FF
+#define RADIC_LEAF_BLOCK_FF 2
+#endif
 template <typename T>
 __host__ __device__ constexpr int leaf_block() {
-  return sizeof(T) == 4 ? RADIC_LEAF_BLOCK_F32 : RADIC_LEAF_BLOCK_F64;
+  return std::is_same<T, ff>::value ? RADIC_LEAF_BLOCK_FF
+                                    : (sizeof(T) == 4 ? RADIC_LEAF_BLOCK_F32 : RADIC_LEAF_BLOCK_F64);
 }
 
 template <typename T>
 __device__ __forceinline__ void leaf_add(T d, T& s, T& a) {
   s += d;
   a += fabs(d);
+}
+// Pairs: the magnitude sum only bounds errors, so it is kept in binary32.
+__device__ __forceinline__ void leaf_add(ff d, ff& s, ff& a) {
+  s += d;
+  a.hi += fabsf(d.hi);
 }
 
 // 2 x 2 and 3 x 3 leaf determinants of Schur-complement columns.
@@ -527,7 +579,7 @@ __global__ void __launch_bounds__(128) k_fp_prefix(SingleArgs a, PrefixTable tab
     double ab = acc.abs_sum;
     block_reduce_dd(d, ab, fl, sm.scratch);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{d.hi, d.lo, ab, fl};
-    finish_fp_main<kMixed>(a, sm.scratch, escale, M);
+    finish_fp_main<kMixed>(a, sm.scratch, escale, M, tier_of<T, kMixed>());
   }
 }
 

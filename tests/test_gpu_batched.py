@@ -4,7 +4,8 @@ Small batches of uneven shapes are checked against the exact enumeration of
 Eq. (1); the full 4096-matrix workload is checked against the exact values
 of tests/golden/workload_exact.txt (written by the oracle's Pfaffian closed
 form).  Binary64 results must be within 1e-12 * sum|terms|; mixed results
-within 1e-10 * sum|terms| (the target the tier router is built for).
+within 1e-10 * sum|terms| (the target the tier router is built for); results
+of the pair tier (elimination in pairs of binary32) within 1e-11 * sum|terms|.
 """
 import math
 import os
@@ -79,6 +80,8 @@ def test_small_batch_matches_oracle(mode):
             continue
         if r["tier"] == 0:  # binary64
             assert abs(Fraction(r["value"]) - val) <= Fraction(1e-12) * abs_sum
+        elif r["tier"] == 3:  # pairs of binary32
+            assert abs(float(Fraction(r["value"]) - val)) <= 1e-11 * float(abs_sum)
         else:
             # small matrices are routed to binary64 by the mixed plan
             assert abs(float(Fraction(r["value"]) - val)) <= 1e-10 * float(abs_sum)
@@ -140,6 +143,36 @@ def test_batch_flagged_task_recomputed_in_binary64():
     assert abs(float(Fraction(res[0]["value"]) - val)) <= 8 * m * 2.0 ** -24 * float(abs_sum)
 
 
+def test_batch_flagged_pair_task_recomputed_in_binary64():
+    m = 9
+    w = np.eye(m) - np.tril(np.ones((m, m)), -1)
+    w[:, -1] = 1.0
+    a = np.concatenate([w, W.uniform_matrix(79, m, 7)], axis=1)
+    tuning = R().make_tuning(tiers=["pair"], tol=1e-10)
+    res, info = run_batch([a, W.uniform_matrix(80, 5, 12)], "mixed", tuning=tuning)
+    assert info["matrices_pair"] == 2
+    val, abs_sum = orc.radic_det_exact(a)
+    assert res[0]["flagged"] > 0
+    assert abs(float(Fraction(res[0]["value"]) - val)) <= 1e-12 * float(abs_sum)
+
+
+def test_batch_flagged_per_minor_task_recomputed_in_binary64():
+    # per-minor binary32 tasks (m = 8) through the growth matrix: the flagged
+    # tasks are redone by the binary64 kernel with the per-minor mapping.  The
+    # rows are scaled to a largest entry of 1/2, so the last pivot of the
+    # growth minor is 2^7 / 2 = 64: a threshold of 16 flags it.
+    m = 8
+    w = np.eye(m) - np.tril(np.ones((m, m)), -1)
+    w[:, -1] = 1.0
+    a = np.concatenate([w, W.uniform_matrix(81, m, 4)], axis=1)
+    tuning = R().make_tuning(kind={8: "thread"}, task_cost={8: 2000}, tol=1.0, growth_threshold=16.0)
+    res, info = run_batch([a], "mixed", tuning=tuning)
+    assert info["matrices_fp32"] == 1
+    val, abs_sum = orc.radic_det_exact(a)
+    assert res[0]["flagged"] > 0
+    assert abs(float(Fraction(res[0]["value"]) - val)) <= 8 * m * 2.0 ** -24 * float(abs_sum)
+
+
 def _golden(name):
     vals = {}
     with open(os.path.join(ROOT, "tests", "golden", "workload_exact.txt")) as f:
@@ -167,11 +200,64 @@ def test_full_batched_4096(mode, dtype, golden, tol):
         err = abs(r["value"] - w) / r["abs_sum"]
         worst = max(worst, err)
     assert worst <= tol, worst
-    assert info["matrices_fp32"] + info["matrices_fp64"] == len(mats)
+    assert info["matrices_fp32"] + info["matrices_pair"] + info["matrices_fp64"] == len(mats)
     if mode == "mixed":
-        # the router sends a matrix to binary32 only when 2.5e-6 / sqrt(C) meets tol
-        want32 = sum(1 for a in mats if a.shape[0] <= a.shape[1]
-                     and 2.5e-6 / math.sqrt(math.comb(a.shape[1], a.shape[0])) <= tol)
+        # binary32 when 2.5e-6 / sqrt(C) meets tol, else pairs (m >= 3) when
+        # 1e-11 / sqrt(C) does, else binary64
+        want32 = want_pair = 0
+        for a in mats:
+            m, n = a.shape
+            if m > n:
+                continue
+            rs = 1.0 / math.sqrt(math.comb(n, m))
+            if 2.5e-6 * rs <= tol:
+                want32 += 1
+            elif m >= 3 and 1e-11 * rs <= tol:
+                want_pair += 1
         assert info["matrices_fp32"] == want32
+        assert info["matrices_pair"] == want_pair
         if tol >= 1e-8:
             assert want32 > 0
+        if tol <= 1e-10:
+            assert want_pair > 0
+    else:
+        assert info["matrices_pair"] == 0
+
+
+def test_pair_tier_small_batch_matches_oracle():
+    mats = small_batch(5, 60, max_m=10, max_d=10)
+    tuning = R().make_tuning(tiers=["pair"], tol=1e-10)
+    res, info = run_batch(mats, "mixed", tuning=tuning)
+    assert info["matrices_fp32"] == 0
+    assert info["matrices_pair"] == sum(1 for a in mats if 3 <= a.shape[0] <= a.shape[1])
+    for a, r in zip(mats, res):
+        val, abs_sum = orc.radic_det_exact(a)
+        m, n = a.shape
+        assert r["status"] == 0
+        if m > n:
+            assert r["value"] == 0.0
+            continue
+        assert r["tier"] == (3 if m >= 3 else 0)
+        assert abs(float(Fraction(r["value"]) - val)) <= 1e-11 * float(abs_sum)
+
+
+@pytest.mark.parametrize("depth", [2, 3])
+def test_pair_tier_both_depths(depth):
+    mats = small_batch(6, 30, max_m=10, max_d=8)
+    mats = [a for a in mats if a.shape[0] >= 4]
+    tuning = R().make_tuning(tiers=["pair"], tol=1e-10, prefix_depth={m: depth for m in range(4, 11)},
+                             task_cost={m: 3000 for m in range(1, 11)})
+    res, info = run_batch(mats, "mixed", tuning=tuning)
+    for a, r in zip(mats, res):
+        val, abs_sum = orc.radic_det_exact(a)
+        if a.shape[0] > a.shape[1]:
+            continue
+        assert r["tier"] == 3
+        assert abs(float(Fraction(r["value"]) - val)) <= 1e-11 * float(abs_sum)
+
+
+def test_fp32_only_router_sends_the_rest_to_binary64():
+    mats = small_batch(7, 30)
+    res, info = run_batch(mats, "mixed", tuning=R().make_tuning(tiers=["fp32"], tol=1e-10))
+    assert info["matrices_pair"] == 0
+    assert all(r["tier"] in (0, 1) for r in res)

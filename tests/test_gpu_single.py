@@ -4,8 +4,8 @@ Element-by-element: the per-minor signed terms and the unranked column
 sequences of the device are compared with the oracle for every rank of small
 cases (several tasks and a ragged tail).  Whole results: det_R(A) against the
 exact value, bit-exact for the multi-modular path, within
-1e-12 * sum|terms| for binary64 and within a derived bound for the mixed
-binary32 path.  Full-size workloads run in the launch configuration the bench
+1e-12 * sum|terms| for binary64 and within derived bounds for the mixed
+binary32 path and the pair (float-float) path.  Full-size workloads run in the launch configuration the bench
 uses and are checked against the Pfaffian closed form and sampled terms.
 """
 import itertools
@@ -23,6 +23,7 @@ from paper_1508_01326_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
+UPAIR = 2.0 ** -44  # unit roundoff allowed for the pair arithmetic (about 2^-46 per operation)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -73,6 +74,7 @@ FP64_LIMIT = {"thread": 8, "thread_l13": 8, "prefix": 10, "prefix_r1": 10, "pref
               "prefix3_r1": 10}
 MIXED_LIMIT = {"thread": 12, "thread_l13": 12, "prefix": 12, "prefix_r1": 12, "prefix2": 12, "prefix3": 12,
                "prefix3_r1": 12}
+PAIR_LIMIT = {"prefix": 10, "prefix_r1": 10, "prefix2": 10, "prefix3": 10, "prefix3_r1": 10, "thread": 0}
 
 
 # ---------------------------------------------------------------------------
@@ -180,6 +182,22 @@ def test_terms_mixed_elementwise(m, n, dtype, key):
     assert np.all(np.abs(got[ok] - want[ok]) <= 8 * m * U32 * h[ok]), np.max(np.abs(got[ok] - want[ok]) / h[ok])
 
 
+@pytest.mark.parametrize("m,n,dtype,key", TERM_CASES)
+def test_terms_pair_elementwise(m, n, dtype, key):
+    if not key.startswith("prefix") or m > PAIR_LIMIT[key]:
+        pytest.skip("the pair mode has the prefix mapping only, m <= 10")
+    a = _matrix(m, n, dtype, 250 + m * n)
+    total = math.comb(n, m)
+    q0 = total // 6
+    count = total - q0
+    got = R().radic_terms(dev(a), q0, count, mode="pair", options=OPTS[key]).cpu().numpy()
+    want = np.array([float(x) for x in orc.radic_terms_exact(a, range(q0, q0 + count))])
+    h = hadamard_terms(a, combos0(n, m)[q0:])
+    # pair LU: backward error O(m u) per entry with u about 2^-46, and the
+    # 48-bit rounding of binary64 input
+    assert np.all(np.abs(got - want) <= 8 * m * UPAIR * h + 1e-300), np.max(np.abs(got - want) / h)
+
+
 EXACT_CASES = [
     (1, 7, np.int32, "thread", 50),
     (3, 12, np.int32, "thread", 9),
@@ -271,6 +289,32 @@ def test_det_mixed_small(m, n, dtype, mapping):
     assert res["tier"] == 1
 
 
+@pytest.mark.parametrize("mapping", ["auto", "prefix", "prefix3"])
+@pytest.mark.parametrize("m,n,dtype", DET_CASES)
+def test_det_pair_small(m, n, dtype, mapping):
+    if not (3 <= m <= 10 and m <= n and _mapping_ok(mapping, m, n, PAIR_LIMIT)):
+        pytest.skip("the pair mode has the prefix mapping only, 3 <= m <= min(n, 10)")
+    a = _matrix(m, n, dtype, 550 + m * n)
+    val, abs_sum = _exact(a)
+    res = R().det(a, mode="pair", options=_det_opts(mapping))
+    assert res["tier"] == 3
+    assert res["minors"] == math.comb(n, m)
+    h = hadamard_terms(a, combos0(n, m)).sum()
+    assert abs(res["value"] - float(val)) <= 8 * m * UPAIR * h
+    assert abs(float(Fraction(res["value"]) - val)) <= 1e-11 * float(abs_sum)
+
+
+def test_pair_mode_rejects_other_mappings_and_shapes():
+    from paper_1508_01326_gb300 import RadicError
+
+    with pytest.raises(RadicError):
+        R().det(W.uniform_matrix(1, 5, 9), mode="pair", options=dict(mapping="thread"))
+    with pytest.raises(RadicError):
+        R().det(W.uniform_matrix(1, 11, 14), mode="pair")
+    with pytest.raises(RadicError):
+        R().det(W.uniform_matrix(1, 2, 14), mode="pair")
+
+
 @pytest.mark.parametrize("m,n,dtype,bound", [(1, 5, np.int32, 7), (3, 12, np.int32, 9), (5, 9, np.int8, 3),
                                              (8, 11, np.int32, 3000), (10, 13, np.int8, 3),
                                              (12, 13, np.int32, 100), (13, 15, np.int8, 3),
@@ -307,7 +351,7 @@ def test_det_leading_dimension():
 
 def test_det_is_deterministic():
     a = dev(W.uniform_matrix(3, 7, 20))
-    for mode in ["fp64", "mixed"]:
+    for mode in ["fp64", "mixed", "pair"]:
         v1 = R().parse_result(R().radic_det(a, mode=mode))["value"]
         v2 = R().parse_result(R().radic_det(a, mode=mode))["value"]
         assert v1 == v2
@@ -326,6 +370,19 @@ def test_mixed_growth_flag_recomputes_in_binary64(key):
     assert res["flagged"] >= 1
     h = hadamard_terms(a, combos0(n, m)).sum()
     assert abs(res["value"] - float(val)) <= 8 * m * U32 * h
+
+
+@pytest.mark.parametrize("key", ["prefix2", "prefix3"])
+def test_pair_growth_flag_recomputes_in_binary64(key):
+    m, n = 9, 11
+    w = np.eye(m) - np.tril(np.ones((m, m)), -1)
+    w[:, -1] = 1.0
+    a = np.concatenate([w, W.uniform_matrix(18, m, n - m)], axis=1)
+    val, abs_sum = _exact(a)
+    res = R().det(a, mode="pair", options=OPTS[key])
+    assert res["flagged"] >= 1
+    h = hadamard_terms(a, combos0(n, m)).sum()
+    assert abs(res["value"] - float(val)) <= 8 * m * UPAIR * h
 
 
 @pytest.mark.parametrize("mapping", ["thread", "prefix", "prefix3"])
@@ -400,6 +457,15 @@ def test_full_fp64_8x32_mixed(fp64_8x32, mapping):
     assert rel <= 1e-10, rel
 
 
+@pytest.mark.parametrize("mapping", ["auto", "prefix", "prefix3"])
+def test_full_fp64_8x32_pair(fp64_8x32, mapping):
+    a, exact = fp64_8x32
+    res = R().det(a, mode="pair", options=_det_opts(mapping))
+    assert res["tier"] == 3 and res["minors"] == 10_518_300
+    rel = abs(float(Fraction(res["value"]) - exact)) / res["abs_sum"]
+    assert rel <= 1e-12, rel
+
+
 def test_full_fp64_8x32_sampled_terms(fp64_8x32):
     a, _ = fp64_8x32
     rng = random.Random(22)
@@ -428,3 +494,17 @@ def test_full_int8_12x40_exact():
     assert res["minors"] == math.comb(40, 12)
     assert res["n_primes"] == 3
     assert res["exact"] == exact
+
+
+def test_plan_info_reports_the_default_mapping_and_depth():
+    info = R().radic_plan_info(8, 32, "mixed")
+    assert info["mapping"] == "prefix" and info["prefix_depth"] == 3  # n - m = 24 <= 3m
+    assert R().radic_plan_info(8, 32, "fp64")["prefix_depth"] == 2    # 24 > 2.5m with 8-byte entries
+    assert R().radic_plan_info(8, 32, "pair")["prefix_depth"] == 2
+    assert R().radic_plan_info(10, 30, "fp64")["prefix_depth"] == 3
+    assert R().radic_plan_info(5, 60, "mixed")["prefix_depth"] == 2   # m < 6
+    g = R().radic_plan_info(14, 20, "fp64")
+    assert g["mapping"] == "group" and g["group_width"] == 16 and g["prefix_depth"] == 0
+    t = R().radic_plan_info(6, 20, "exact")
+    assert t["mapping"] == "thread" and t["threads"] == 128 and t["blocks"] >= 1
+    assert t["workspace_bytes"] == R().radic_workspace_bytes(6, 20, "exact")
