@@ -109,9 +109,10 @@ typedef struct radic_options {
                                stream right before and right after the main
                                per-minor kernel (profiling hook)             */
   int32_t prefix_depth;     /* PREFIX mapping: trailing columns per leaf, 2 or
-                               3 (0: 3 when m >= 6 and n - m <= 3m (MIXED)
-                               or 2.5m (FP64), else 2)                       */
-  int32_t pad;
+                               3 (0: 3 when m >= 7 and n - m <= 3.5m, else 2) */
+  int32_t lanes_per_prefix; /* PREFIX mapping: lanes of a warp that share the
+                               leaves of one prefix (1, 2, 4, ..., 32; 0:
+                               per prefix group, from the plan's cost model) */
   int64_t reserved[2];
 } radic_options;
 

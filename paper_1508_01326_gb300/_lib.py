@@ -29,7 +29,7 @@ class RadicOptions(ctypes.Structure):
         ("growth_threshold", ctypes.c_double),
         ("kernel_events", ctypes.c_void_p),
         ("prefix_depth", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("lanes_per_prefix", ctypes.c_int32),
         ("reserved", ctypes.c_int64 * 2),
     ]
 
@@ -122,7 +122,8 @@ def check(fn: str, code: int) -> None:
 
 def make_options(mapping: str | int = 0, group_width: int = 0, ranks_per_task: int = 0,
                  threads_per_block: int = 0, blocks: int = 0, flag_capacity: int = 0,
-                 growth_threshold: float = 0.0, kernel_events: int = 0, prefix_depth: int = 0) -> RadicOptions:
+                 growth_threshold: float = 0.0, kernel_events: int = 0, prefix_depth: int = 0,
+                 lanes_per_prefix: int = 0) -> RadicOptions:
     o = RadicOptions()
     o.mapping = MAPPINGS[mapping] if isinstance(mapping, str) else int(mapping)
     o.group_width = group_width
@@ -133,4 +134,5 @@ def make_options(mapping: str | int = 0, group_width: int = 0, ranks_per_task: i
     o.growth_threshold = growth_threshold
     o.kernel_events = kernel_events or None
     o.prefix_depth = prefix_depth
+    o.lanes_per_prefix = lanes_per_prefix
     return o

@@ -1,9 +1,11 @@
 """Command-line runner: one workload, one mode, a few repetitions.
 
     python -m paper_1508_01326_gb300.cli --workload fp64_8x32 --mode mixed --reps 3
+    python -m paper_1508_01326_gb300.cli --batched-m 10 --mode mixed --tol 1e-10 --reps 2
 
 Prints the parsed result and the CUDA-event time of each repetition.  Useful
-as a small, self-contained target for profilers.
+as a small, self-contained target for profilers.  With --batched-m the run
+is the batched path over the matrices with that m of the 4096-matrix batch.
 """
 from __future__ import annotations
 
@@ -26,22 +28,49 @@ WORKLOADS = {
 }
 
 
+def run_batched(args) -> None:
+    mats = [a for a in W.batched_4096() if a.shape[0] == args.batched_m]
+    data, ms, ns, offs = W.pack_batch(mats, np.float64)
+    A = torch.from_numpy(data).cuda()
+    depth = {args.batched_m: args.depth} if args.depth else None
+    tuning = api.make_tuning(tol=args.tol, prefix_depth=depth)
+    plan = api.BatchPlan(list(zip(ms, ns)), offs, mode=args.mode, tuning=tuning)
+    out = plan.new_results()
+    times = []
+    for _ in range(args.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.radic_det_batched(A, out)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    print(json.dumps({"batched_m": args.batched_m, "matrices": len(mats), "mode": args.mode, "ms": times,
+                      "routing": plan.info()}))
+    plan.close()
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="fp64_8x32", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="mixed", choices=["fp64", "mixed", "exact"])
+    ap.add_argument("--mode", default="mixed", choices=["fp64", "mixed", "exact", "pair"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--mapping", default="auto", choices=["auto", "thread", "group", "prefix"])
     ap.add_argument("--group-width", type=int, default=0)
     ap.add_argument("--ranks-per-task", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--depth", type=int, default=0, help="prefix depth (0: library default)")
+    ap.add_argument("--batched-m", type=int, default=0, help="batched path over this m of the 4096 batch")
+    ap.add_argument("--tol", type=float, default=1e-10, help="batched MIXED router tolerance")
     args = ap.parse_args()
     from . import build as B
 
     B.build()
+    if args.batched_m:
+        run_batched(args)
+        return
     a = torch.from_numpy(np.ascontiguousarray(WORKLOADS[args.workload]())).cuda()
     opts = dict(mapping=args.mapping, group_width=args.group_width, ranks_per_task=args.ranks_per_task,
-                threads_per_block=args.threads)
+                threads_per_block=args.threads, prefix_depth=args.depth)
     out = api.new_result()
     ws = torch.empty(max(api.radic_workspace_bytes(*a.shape, mode=args.mode, options=opts), 256),
                      dtype=torch.uint8, device="cuda")

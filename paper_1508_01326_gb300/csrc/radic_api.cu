@@ -52,6 +52,7 @@ size_t smem_of(const SinglePlan& p) {
 
 void layout_workspace(SinglePlan& pl);
 
+
 int plan_prefix(SinglePlan pl, const radic_options& d, int sms, int per_sm, unsigned long long units,
                 SinglePlan* out) {
   const int m = pl.m, n = pl.n, D = pl.depth, P = m - D;
@@ -69,14 +70,35 @@ int plan_prefix(SinglePlan pl, const radic_options& d, int sms, int per_sm, unsi
   const double per_lane = total_cost / (double)lanes / 4.0;  // about four tasks per warp
   unsigned long long start = 0;
   for (int v = t.v_lo; v <= t.v_hi; ++v) {
-    double r = per_lane / cost[v];
+    // Lanes per prefix: a prefix with many candidate columns costs far more
+    // than a lane's share of the launch (the leaves grow like C(k, D)), so
+    // its leaves are split over LP lanes of the warp, each of which repeats
+    // the factorisation and the column reductions.  LP is the smallest power
+    // of two that brings a lane's cost down to the mean per-lane work.
+    int lp = 1;
+    if (d.lanes_per_prefix > 0) {
+      lp = d.lanes_per_prefix;
+    } else if (D == 3) {
+      // Only depth 3 (its leaves grow like C(k, 3); splitting depth-2
+      // prefixes measured slower).  Target: twice the mean lane work when
+      // that is large, four times when the launch is small and the repeated
+      // factorisations would dominate (measured on the shapes of
+      // prefix_auto_depth).
+      const double mean = 4.0 * per_lane;
+      const double target = (mean >= 1000.0 ? 2.0 : 4.0) * mean;
+      const double red = prefix_cost_shared(m, D, n - 1 - v), split = cost[v] - red;
+      while (lp < 32 && red + split / lp > target) lp *= 2;
+    }
+    const unsigned long long groups = 32 / lp;  // lane groups per warp
+    double r = per_lane * lp / cost[v];
     unsigned long long run = r < 1.0 ? 1ull : (unsigned long long)r;
     if (d.ranks_per_task > 0) run = (unsigned long long)d.ranks_per_task;
-    const unsigned long long maxrun = (t.count[v] + 31) / 32;
+    const unsigned long long maxrun = (t.count[v] + groups - 1) / groups;
     if (run > maxrun) run = maxrun > 0 ? maxrun : 1;
+    t.lanes[v] = lp;
     t.run[v] = run;
     t.task_start[v] = start;
-    start += (t.count[v] + 32 * run - 1) / (32 * run);
+    start += (t.count[v] + groups * run - 1) / (groups * run);
   }
   if (t.v_hi + 1 < kMaxN) t.task_start[t.v_hi + 1] = start;
   if (t.v_hi < t.v_lo) start = 0;
@@ -129,8 +151,10 @@ int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long
   pl.mapping = mapping;
   if (mapping == RADIC_MAP_PREFIX) {
     if (d.prefix_depth != 0 && d.prefix_depth != 2 && d.prefix_depth != 3) return RADIC_EINVAL;
+    const int lp = d.lanes_per_prefix;
+    if (lp < 0 || lp > 32 || (lp & (lp - 1)) != 0) return RADIC_EINVAL;
     if (d.prefix_depth == 3 && m < 4) return RADIC_EUNSUPPORTED;
-    pl.depth = d.prefix_depth ? d.prefix_depth : prefix_auto_depth(m, n, mode == kModeMixed ? 4 : 8);
+    pl.depth = d.prefix_depth ? d.prefix_depth : prefix_auto_depth(m, n, false);
   }
   if (mapping == RADIC_MAP_GROUP) {
     const int gw = d.group_width ? d.group_width : (m <= 16 ? 16 : 32);

@@ -169,7 +169,7 @@ __device__ bool run_prefix(const BatchArgs& a, const BatchTask& t, const WarpSli
 #pragma unroll
     for (int j = 0; j < P - 1; ++j) c[j] = head[j];
     c[P - 1] = t.v;
-    const bool f = prefix_one<T, M, D, CS, false>(w.As, w.binom, t.n, t.v, c, zb, thr, act, acc.p, ts);
+    const bool f = prefix_one<T, M, D, CS, false>(w.As, w.binom, t.n, t.v, c, zb, thr, act, 0, 1, acc.p, ts);
     if (kFlag && act && f) flagged = true;
     acc.p.end_prefix();
     if constexpr (P > 1) {
@@ -396,10 +396,9 @@ int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* 
   const int m = pl.shape[2 * b], n = pl.shape[2 * b + 1];
   std::vector<BatchTask>& out = (tier == kModeFp64) ? pl.t64 : pl.t32;
   if (m > n) return RADIC_OK;
-  const int elem = (tier == kModeMixed) ? 4 : 8;  // pairs are 8 bytes like binary64
-  int kind = (m >= 3) ? prefix_auto_depth(m, n, elem) : kKindMinor;
+  int kind = (m >= 3) ? prefix_auto_depth(m, n, true) : kKindMinor;
   if (tun && tun->kind[m] == RADIC_MAP_THREAD && m <= 8 && tier == kModeMixed) kind = kKindMinor;
-  if (tun && tun->kind[m] == RADIC_MAP_PREFIX && m >= 3) kind = prefix_auto_depth(m, n, elem);
+  if (tun && tun->kind[m] == RADIC_MAP_PREFIX && m >= 3) kind = prefix_auto_depth(m, n, true);
   if (kind != kKindMinor && tun && (tun->prefix_depth[m] == 2 || (tun->prefix_depth[m] == 3 && m >= 4)))
     kind = tun->prefix_depth[m];
   const double lane_cost = (tun && tun->task_cost[m] > 0.0) ? tun->task_cost[m] : 30000.0;

@@ -58,9 +58,10 @@ struct FpPartial {
 struct PrefixTable {
   int v_lo, v_hi;                          // groups v_lo .. v_hi
   unsigned long long total_tasks;          // warp tasks over all groups
-  unsigned long long count[kMaxN];         // prefixes in group v: C(v, m-3)
-  unsigned long long run[kMaxN];           // prefixes per lane in one task
+  unsigned long long count[kMaxN];         // prefixes in group v: C(v, m-D-1)
+  unsigned long long run[kMaxN];           // prefixes per lane group in one task
   unsigned long long task_start[kMaxN];    // first task index of group v
+  int lanes[kMaxN];                        // lanes sharing one prefix in group v (1..32, power of 2)
 };
 
 // Launch plan of one single-matrix call (computed identically by
@@ -148,19 +149,24 @@ inline double prefix_cost(int m, int D, int k) {
   return c;
 }
 
-// Default prefix depth for an m x n matrix whose elimination uses elements
-// of `elem` bytes.  Depth 3 divides the number of prefix factorisations by
-// about (n - m + 3) / (m - 2) but holds three Schur-complement entries per
-// candidate column, up to n - m + 3 columns per lane, in shared memory; with
-// many candidate columns that buffer cuts occupancy and the leaves' longer
-// chains are no longer hidden.  Measured on GB300 (single 8x32, 6x40, 10x30,
-// 12x28, 5x60 matrices and the batched m = 3..10 sets): depth 3 wins from
-// m = 6 on while n - m <= 3m with binary32 elements, n - m <= 2.5m with
-// binary64 elements (twice the bytes per entry), and loses below m = 6.
-inline int prefix_auto_depth(int m, int n, int elem) {
-  if (m < 6) return 2;
-  const int extra = n - m;
-  return (elem <= 4 ? extra <= 3 * m : 2 * extra <= 5 * m) ? 3 : 2;
+// The part of prefix_cost that every lane sharing one prefix repeats: the
+// factorisation and the k column reductions.
+inline double prefix_cost_shared(int m, int D, int k) {
+  const int P = m - D;
+  return (double)m * P * P + (double)k * (m + 2.0 * D * P);
+}
+
+// Default prefix depth for an m x n matrix.  Depth 3 divides the number of
+// prefix factorisations by about (n - m + 3) / (m - 2) but holds three
+// Schur-complement entries per candidate column, up to n - m + 3 columns per
+// lane, in shared memory, and its leaves grow like C(k, 3).  Measured on
+// GB300 in all three floating-point modes (single 5x60, 6x24, 6x40, 7x30,
+// 8x24, 8x32, 9x28, 10x20, 10x30, 12x28 matrices; batched m = 3..10 sets
+// with n - m <= 20): depth 3 wins while n - m <= 3.5m, from m = 7 on for
+// single matrices and from m = 6 on in the batched path.
+inline int prefix_auto_depth(int m, int n, bool batched) {
+  if (m < (batched ? 6 : 7)) return 2;
+  return 2 * (n - m) <= 7 * m ? 3 : 2;
 }
 
 inline int ceil_div(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }

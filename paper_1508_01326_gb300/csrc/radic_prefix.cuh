@@ -324,11 +324,14 @@ __device__ __forceinline__ void leaf_column(const T* __restrict__ As, int col, c
 // once for the whole block; leaves with two or three columns inside the
 // block are formed from registers.  Leaf sums are kept per column and added
 // to acc in column order.  Columns past k in the last block are zero and
-// their sums are discarded.
+// their sums are discarded.  When `lp` lanes share the prefix, lane `sub`
+// takes the leaves whose second-to-last column from the buffer is
+// congruent to sub modulo lp (and sub 0 those inside a block); every lane
+// computes all columns' z.
 template <typename T, int M, int D, int CS>
 __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, int v, int k, const T (&W)[D][M - D],
                                                       const int (&idx)[M], T alpha, const ZBuf<T, D>& zb, bool act,
-                                                      PrefixAcc<T>& acc, T& zmax) {
+                                                      int sub, int lp, PrefixAcc<T>& acc, T& zmax) {
   constexpr int LB = leaf_block<T>();
   for (int q = 0; q < k; q += LB) {
     T z[LB][D];
@@ -347,21 +350,23 @@ __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, 
     if constexpr (D == 2) {
       // (q2, q + b), q2 < q
 #pragma unroll 2
-      for (int q2 = 0; q2 < q; ++q2) {
+      for (int q2 = sub; q2 < q; q2 += lp) {
         T y[2];
         zb.get(q2, y);
 #pragma unroll
         for (int b = 0; b < LB; ++b) leaf_add(det2(y, z[b]), cs[b], ca[b]);
       }
       // (q + b2, q + b), b2 < b
+      if (sub == 0) {
 #pragma unroll
-      for (int b = 1; b < LB; ++b) {
+        for (int b = 1; b < LB; ++b) {
 #pragma unroll
-        for (int b2 = 0; b2 < b; ++b2) leaf_add(det2(z[b2], z[b]), cs[b], ca[b]);
+          for (int b2 = 0; b2 < b; ++b2) leaf_add(det2(z[b2], z[b]), cs[b], ca[b]);
+        }
       }
     } else {
       // (q1, q2, q + b), q1 < q2 < q: y1 . (y2 x z_b)
-      for (int q2 = 0; q2 < q; ++q2) {
+      for (int q2 = sub; q2 < q; q2 += lp) {
         T y2[3];
         zb.get(q2, y2);
         T w[LB][3];
@@ -385,7 +390,7 @@ __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, 
           for (int b2 = 0; b2 < b; ++b2) cross3(z[b2], z[b], w[b * (b - 1) / 2 + b2]);
         }
 #pragma unroll 2
-        for (int q1 = 0; q1 < q; ++q1) {
+        for (int q1 = sub; q1 < q; q1 += lp) {
           T y1[3];
           zb.get(q1, y1);
 #pragma unroll
@@ -395,12 +400,14 @@ __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, 
           }
         }
         // (q + b1, q + b2, q + b), b1 < b2 < b
+        if (sub == 0) {
 #pragma unroll
-        for (int b = 2; b < LB; ++b) {
+          for (int b = 2; b < LB; ++b) {
 #pragma unroll
-          for (int b2 = 1; b2 < b; ++b2) {
+            for (int b2 = 1; b2 < b; ++b2) {
 #pragma unroll
-            for (int b1 = 0; b1 < b2; ++b1) leaf_add(dot3(z[b1], w[b * (b - 1) / 2 + b2]), cs[b], ca[b]);
+              for (int b1 = 0; b1 < b2; ++b1) leaf_add(dot3(z[b1], w[b * (b - 1) / 2 + b2]), cs[b], ca[b]);
+            }
           }
         }
       }
@@ -422,7 +429,8 @@ template <typename T, int M, int D, int CS>
 __device__ __forceinline__ void prefix_leaves_terms(const T* __restrict__ As, const uint64_t* binom, int n, int v,
                                                     int k, const T (&W)[D][M - D], const int (&idx)[M], T alpha,
                                                     unsigned long long rank_prefix, const ZBuf<T, D>& zb, bool act,
-                                                    PrefixAcc<T>& acc, T& zmax, const TermsSink& ts) {
+                                                    int sub, int lp, PrefixAcc<T>& acc, T& zmax,
+                                                    const TermsSink& ts) {
   const int bs = M + 1;
   auto emit = [&](T d, unsigned long long rk) {
     rk = ts.qtot - 1 - rk;
@@ -435,7 +443,7 @@ __device__ __forceinline__ void prefix_leaves_terms(const T* __restrict__ As, co
     const unsigned long long rk_col = rank_prefix + rank_part(binom, bs, n, col, 1);
     T colsum = T(0), colabs = T(0);
     if constexpr (D == 2) {
-      for (int q2 = 0; q2 < q; ++q2) {
+      for (int q2 = sub; q2 < q; q2 += lp) {
         T y[2];
         zb.get(q2, y);
         const T d = det2(y, z);
@@ -443,7 +451,7 @@ __device__ __forceinline__ void prefix_leaves_terms(const T* __restrict__ As, co
         leaf_add(d, colsum, colabs);
       }
     } else {
-      for (int q2 = 0; q2 < q; ++q2) {
+      for (int q2 = sub; q2 < q; q2 += lp) {
         T y2[3], w[3];
         zb.get(q2, y2);
         cross3(y2, z, w);
@@ -472,8 +480,8 @@ __device__ __forceinline__ void prefix_leaves_terms(const T* __restrict__ As, co
 // pivots under partial pivoting), above `thr`, or a non-finite scale.
 template <typename T, int M, int D, int CS, bool kTerms>
 __device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint64_t* binom, int n, int v,
-                                           const int (&c)[M - D], const ZBuf<T, D>& zb, T thr, bool act,
-                                           PrefixAcc<T>& acc, const TermsSink& ts) {
+                                           const int (&c)[M - D], const ZBuf<T, D>& zb, T thr, bool act, int sub,
+                                           int lp, PrefixAcc<T>& acc, const TermsSink& ts) {
   constexpr int P = M - D;
   T W[D][P];
   int idx[M];
@@ -493,9 +501,10 @@ __device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint6
     unsigned long long rank_prefix = 0;
 #pragma unroll
     for (int j = 0; j < P; ++j) rank_prefix += rank_part(binom, M + 1, n, c[j], M - j);
-    prefix_leaves_terms<T, M, D, CS>(As, binom, n, v, k, W, idx, alpha, rank_prefix, zb, act, acc, zmax, ts);
+    prefix_leaves_terms<T, M, D, CS>(As, binom, n, v, k, W, idx, alpha, rank_prefix, zb, act, sub, lp, acc, zmax,
+                                     ts);
   } else {
-    prefix_leaves_blocked<T, M, D, CS>(As, v, k, W, idx, alpha, zb, act, acc, zmax);
+    prefix_leaves_blocked<T, M, D, CS>(As, v, k, W, idx, alpha, zb, act, sub, lp, acc, zmax);
   }
   const T growth_bound = (D == 2 ? T(2) : T(4)) * zmax;
   return !(gmax <= thr) || !(growth_bound <= thr) || !(fabs(alpha) <= static_cast<T>(FLT_MAX));
@@ -504,8 +513,18 @@ __device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint6
 // ---------------------------------------------------------------------------
 // Single-matrix prefix kernel.
 // ---------------------------------------------------------------------------
+// Minimum resident blocks per SM the compiler must allow for (register cap)
+// of the binary32 prefix kernels.
+#ifndef RADIC_PREFIX_MIN_BLOCKS_F32
+#define RADIC_PREFIX_MIN_BLOCKS_F32 1
+#endif
+template <typename T>
+__host__ __device__ constexpr int prefix_min_blocks() {
+  return std::is_same<T, float>::value ? RADIC_PREFIX_MIN_BLOCKS_F32 : 1;
+}
+
 template <typename T, int M, int D, bool kMixed, bool kTerms>
-__global__ void __launch_bounds__(128) k_fp_prefix(SingleArgs a, PrefixTable tab) {
+__global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(SingleArgs a, PrefixTable tab) {
   static_assert(M > D, "the prefix needs at least one column");
   constexpr int P = M - D;
   constexpr int CS = ColStride<T, M>::value;
@@ -532,7 +551,10 @@ __global__ void __launch_bounds__(128) k_fp_prefix(SingleArgs a, PrefixTable tab
     int v = tab.v_lo;
     while (v < tab.v_hi && t >= tab.task_start[v + 1]) ++v;
     const unsigned long long runlen = tab.run[v], cnt = tab.count[v];
-    const unsigned long long r0 = (t - tab.task_start[v]) * 32ull * runlen + (unsigned long long)lane * runlen;
+    // lanes [grp * lp, grp * lp + lp) share each prefix of one run
+    const int lp = tab.lanes[v], grp = lane / lp, sub = lane - grp * lp;
+    const unsigned long long groups = 32 / lp;
+    const unsigned long long r0 = (t - tab.task_start[v]) * groups * runlen + (unsigned long long)grp * runlen;
     const unsigned long long r1 = min(r0 + runlen, cnt);
     constexpr int H = P > 1 ? P - 1 : 1;
     int head[H];  // first P-1 prefix columns, a (P-1)-subset of {0..v-1}
@@ -543,12 +565,13 @@ __global__ void __launch_bounds__(128) k_fp_prefix(SingleArgs a, PrefixTable tab
 #pragma unroll
       for (int j = 0; j < P - 1; ++j) c[j] = head[j];
       c[P - 1] = v;
-      const bool flag = prefix_one<T, M, D, CS, kTerms>(sm.As, sm.binom, n, v, c, zb, thr, act, acc, ts);
+      const bool flag = prefix_one<T, M, D, CS, kTerms>(sm.As, sm.binom, n, v, c, zb, thr, act, sub, lp, acc, ts);
       if constexpr (kMixed && !kTerms) {
         if (act && flag) acc.drop_prefix();  // its leaves are recomputed in binary64
-        const unsigned fm = __ballot_sync(kFull, act && flag);
+        // every lane of the group drops its share; the first one records the prefix
+        const unsigned fm = __ballot_sync(kFull, act && flag && sub == 0);
         if (fm) {
-          if (act && flag) {
+          if (act && flag && sub == 0) {
             const int pos = fcnt + __popc(fm & ((1u << lane) - 1u));
             // record the prefix by its rank among all P-subsets of {0..n-1}
             unsigned long long rp = sm.binom[n * bs + P] - 1;

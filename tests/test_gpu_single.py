@@ -68,13 +68,19 @@ OPTS = {
     "prefix2": dict(mapping=3, prefix_depth=2),
     "prefix3": dict(mapping=3, prefix_depth=3),
     "prefix3_r1": dict(mapping=3, prefix_depth=3, ranks_per_task=1, threads_per_block=64),
+    # several lanes share the leaves of one prefix
+    "prefix_lp4": dict(mapping=3, prefix_depth=2, lanes_per_prefix=4),
+    "prefix3_lp8": dict(mapping=3, prefix_depth=3, lanes_per_prefix=8, ranks_per_task=1, threads_per_block=64),
+    "prefix3_lp32": dict(mapping=3, prefix_depth=3, lanes_per_prefix=32),
 }
 
+_LP = ("prefix_lp4", "prefix3_lp8", "prefix3_lp32")
 FP64_LIMIT = {"thread": 8, "thread_l13": 8, "prefix": 10, "prefix_r1": 10, "prefix2": 10, "prefix3": 10,
-              "prefix3_r1": 10}
+              "prefix3_r1": 10, **{k: 10 for k in _LP}}
 MIXED_LIMIT = {"thread": 12, "thread_l13": 12, "prefix": 12, "prefix_r1": 12, "prefix2": 12, "prefix3": 12,
-               "prefix3_r1": 12}
-PAIR_LIMIT = {"prefix": 10, "prefix_r1": 10, "prefix2": 10, "prefix3": 10, "prefix3_r1": 10, "thread": 0}
+               "prefix3_r1": 12, **{k: 12 for k in _LP}}
+PAIR_LIMIT = {"prefix": 10, "prefix_r1": 10, "prefix2": 10, "prefix3": 10, "prefix3_r1": 10, "thread": 0,
+              **{k: 10 for k in _LP}}
 
 
 # ---------------------------------------------------------------------------
@@ -142,6 +148,10 @@ TERM_CASES = [
     (8, 13, np.float32, "prefix2"),
     (10, 15, np.float64, "prefix3"),
     (12, 16, np.float64, "prefix3"),
+    (8, 14, np.float64, "prefix_lp4"),
+    (8, 16, np.float64, "prefix3_lp8"),
+    (6, 20, np.float32, "prefix3_lp32"),
+    (10, 15, np.float64, "prefix3_lp32"),
 ]
 
 
@@ -250,16 +260,18 @@ def _mapping_ok(mapping, m, n, limits):
         return m <= 32
     if mapping == "prefix":
         return 3 <= m <= limits["prefix"] and m <= n
-    if mapping == "prefix3":
+    if mapping in ("prefix3", "prefix3_lp32"):
         return 4 <= m <= limits["prefix"] and m <= n
     return m <= limits["thread"]
 
 
 def _det_opts(mapping):
+    if mapping == "prefix3_lp32":
+        return dict(OPTS[mapping])
     return dict(mapping=3, prefix_depth=3) if mapping == "prefix3" else dict(mapping=mapping)
 
 
-@pytest.mark.parametrize("mapping", ["auto", "thread", "group", "prefix", "prefix3"])
+@pytest.mark.parametrize("mapping", ["auto", "thread", "group", "prefix", "prefix3", "prefix3_lp32"])
 @pytest.mark.parametrize("m,n,dtype", DET_CASES)
 def test_det_fp64_small(m, n, dtype, mapping):
     if not _mapping_ok(mapping, m, n, FP64_LIMIT):
@@ -273,7 +285,7 @@ def test_det_fp64_small(m, n, dtype, mapping):
         assert abs(res["abs_sum"] - float(abs_sum)) <= 1e-12 * float(abs_sum)
 
 
-@pytest.mark.parametrize("mapping", ["auto", "thread", "group", "prefix", "prefix3"])
+@pytest.mark.parametrize("mapping", ["auto", "thread", "group", "prefix", "prefix3", "prefix3_lp32"])
 @pytest.mark.parametrize("m,n,dtype", DET_CASES)
 def test_det_mixed_small(m, n, dtype, mapping):
     if not _mapping_ok(mapping, m, n, MIXED_LIMIT):
@@ -289,7 +301,7 @@ def test_det_mixed_small(m, n, dtype, mapping):
     assert res["tier"] == 1
 
 
-@pytest.mark.parametrize("mapping", ["auto", "prefix", "prefix3"])
+@pytest.mark.parametrize("mapping", ["auto", "prefix", "prefix3", "prefix3_lp32"])
 @pytest.mark.parametrize("m,n,dtype", DET_CASES)
 def test_det_pair_small(m, n, dtype, mapping):
     if not (3 <= m <= 10 and m <= n and _mapping_ok(mapping, m, n, PAIR_LIMIT)):
@@ -357,7 +369,7 @@ def test_det_is_deterministic():
         assert v1 == v2
 
 
-@pytest.mark.parametrize("key", ["thread", "g16", "prefix2", "prefix3"])
+@pytest.mark.parametrize("key", ["thread", "g16", "prefix2", "prefix3", "prefix3_lp8", "prefix3_lp32"])
 def test_mixed_growth_flag_recomputes_in_binary64(key):
     # Partial pivoting grows the last column of this minor to 2^(m-1) times
     # its entries (Wilkinson's example), above the default threshold 64.
@@ -372,7 +384,7 @@ def test_mixed_growth_flag_recomputes_in_binary64(key):
     assert abs(res["value"] - float(val)) <= 8 * m * U32 * h
 
 
-@pytest.mark.parametrize("key", ["prefix2", "prefix3"])
+@pytest.mark.parametrize("key", ["prefix2", "prefix3", "prefix3_lp8"])
 def test_pair_growth_flag_recomputes_in_binary64(key):
     m, n = 9, 11
     w = np.eye(m) - np.tril(np.ones((m, m)), -1)
@@ -498,11 +510,12 @@ def test_full_int8_12x40_exact():
 
 def test_plan_info_reports_the_default_mapping_and_depth():
     info = R().radic_plan_info(8, 32, "mixed")
-    assert info["mapping"] == "prefix" and info["prefix_depth"] == 3  # n - m = 24 <= 3m
-    assert R().radic_plan_info(8, 32, "fp64")["prefix_depth"] == 2    # 24 > 2.5m with 8-byte entries
-    assert R().radic_plan_info(8, 32, "pair")["prefix_depth"] == 2
-    assert R().radic_plan_info(10, 30, "fp64")["prefix_depth"] == 3
-    assert R().radic_plan_info(5, 60, "mixed")["prefix_depth"] == 2   # m < 6
+    assert info["mapping"] == "prefix" and info["prefix_depth"] == 3  # m >= 7, n - m = 24 <= 3.5m
+    assert R().radic_plan_info(8, 32, "fp64")["prefix_depth"] == 3
+    assert R().radic_plan_info(8, 32, "pair")["prefix_depth"] == 3
+    assert R().radic_plan_info(7, 40, "pair")["prefix_depth"] == 2   # n - m = 33 > 3.5m
+    assert R().radic_plan_info(6, 24, "mixed")["prefix_depth"] == 2  # m < 7
+    assert R().radic_plan_info(5, 60, "mixed")["prefix_depth"] == 2
     g = R().radic_plan_info(14, 20, "fp64")
     assert g["mapping"] == "group" and g["group_width"] == 16 and g["prefix_depth"] == 0
     t = R().radic_plan_info(6, 20, "exact")
