@@ -2,6 +2,9 @@
 // planning (mapping, grid, workspace layout) and launches.  Validation happens
 // entirely on the host before anything is enqueued.
 #include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
 
 #include "radic_device.cuh"
 
@@ -124,7 +127,45 @@ int plan_prefix(SinglePlan pl, const radic_options& d, int sms, int per_sm, unsi
 
 // Plans a launch over `units` ranks (C(n,m) for radic_det, `count` for
 // radic_terms).  Returns a RADIC_* code.
+int make_plan_uncached(int m, int n, int mode, const radic_options* o, unsigned long long units, SinglePlan* p);
+
+// Plans are pure functions of (device, shape, mode, options, units); repeated
+// calls on one shape (the common case when serving) reuse the plan instead of
+// repeating the occupancy queries.  The kernel_events pointer is not part of
+// the plan and is filled in per call.
 int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long units, SinglePlan* p) {
+  int dev = 0;
+  // without a device the uncached planner still reports argument errors first
+  if (cudaGetDevice(&dev) != cudaSuccess) return make_plan_uncached(m, n, mode, o, units, p);
+  radic_options key_opts;
+  std::memset(&key_opts, 0, sizeof(key_opts));
+  if (o) key_opts = *o;
+  key_opts.kernel_events = nullptr;
+  const int head[4] = {dev, m, n, mode};
+  std::string key(reinterpret_cast<const char*>(head), sizeof(head));
+  key.append(reinterpret_cast<const char*>(&units), sizeof(units));
+  key.append(reinterpret_cast<const char*>(&key_opts), sizeof(key_opts));
+  static std::mutex mu;
+  static std::unordered_map<std::string, SinglePlan> cache;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *p = it->second;
+      p->events = o ? o->kernel_events : nullptr;
+      return RADIC_OK;
+    }
+  }
+  const int rc = make_plan_uncached(m, n, mode, o, units, p);
+  if (rc == RADIC_OK) {
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache.size() >= 4096) cache.clear();
+    cache.emplace(key, *p);
+  }
+  return rc;
+}
+
+int make_plan_uncached(int m, int n, int mode, const radic_options* o, unsigned long long units, SinglePlan* p) {
   if (m < 1 || m > kMaxM || n < 1 || n > kMaxN || !valid_mode(mode)) return RADIC_EINVAL;
   radic_options d;
   std::memset(&d, 0, sizeof(d));

@@ -110,15 +110,29 @@ __device__ int stage_warp(const BatchArgs& a, const BatchTask& t, int cs, const 
   const void* A = a.A;
   int esum = 0;
   for (int i = 0; i < m; ++i) {
-    double mx = 0.0;
-    for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(load_elem(A, a.dtype, t.offset + (long long)i * n + j)));
+    uint32_t h = 0u;
+    double xm = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      const double x = load_elem(A, a.dtype, t.offset + (long long)i * n + j);
+      const uint32_t hx = hi_abs(x);
+      if (hx > h) {
+        h = hx;
+        xm = x;
+      }
+    }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, off));
-    int e = 0;
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    for (int off = 16; off > 0; off >>= 1) {
+      const uint32_t ho = __shfl_xor_sync(kFull, h, off);
+      const double xo = __shfl_xor_sync(kFull, xm, off);
+      if (ho > h) {
+        h = ho;
+        xm = xo;
+      }
+    }
+    const int e = row_exponent(h, xm);  // the same in every lane
     esum += e;
     for (int j = lane; j < n; j += 32)
-      w.As[j * cs + i] = to_elem<T>(ldexp(load_elem(A, a.dtype, t.offset + (long long)i * n + j), -e));
+      w.As[j * cs + i] = to_elem<T>(scale_pow2(load_elem(A, a.dtype, t.offset + (long long)i * n + j), e));
   }
   for (int idx = lane; idx < (cs - m) * n; idx += 32) {
     const int j = idx / (cs - m), i = m + (idx - j * (cs - m));

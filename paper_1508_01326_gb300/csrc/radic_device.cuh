@@ -352,28 +352,68 @@ __device__ __forceinline__ double load_elem(const void* A, int dtype, long long 
   }
 }
 
+// Row scaling by powers of two with integer operations on the binary64 bits
+// (binary64 arithmetic runs at 1/64 of the binary32 rate on this GPU, and
+// ldexp/frexp take several binary64 operations each).  hi_abs orders
+// magnitudes by the exponent and leading mantissa bits, which is all the
+// exponent of the largest entry needs.
+__device__ __forceinline__ uint32_t hi_abs(double x) {
+  return static_cast<uint32_t>(__double2hiint(x)) & 0x7fffffffu;
+}
+
+// Exponent e with |x| * 2^-e in [0.5, 1) for the entry x whose hi_abs is
+// `h` (0 for a zero, infinite or NaN row maximum, as frexp's convention).
+__device__ __forceinline__ int row_exponent(uint32_t h, double x) {
+  const int be = static_cast<int>(h >> 20);
+  if (h == 0u || be == 0x7ff) return 0;
+  if (be == 0) {  // subnormal maximum: rare, take the library path
+    int e = 0;
+    frexp(x, &e);
+    return e;
+  }
+  return be - 1022;
+}
+
+// x * 2^-e, exact: one multiply by a power of two built from its bits when
+// 2^-e is a normal binary64 number, ldexp otherwise.
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  if (e >= -1022 && e <= 1022) return x * __hiloint2double((1023 - e) << 20, 0);
+  return ldexp(x, -e);
+}
+
 template <typename T>
 __device__ inline int stage_scaled(const void* A, int dtype, int m, int n, long long lda, T* As, int cs,
                                    int* row_exp /* smem, m ints */) {
   // 1. one warp per row: largest magnitude -> exponent e_i (|row| in [0.5, 1) after scaling)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = warp; i < m; i += nw) {
-    double mx = 0.0;
-    for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(load_elem(A, dtype, (long long)i * lda + j)));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, off));
-    if (lane == 0) {
-      int e = 0;
-      if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
-      row_exp[i] = e;
+    uint32_t h = 0u;
+    double xm = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      const double x = load_elem(A, dtype, (long long)i * lda + j);
+      const uint32_t hx = hi_abs(x);
+      if (hx > h) {
+        h = hx;
+        xm = x;
+      }
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const uint32_t ho = __shfl_xor_sync(kFull, h, off);
+      const double xo = __shfl_xor_sync(kFull, xm, off);
+      if (ho > h) {
+        h = ho;
+        xm = xo;
+      }
+    }
+    if (lane == 0) row_exp[i] = row_exponent(h, xm);
   }
   __syncthreads();
-  // 2. scaled copy (binary64 arithmetic, exact power-of-two scaling) into the
-  //    column-major shared copy, padding rows zeroed for vector loads
+  // 2. scaled copy (exact power-of-two scaling) into the column-major shared
+  //    copy, padding rows zeroed for vector loads
   for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
-    As[j * cs + i] = to_elem<T>(ldexp(load_elem(A, dtype, (long long)i * lda + j), -row_exp[i]));
+    As[j * cs + i] = to_elem<T>(scale_pow2(load_elem(A, dtype, (long long)i * lda + j), row_exp[i]));
   }
   for (int idx = threadIdx.x; idx < (cs - m) * n; idx += blockDim.x) {
     const int j = idx / (cs - m), i = m + (idx - j * (cs - m));

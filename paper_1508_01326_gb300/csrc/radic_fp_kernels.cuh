@@ -11,6 +11,9 @@
 #pragma once
 
 #include <cfloat>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "radic_device.cuh"
 
@@ -19,10 +22,23 @@ namespace radic {
 constexpr int kMaxThreadsFp = 256;
 
 // Kernels whose dynamic shared memory exceeds the default 48 KiB must opt in.
+// Raises a kernel's dynamic shared-memory limit above the 48 KB default.  The
+// attribute persists in the device's context, so each (device, kernel) pair
+// is set once to the largest size asked for so far.
 inline bool allow_smem(const void* kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return true;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) ==
-         cudaSuccess;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = done[{dev, kernel}];
+  if (have >= bytes) return true;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) !=
+      cudaSuccess)
+    return false;
+  have = bytes;
+  return true;
 }
 
 // Shared-memory layout of the floating-point kernels.

@@ -521,3 +521,22 @@ def test_plan_info_reports_the_default_mapping_and_depth():
     t = R().radic_plan_info(6, 20, "exact")
     assert t["mapping"] == "thread" and t["threads"] == 128 and t["blocks"] >= 1
     assert t["workspace_bytes"] == R().radic_workspace_bytes(6, 20, "exact")
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "pair"])
+def test_det_extreme_row_scales(mode):
+    # rows far outside binary32 range, one of them subnormal in binary64: the
+    # power-of-two row scaling of the staging step must keep every path exact
+    # up to its rounding
+    a = W.uniform_matrix(31, 5, 11)
+    a[0] *= 1e-310          # subnormal binary64 entries
+    a[1] *= 1e300
+    a[2] *= 2.0 ** -600
+    a[3, 4] = 0.0
+    val, abs_sum = _exact(a)
+    res = R().det(a, mode=mode, options=dict(mapping=3))
+    # relative to sum|terms| (the Hadamard bound overflows binary64 here)
+    tol = {"fp64": 1e-12, "mixed": 1e-5, "pair": 1e-11}[mode]
+    assert abs(float(Fraction(res["value"]) - val)) <= tol * float(abs_sum)
+    assert abs(res["abs_sum"] - float(abs_sum)) <= 1e-5 * float(abs_sum)
+    assert res["status"] == 0
