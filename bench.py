@@ -271,8 +271,10 @@ def measure_configs(R, W, torch) -> dict:
     ws = torch.empty(R.radic_workspace_bytes(12, 40, "exact"), dtype=torch.uint8, device="cuda")
     ms = ev_time(lambda: R.radic_det(a, mode="exact", out=res, workspace=ws))
     r = R.parse_result(res)
+    info = R.radic_plan_info(12, 40, "exact")
     out["int8_12x40_exact"] = {"value": r["minors"] / (ms / 1e3), "unit": UNIT, "ms": ms, "n_primes": r["n_primes"],
-                               "exact_ok": r["exact"] == int(golden_list("int8_12x40")[0][0])}
+                               "exact_ok": r["exact"] == int(golden_list("int8_12x40")[0][0]),
+                               "mapping": f"{info['mapping']} depth {info['prefix_depth']}"}
     # batched 4096
     mats = W.batched_4096()
     minors = sum(math.comb(x.shape[1], x.shape[0]) for x in mats if x.shape[0] <= x.shape[1])

@@ -83,16 +83,17 @@ enum { RADIC_MODE_FP64 = 0, RADIC_MODE_MIXED = 1, RADIC_MODE_EXACT = 2, RADIC_MO
  *            m <= 12 for MIXED and EXACT).
  *  GROUP  -- a group of `group_width` lanes of one warp (16 or 32) factors
  *            one minor, one row per lane, pivot rows shared by warp shuffles.
- *  PREFIX -- FP64 and MIXED, 3 <= m <= 10 (FP64) or 12 (MIXED): one thread
- *            factors the m x (m-D) matrix of an ascending (m-D)-column
- *            prefix once with partial pivoting (D = 2 or 3, the prefix
- *            depth); every minor of that prefix's lexicographic subtree
- *            then costs one D x D determinant of Schur-complement entries
- *            (for D = 3 a scalar triple product).  Same pivots and
- *            elimination steps as per-minor LU, shared by the subtree.
- *  AUTO   -- FP64/MIXED: PREFIX when 3 <= m within its limit, else THREAD
- *            when m <= 8, else GROUP.  EXACT: THREAD when m <= 12, else
- *            GROUP. */
+ *  PREFIX -- 3 <= m <= n, m <= 10 (FP64, PAIR) or 12 (MIXED, EXACT): one
+ *            thread factors the m x (m-D) matrix of an ascending
+ *            (m-D)-column prefix once (D = 2 or 3, the prefix depth;
+ *            partial pivoting, or in EXACT mode the first nonzero pivot of
+ *            a non-dividing elimination mod p); every minor of that
+ *            prefix's lexicographic subtree then costs one D x D
+ *            determinant of Schur-complement entries (for D = 3 a scalar
+ *            triple product).  Same pivots and elimination steps as
+ *            per-minor LU, shared by the subtree.
+ *  AUTO   -- PREFIX when 3 <= m <= n within its limit, else THREAD when
+ *            m <= 8 (12 for EXACT), else GROUP. */
 enum { RADIC_MAP_AUTO = 0, RADIC_MAP_THREAD = 1, RADIC_MAP_GROUP = 2, RADIC_MAP_PREFIX = 3 };
 
 /* Launch and precision options.  Pass NULL for the defaults; a zero field

@@ -179,7 +179,7 @@ int make_plan_uncached(int m, int n, int mode, const radic_options* o, unsigned 
   const int prefix_limit = (mode == kModeFp64)    ? kPrefixMaxMFp64
                            : (mode == kModeMixed) ? kPrefixMaxMFp32
                            : (mode == kModePair)  ? kPrefixMaxMPair
-                                                  : 0;
+                                                  : kPrefixMaxMModp;
   int mapping = d.mapping;
   if (mapping == RADIC_MAP_AUTO) {
     if (m >= 3 && m <= prefix_limit && m <= n) mapping = RADIC_MAP_PREFIX;

@@ -27,6 +27,7 @@ constexpr int kThreadMaxMModp = 12;
 constexpr int kPrefixMaxMFp64 = 10;  // prefix mapping limits
 constexpr int kPrefixMaxMFp32 = 12;
 constexpr int kPrefixMaxMPair = 10;
+constexpr int kPrefixMaxMModp = 12;
 
 // 31-bit primes of the exact mode (largest primes below 2^31).
 constexpr uint32_t kPrime0 = 2147483647u, kPrime1 = 2147483629u, kPrime2 = 2147483587u, kPrime3 = 2147483579u;

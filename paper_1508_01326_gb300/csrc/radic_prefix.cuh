@@ -65,6 +65,19 @@ struct ZBuf<ff, 2> {  // (x.hi, x.lo, y.hi, y.lo) in one 16-byte vector
     p[q * stride] = make_float4(z[0].hi, z[0].lo, z[1].hi, z[1].lo);
   }
 };
+template <>
+struct ZBuf<uint32_t, 2> {  // residues of the exact mode
+  uint2* p;
+  int stride;
+  __device__ ZBuf(void* base, int lane, int stride_, int /*kcap*/)
+      : p(static_cast<uint2*>(base) + lane), stride(stride_) {}
+  __device__ __forceinline__ void get(int q, uint32_t (&y)[2]) const {
+    const uint2 v = p[q * stride];
+    y[0] = v.x;
+    y[1] = v.y;
+  }
+  __device__ __forceinline__ void put(int q, const uint32_t (&z)[2]) const { p[q * stride] = make_uint2(z[0], z[1]); }
+};
 template <typename T>
 struct ZBuf<T, 3> {
   T* p;

@@ -218,6 +218,16 @@ EXACT_CASES = [
     (13, 16, np.int8, "g16", 3),
     (14, 15, np.int32, "g16_l5", 20),
     (18, 19, np.int8, "g32", 2),
+    # prefix mapping in modular arithmetic (non-dividing elimination)
+    (3, 12, np.int32, "prefix", 9),
+    (4, 10, np.int8, "prefix", 1),  # many zeros: prefixes singular mod p
+    (7, 12, np.int8, "prefix3", 3),
+    (8, 14, np.int32, "prefix3", 1000),
+    (6, 16, np.int8, "prefix_lp4", 3),
+    (9, 16, np.int8, "prefix3_lp8", 3),
+    (10, 15, np.int32, "prefix3_lp32", 50),
+    (12, 15, np.int8, "prefix3", 3),
+    (12, 16, np.int8, "prefix2", 2),
 ]
 
 
@@ -327,14 +337,17 @@ def test_pair_mode_rejects_other_mappings_and_shapes():
         R().det(W.uniform_matrix(1, 2, 14), mode="pair")
 
 
+@pytest.mark.parametrize("mapping", ["auto", "thread"])
 @pytest.mark.parametrize("m,n,dtype,bound", [(1, 5, np.int32, 7), (3, 12, np.int32, 9), (5, 9, np.int8, 3),
                                              (8, 11, np.int32, 3000), (10, 13, np.int8, 3),
                                              (12, 13, np.int32, 100), (13, 15, np.int8, 3),
-                                             (16, 17, np.int32, 10), (4, 3, np.int8, 3)])
-def test_det_exact_small(m, n, dtype, bound):
+                                             (16, 17, np.int32, 10), (4, 3, np.int8, 3), (7, 19, np.int8, 1)])
+def test_det_exact_small(m, n, dtype, bound, mapping):
+    if mapping == "thread" and m > 12:
+        pytest.skip("thread mapping of the exact mode: m <= 12")
     a = W.integer_matrix(600 + m * n, m, n, bound, dtype)
     val, _ = _exact(a.astype(np.int64))
-    res = R().det(a, mode="exact")
+    res = R().det(a, mode="exact", options=dict(mapping=mapping))
     assert res["status"] == 0
     assert res["exact"] == val
     assert res["value"] == float(val)
@@ -492,10 +505,12 @@ def test_full_fp64_8x32_sampled_terms(fp64_8x32):
         assert np.all(np.abs(got - want) <= 1e-13 * h)
 
 
-def test_full_int8_10x24_exact():
+@pytest.mark.parametrize("mapping", ["auto", "thread", "prefix2"])
+def test_full_int8_10x24_exact(mapping):
     a = W.int8_10x24()
     exact = orc.radic_det_pfaffian(a.astype(np.int64))
-    res = R().det(a, mode="exact")
+    opts = OPTS[mapping] if mapping == "prefix2" else dict(mapping=mapping)
+    res = R().det(a, mode="exact", options=opts)
     assert res["exact"] == exact
 
 
