@@ -12,9 +12,28 @@
 // incoming gradient.  Binary64 throughout.  A minor with an exactly zero
 // pivot (singular) takes a slow path that forms its cofactors from
 // (m-1) x (m-1) determinants.
+//
+// For 3 <= m the default kernel shares the work per (m-2)-column prefix, as
+// the forward prefix kernels do.  With the prefix rows T (pivot order) and B
+// (the other two), A = A_TT, W = -A_BT A^{-1}, the Schur complement of a leaf
+// (x, y) is S = [z(x) z(y)], z = x_B + W x_T, det(N) = det(A) det(S) for the
+// row-permuted minor N, and by the block inverse
+//   det(N) N^{-1} = det(A) [[det(S) A^{-1} - A^{-1} X_T adj(S) W, -A^{-1} X_T adj(S)],
+//                           [adj(S) W,                            adj(S)]].
+// Summed over the leaves of the prefix with their signs (column parities
+// folded into z~ = (-1)^col z), every candidate column q receives
+//   alpha (-1)^q [W^T; I] g_q,   g_q = rot(Z_>q - Z_<q),   rot(h) = (h1, -h0),
+// where Z_<q and Z_>q are the sums of z~ over the columns before and after
+// q, and the prefix columns receive alpha [s A^{-1} - A^{-1} Q W | -A^{-1} Q]^T
+// with s = sum over leaves of det[z~_x z~_y] and
+// Q = sum_q (-1)^q x_T(q) g_q^T.  A prefix thus costs O(m^2 (m-2) + k m)
+// operations for its k candidate columns and its C(k, 2) leaves, and scatters
+// m (m - 2 + k) gradient entries.  A prefix with an exactly zero pivot falls
+// back to the per-minor cofactors for its leaves.
 #include <algorithm>
+#include <cstring>
 
-#include "radic_fp_kernels.cuh"
+#include "radic_prefix.cuh"
 
 namespace radic {
 namespace {
@@ -215,6 +234,216 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(BwdArgs a) {
   for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) slot[idx] = G[idx];
 }
 
+// Signed cofactors of one minor (columns c) added into the gradient tile G.
+template <int M>
+__device__ __noinline__ void minor_cofactors_scatter(const double* As, int cs, const int (&c)[M], double* G, int n) {
+  double mm[M][M];
+  for (int j = 0; j < M; ++j)
+    for (int i = 0; i < M; ++i) mm[i][j] = As[c[j] * cs + i];
+  int idx[M];
+  bool zp;
+  const double det = lu_full<M>(mm, idx, zp);
+  const double sgn = sign_negative<M>(c) ? -1.0 : 1.0;
+  if (!zp) {
+    double B[M][M];
+    inverse_factors<M>(mm, B);
+    const double s = sgn * det;
+    for (int sl = 0; sl < M; ++sl)
+      for (int j = 0; j < M; ++j) atomicAdd(G + idx[sl] * n + c[j], s * B[j][sl]);
+  } else {
+    double cof[M][M];
+    cofactors_slow<M>(As, cs, c, cof);
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) atomicAdd(G + i * n + c[j], sgn * cof[i][j]);
+  }
+}
+
+template <int M>
+__global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, PrefixTable tab) {
+  constexpr int D = 2, P = M - D;
+  constexpr int CS = ColStride<double, M>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = a.n;
+  const int b = blockIdx.y, chunk = blockIdx.x;
+  uint64_t* binom = reinterpret_cast<uint64_t*>(smem_raw);
+  size_t off = ((size_t)(n + 1) * (M + 1) * 8 + 15) / 16 * 16;
+  double* As = reinterpret_cast<double*>(smem_raw + off);
+  off += ((size_t)n * CS * 8 + 15) / 16 * 16;
+  double* G = reinterpret_cast<double*>(smem_raw + off);  // M x n gradient tile
+  off += ((size_t)M * n * 8 + 15) / 16 * 16;
+  const ZBuf<double, D> zb(smem_raw + off, threadIdx.x, blockDim.x, n - M + D);
+  build_binom(binom, n, M);
+  const double* Ab = a.A + (long long)b * a.stride;
+  for (int idx = threadIdx.x; idx < n * CS; idx += blockDim.x) {
+    const int j = idx / CS, i = idx - j * CS;
+    As[idx] = (i < M) ? Ab[(long long)i * a.lda + j] : 0.0;
+  }
+  for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) G[idx] = 0.0;
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int bs = M + 1;
+  for (unsigned long long t = (unsigned long long)chunk * wpb + warp; t < tab.total_tasks;
+       t += (unsigned long long)a.chunks * wpb) {
+    int v = tab.v_lo;
+    while (v < tab.v_hi && t >= tab.task_start[v + 1]) ++v;
+    const unsigned long long runlen = tab.run[v], cnt = tab.count[v];
+    const unsigned long long r0 = (t - tab.task_start[v]) * 32ull * runlen + (unsigned long long)lane * runlen;
+    const unsigned long long r1 = min(r0 + runlen, cnt);
+    if (r0 >= r1) continue;  // lanes past the group's end (no warp-wide operations below)
+    constexpr int H = P > 1 ? P - 1 : 1;
+    int head[H];
+    if constexpr (P > 1) unrank<P - 1>(r0, v, binom, bs, head);
+    const int k = n - 1 - v;
+    for (unsigned long long r = r0; r < r1; ++r) {
+      int c[P];
+#pragma unroll
+      for (int j = 0; j < P - 1; ++j) c[j] = head[j];
+      c[P - 1] = v;
+      // factor the M x P prefix: partial pivoting, L \ U packed in fa
+      double fa[M][P];
+#pragma unroll
+      for (int j = 0; j < P; ++j)
+#pragma unroll
+        for (int i = 0; i < M; ++i) fa[i][j] = As[c[j] * CS + i];
+      int idx[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) idx[i] = i;
+      bool neg = false, zp = false;
+      double prod = 1.0;
+#pragma unroll
+      for (int kk = 0; kk < P; ++kk) {
+#pragma unroll
+        for (int i = kk + 1; i < M; ++i) {
+          const bool sw = mag_key(fa[i][kk]) > mag_key(fa[kk][kk]);
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            const double x = fa[kk][j], y = fa[i][j];
+            fa[kk][j] = sw ? y : x;
+            fa[i][j] = sw ? x : y;
+          }
+          const int ik = idx[kk], ii = idx[i];
+          idx[kk] = sw ? ii : ik;
+          idx[i] = sw ? ik : ii;
+          neg ^= sw;
+        }
+        const double piv = fa[kk][kk];
+        zp |= (piv == 0.0);
+        prod *= piv;
+        const double rr = rcp_f64(piv);
+#pragma unroll
+        for (int i = kk + 1; i < M; ++i) {
+          const double l = fa[i][kk] * rr;
+          fa[i][kk] = l;
+#pragma unroll
+          for (int j = kk + 1; j < P; ++j) fa[i][j] = fma(-l, fa[kk][j], fa[i][j]);
+        }
+      }
+      if (zp) {  // singular prefix: per-minor cofactors of its leaves
+        for (int x = v + 1; x < n; ++x)
+          for (int y = x + 1; y < n; ++y) {
+            int cm[M];
+            for (int j = 0; j < P; ++j) cm[j] = c[j];
+            cm[P] = x;
+            cm[P + 1] = y;
+            minor_cofactors_scatter<M>(As, CS, cm, G, n);
+          }
+      } else {
+        // W = -L21 L11^{-1} (D x P) and Ainv = U11^{-1} L11^{-1} (P x P)
+        double W[D][P];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+#pragma unroll
+          for (int j = P - 1; j >= 0; --j) {
+            double sum = -fa[P + d][j];
+#pragma unroll
+            for (int i = j + 1; i < P; ++i) sum = fma(-W[d][i], fa[i][j], sum);
+            W[d][j] = sum;
+          }
+        }
+        double Ai[P][P];
+        {
+          double top[P][P];
+#pragma unroll
+          for (int i = 0; i < P; ++i)
+#pragma unroll
+            for (int j = 0; j < P; ++j) top[i][j] = fa[i][j];
+          inverse_factors<P>(top, Ai);
+        }
+        int sp = M * (M + 1) / 2 + D;
+#pragma unroll
+        for (int j = 0; j < P; ++j) sp += c[j] + 1;
+        const double alpha = ((sp & 1) != neg) ? -prod : prod;
+        // pass 1: z~ of every candidate column, their sum, and s
+        double zt0 = 0.0, zt1 = 0.0, ssum = 0.0;
+        for (int q = 0; q < k; ++q) {
+          const int col = v + 1 + q;
+          double z[D];
+          prefix_column<double, M, D>(As + col * CS, W, idx, z);
+          if (col & 1) {
+            z[0] = -z[0];
+            z[1] = -z[1];
+          }
+          ssum = fma(zt0, z[1], fma(-zt1, z[0], ssum));  // det[Z_<q, z~_q]
+          zt0 += z[0];
+          zt1 += z[1];
+          zb.put(q, z);
+        }
+        // pass 2: candidate-column gradients and Q
+        double Q[P][D];
+#pragma unroll
+        for (int i = 0; i < P; ++i) Q[i][0] = Q[i][1] = 0.0;
+        double zp0 = 0.0, zp1 = 0.0;
+        for (int q = 0; q < k; ++q) {
+          const int col = v + 1 + q;
+          double z[D];
+          zb.get(q, z);
+          const double h0 = zt0 - 2.0 * zp0 - z[0], h1 = zt1 - 2.0 * zp1 - z[1];
+          const double g0 = h1, g1 = -h0;  // rot(Z_>q - Z_<q)
+          zp0 += z[0];
+          zp1 += z[1];
+          const double sc = (col & 1) ? -alpha : alpha;
+          double* gcol = G + col;
+#pragma unroll
+          for (int r = 0; r < P; ++r) atomicAdd(gcol + idx[r] * n, sc * fma(W[0][r], g0, W[1][r] * g1));
+          atomicAdd(gcol + idx[P] * n, sc * g0);
+          atomicAdd(gcol + idx[P + 1] * n, sc * g1);
+          const double sgn = (col & 1) ? -1.0 : 1.0;
+          const double* xc = As + col * CS;
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            const double xt = sgn * xc[idx[i]];
+            Q[i][0] = fma(xt, g0, Q[i][0]);
+            Q[i][1] = fma(xt, g1, Q[i][1]);
+          }
+        }
+        // prefix columns: alpha [s Ainv - Ainv Q W | -Ainv Q]^T
+#pragma unroll
+        for (int tt = 0; tt < P; ++tt) {
+          double R0 = 0.0, R1 = 0.0;  // (Ainv Q)[tt][:]
+#pragma unroll
+          for (int u = 0; u < P; ++u) {
+            R0 = fma(Ai[tt][u], Q[u][0], R0);
+            R1 = fma(Ai[tt][u], Q[u][1], R1);
+          }
+          double* gcol = G + c[tt];
+#pragma unroll
+          for (int r = 0; r < P; ++r)
+            atomicAdd(gcol + idx[r] * n, alpha * (ssum * Ai[tt][r] - fma(R0, W[0][r], R1 * W[1][r])));
+          atomicAdd(gcol + idx[P] * n, -alpha * R0);
+          atomicAdd(gcol + idx[P + 1] * n, -alpha * R1);
+        }
+      }
+      if constexpr (P > 1) {
+        if (r + 1 < r1) successor<P - 1>(head, v);
+      }
+    }
+  }
+  __syncthreads();
+  double* slot = a.slots + ((size_t)b * a.chunks + chunk) * (size_t)M * n;
+  for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) slot[idx] = G[idx];
+}
+
 // grad_A[b] = grad_out[b] * sum over chunks (in order) of the tiles.
 __global__ void k_backward_reduce(const double* slots, int batch, int m, int n, int chunks, const double* grad_out,
                                   double* grad, long long lda, long long stride) {
@@ -242,6 +471,72 @@ const void* bwd_kernel(int m) {
     case 8: return reinterpret_cast<const void*>(&k_backward<8>);
     default: return nullptr;
   }
+}
+
+template <int M>
+const void* bwd_prefix_kernel_m() {
+  if constexpr (M >= 3) return reinterpret_cast<const void*>(&k_backward_prefix<M>);
+  else return nullptr;
+}
+
+const void* bwd_prefix_kernel(int m) {
+  switch (m) {
+    case 3: return bwd_prefix_kernel_m<3>();
+    case 4: return bwd_prefix_kernel_m<4>();
+    case 5: return bwd_prefix_kernel_m<5>();
+    case 6: return bwd_prefix_kernel_m<6>();
+    case 7: return bwd_prefix_kernel_m<7>();
+    case 8: return bwd_prefix_kernel_m<8>();
+    default: return nullptr;
+  }
+}
+
+// Work split of the prefix backward: prefixes grouped by their last column v
+// (k = n-1-v candidate columns), warp tasks of 32 lanes x a run of prefixes,
+// run lengths from a cost model (factorisation m P^2 + P^3, per candidate
+// column m + 4P and 2(m + P) gradient entries), `chunks` blocks per matrix.
+void bwd_prefix_plan(int batch, int m, int n, int sms, int* chunks, PrefixTable* tab) {
+  const int P = m - 2;
+  PrefixTable t;
+  std::memset(&t, 0, sizeof(t));
+  t.v_lo = P - 1;
+  t.v_hi = n - 3;
+  double cost[kMaxN] = {0}, total = 0.0;
+  for (int v = t.v_lo; v <= t.v_hi; ++v) {
+    const int k = n - 1 - v;
+    t.count[v] = binom_host(v, P - 1);
+    cost[v] = (double)m * P * P + (double)P * P * P + (double)k * (3.0 * m + 6.0 * P);
+    total += cost[v] * (double)t.count[v];
+  }
+  const long long want = (long long)(sms > 0 ? sms : 1) * 16;  // about 16 blocks per SM in all
+  long long ch = (want + batch - 1) / batch;
+  if (ch > 65535) ch = 65535;
+  if (ch < 1) ch = 1;
+  const double per_lane = total / ((double)ch * kBwdThreads) / 2.0;  // about two tasks per warp
+  unsigned long long start = 0;
+  for (int v = t.v_lo; v <= t.v_hi; ++v) {
+    double r = per_lane / cost[v];
+    unsigned long long run = r < 1.0 ? 1ull : (unsigned long long)r;
+    const unsigned long long maxrun = (t.count[v] + 31) / 32;
+    if (run > maxrun) run = maxrun > 0 ? maxrun : 1;
+    t.lanes[v] = 1;
+    t.run[v] = run;
+    t.task_start[v] = start;
+    start += (t.count[v] + 32 * run - 1) / (32 * run);
+  }
+  if (t.v_hi + 1 < kMaxN) t.task_start[t.v_hi + 1] = start;
+  t.total_tasks = start;
+  *chunks = (int)ch;
+  *tab = t;
+}
+
+size_t bwd_prefix_smem(int m, int n) {
+  const int cs = ((m + 1) / 2) * 2;
+  size_t off = ((size_t)(n + 1) * (m + 1) * 8 + 15) / 16 * 16;
+  off += ((size_t)n * cs * 8 + 15) / 16 * 16;
+  off += ((size_t)m * n * 8 + 15) / 16 * 16;
+  off += zbuf_bytes(n - m + 2, kBwdThreads, 2, 8);
+  return off;
 }
 
 int bwd_chunks(int batch, unsigned long long total) {
@@ -273,7 +568,11 @@ extern "C" {
 size_t radic_backward_workspace_bytes(int batch, int m, int n) {
   if (batch < 1 || m < 1 || m > kBwdMaxM || n < 1 || n > kMaxN) return 0;
   const unsigned long long total = (m <= n) ? binom_host(n, m) : 0ull;
-  const int chunks = bwd_chunks(batch, total);
+  int chunks = bwd_chunks(batch, total);
+  if (m >= 3 && m <= n) {
+    PrefixTable tab;
+    bwd_prefix_plan(batch, m, n, device_sm_count(), &chunks, &tab);
+  }
   return align_up((size_t)batch * chunks * m * n * sizeof(double), 256) + 256;
 }
 
@@ -302,10 +601,19 @@ int radic_det_backward(const double* A, int batch, int m, int n, int64_t lda, in
   a.total = binom_host(n, m);
   a.chunks = bwd_chunks(batch, a.total);
   a.slots = static_cast<double*>(workspace);
-  const void* k = bwd_kernel(m);
-  const size_t smem = bwd_smem(m, n);
-  if (!allow_smem(k, smem)) return RADIC_EUNSUPPORTED;
-  void* params[] = {&a};
+  PrefixTable tab;
+  const void* k;
+  size_t smem;
+  if (m >= 3) {  // prefix-shared backward
+    bwd_prefix_plan(batch, m, n, device_sm_count(), &a.chunks, &tab);
+    k = bwd_prefix_kernel(m);
+    smem = bwd_prefix_smem(m, n);
+  } else {
+    k = bwd_kernel(m);
+    smem = bwd_smem(m, n);
+  }
+  if (!k || !allow_smem(k, smem)) return RADIC_EUNSUPPORTED;
+  void* params[] = {&a, &tab};
   if (cudaLaunchKernel(k, dim3(a.chunks, batch), dim3(kBwdThreads), params, smem, s) != cudaSuccess)
     return RADIC_ECUDA;
   const long long total = (long long)batch * m * n;

@@ -31,7 +31,8 @@ def R():
     return R_
 
 
-@pytest.mark.parametrize("m,n", [(1, 6), (2, 5), (3, 7), (4, 9), (5, 5), (6, 10), (7, 10), (8, 11), (4, 3)])
+@pytest.mark.parametrize("m,n", [(1, 6), (2, 5), (3, 7), (4, 9), (5, 5), (6, 10), (7, 10), (8, 11), (4, 3),
+                                 (3, 14), (5, 16), (8, 13)])
 def test_backward_matches_exact_gradient(m, n):
     rng = np.random.default_rng(100 * m + n)
     mats = rng.uniform(-1, 1, (3, m, n))
@@ -45,6 +46,21 @@ def test_backward_matches_exact_gradient(m, n):
             want = np.array([[float(x) for x in row] for row in orc.radic_grad_exact(mats[b], use_pfaffian=False)])
         scale = max(np.abs(want).max(), 1e-300)
         assert np.abs(grad[b] - float(g_out[b]) * want).max() <= 1e-11 * scale * max(1.0, abs(float(g_out[b])))
+
+
+def test_backward_singular_prefixes():
+    # integer entries with a repeated column and a zero column: prefixes that
+    # contain both copies, or the zero column, have an exactly zero pivot and
+    # take the per-minor path for their leaves
+    a = W.integer_matrix(17, 5, 10, 4, np.int32).astype(np.float64)
+    a[:, 3] = a[:, 1]
+    a[:, 6] = 0.0
+    mats = np.stack([a, W.integer_matrix(18, 5, 10, 4, np.int32).astype(np.float64)])
+    grad = R().radic_det_backward(torch.from_numpy(mats).cuda(), torch.ones(2, dtype=torch.float64,
+                                                                           device="cuda")).cpu().numpy()
+    for b in range(2):
+        want = np.array([[float(x) for x in row] for row in orc.radic_grad_exact(mats[b], use_pfaffian=False)])
+        assert np.abs(grad[b] - want).max() <= 1e-11 * max(np.abs(want).max(), 1.0)
 
 
 def test_autograd_function_and_gradcheck():
