@@ -224,7 +224,10 @@ typedef struct radic_batch_tuning {
   int32_t prefix_depth[RADIC_MAX_M + 1]; /* 2, 3, or 0 for the default rule */
   int32_t tiers;           /* MIXED: allowed low tiers, bit 0 binary32, bit 1
                               pairs (0: both); binary64 is always allowed  */
-  int32_t reserved[6];
+  int32_t head_sharing;    /* prefix tasks with m - D - 1 >= 5: factor each
+                              head (first m-D-1 columns) once for all its
+                              prefixes (0: on, -1: off)                      */
+  int32_t reserved[5];
 } radic_batch_tuning;
 
 /* Builds the plan of `batch` matrices: matrix b is m[b] x n[b], row-major

@@ -46,7 +46,8 @@ class RadicBatchTuning(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_int32),
         ("prefix_depth", ctypes.c_int32 * (RADIC_MAX_M + 1)),
         ("tiers", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("head_sharing", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 _lib = None

@@ -173,11 +173,13 @@ TIERS = {"fp32": 1, "pair": 2}
 
 
 def make_tuning(kind=None, task_cost=None, tol=0.0, growth_threshold=0.0, blocks_per_sm=0,
-                prefix_depth=None, tiers=None) -> "L.RadicBatchTuning":
+                prefix_depth=None, tiers=None, head_sharing=True) -> "L.RadicBatchTuning":
     """Batched-path tuning: `kind`, `task_cost` and `prefix_depth` map m to a mapping name, a task size
     and a prefix depth (2 or 3); `tiers` lists the low tiers the mixed router may use ("fp32",
-    "pair"; default both; binary64 is always available)."""
+    "pair"; default both; binary64 is always available); `head_sharing` factors each prefix head
+    once for all its prefixes."""
     t = L.RadicBatchTuning()
+    t.head_sharing = 0 if head_sharing else -1
     if tiers is not None:
         mask = 0
         for name in tiers:

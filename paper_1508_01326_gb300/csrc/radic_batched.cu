@@ -38,6 +38,7 @@ struct BatchTask {
   unsigned long long lim;   // prefixes in the group, or C(n,m): end of the range
   int b, m, n, v;           // matrix, shape, prefix group
   int kind, tier;           // kKindMinor or the prefix depth; kModeMixed, kModePair or kModeFp64
+  int shared;               // prefix kind: units are heads (first m-D-1 columns, v = their last column)
 };
 
 struct BatchHeader {
@@ -193,6 +194,56 @@ __device__ bool run_prefix(const BatchArgs& a, const BatchTask& t, const WarpSli
   return flagged;
 }
 
+// Head-shared prefix task: each lane takes a run of heads (the first
+// H = m-D-1 prefix columns, H-1 of them from {0..u-1} plus u = t.v), factors
+// each head once and appends every last column v = u+1 .. n-1-D in turn.
+template <typename T, int M, int D, bool kFlag>
+__device__ bool run_prefix_heads(const BatchArgs& a, const BatchTask& t, const WarpSlice<T>& w, TaskAcc<T>& acc,
+                                 unsigned long long first, unsigned long long last) {
+  constexpr int CS = ColStride<T, M>::value;
+  constexpr int P = M - D, H = P - 1;
+  static_assert(H >= 2, "head sharing needs a head of two or more columns");
+  const int lane = threadIdx.x & 31;
+  const int u = t.v;
+  const T thr = static_cast<T>(a.growth);
+  bool flagged = false;
+  int hc[H - 1];  // first H-1 head columns, an (H-1)-subset of {0..u-1}
+  unrank<H - 1>(first < t.lim ? first : 0ull, u, w.binom, M + 1, hc);
+  TermsSink ts{nullptr, 0, 0, 0, 0};
+  const ZBuf<T, D> zb(w.zbuf, lane, 32, t.n - M + D);
+  for (unsigned long long it = 0; it < t.run; ++it) {
+    const bool act = first + it < last;
+    int c[P];
+#pragma unroll
+    for (int j = 0; j < H - 1; ++j) c[j] = hc[j];
+    c[H - 1] = u;
+    T W1[D + 1][H];
+    int idx1[M];
+    T prod1, gmax1;
+    bool neg1;
+    {
+      int ch[H];
+#pragma unroll
+      for (int j = 0; j < H; ++j) ch[j] = c[j];
+      prefix_factor<T, M, D + 1, CS>(w.As, ch, W1, idx1, prod1, gmax1, neg1);
+    }
+    for (int v = u + 1; v <= t.n - 1 - D; ++v) {
+      c[P - 1] = v;
+      T W[D][P];
+      int idx[M];
+      T prod, gmax;
+      bool neg;
+      prefix_extend<T, M, D, CS>(w.As, v, W1, idx1, prod1, gmax1, neg1, W, idx, prod, gmax, neg);
+      const bool f = prefix_leaves<T, M, D, CS, false>(w.As, w.binom, t.n, v, c, W, idx, prod, gmax, neg, zb, thr, act,
+                                                       0, 1, acc.p, ts);
+      if (kFlag && act && f) flagged = true;
+      acc.p.end_prefix();
+    }
+    if (first + it + 1 < last) successor<H - 1>(hc, u);
+  }
+  return flagged;
+}
+
 // Works one task in the warp; returns (in every lane) whether a lane flagged.
 template <typename T, int M, bool kFlag>
 __device__ bool run_task(const BatchArgs& a, const BatchTask& t, const WarpSlice<T>& w, TaskAcc<T>& acc) {
@@ -202,7 +253,11 @@ __device__ bool run_task(const BatchArgs& a, const BatchTask& t, const WarpSlice
   bool flagged = false;
   const unsigned long long first = t.r0 + (unsigned long long)lane * t.run;
   const unsigned long long last = min(first + t.run, t.lim);
-  if (t.kind == 2) {
+  if (t.kind == 2 && t.shared) {
+    if constexpr (M >= 5) flagged = run_prefix_heads<T, M, 2, kFlag>(a, t, w, acc, first, last);
+  } else if (t.kind == 3 && t.shared) {
+    if constexpr (M >= 6) flagged = run_prefix_heads<T, M, 3, kFlag>(a, t, w, acc, first, last);
+  } else if (t.kind == 2) {
     if constexpr (M >= 3) flagged = run_prefix<T, M, 2, kFlag>(a, t, w, acc, first, last);
   } else if (t.kind == 3) {
     if constexpr (M >= 4) flagged = run_prefix<T, M, 3, kFlag>(a, t, w, acc, first, last);
@@ -266,7 +321,9 @@ __device__ void do_task(const BatchArgs& a, const BatchTask& t, unsigned char* s
       if (!kFlag && t.tier != kModeFp64) {
         const unsigned long long units = min(32ull * t.run, t.lim - t.r0);
         const int D = t.kind;
-        redone = (long long)(D == kKindMinor ? units : units * c_binom.v[t.n - 1 - t.v][D]);
+        redone = (long long)(D == kKindMinor ? units
+                             : t.shared     ? units * c_binom.v[t.n - 1 - t.v][D + 1]
+                                            : units * c_binom.v[t.n - 1 - t.v][D]);
       }
       a.slots[slot_id] = FpPartial{d.hi, d.lo, ab, redone};
     }
@@ -406,6 +463,18 @@ namespace {
 
 double cost_minor(int m) { return 10.0 * m * m * m / 3.0 + 40.0; }
 
+// Cost of one head (H = m-D-1 columns, last column u): its factorisation,
+// then per appended column v one elimination step and the prefix's leaves.
+double head_cost(int m, int D, int n, int u) {
+  const int H = m - D - 1, P = m - D;
+  double c = (double)m * H * H;
+  for (int v = u + 1; v <= n - 1 - D; ++v) {
+    const int k = n - 1 - v;
+    c += m + 4.0 * (D + 1) * H + prefix_cost(m, D, k) - (double)m * P * P;
+  }
+  return c;
+}
+
 int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* tun) {
   const int m = pl.shape[2 * b], n = pl.shape[2 * b + 1];
   std::vector<BatchTask>& out = (tier == kModeFp64) ? pl.t64 : pl.t32;
@@ -424,7 +493,29 @@ int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* 
   t.n = n;
   t.kind = kind;
   t.tier = tier;
-  if (kind != kKindMinor) {
+  // Head sharing pays from heads of five columns on (measured on the batched
+  // m = 5..10 sets: 25% faster at m = 10, depth 3; slower below four head
+  // columns, where heads are few and their work uneven).
+  const bool share = kind != kKindMinor && m - kind - 1 >= 5 && !(tun && tun->head_sharing < 0);
+  if (share) {
+    // head-shared tasks: group u = last head column, C(u, H-1) heads each
+    const int D = kind, H = m - D - 1;
+    t.shared = 1;
+    for (int u = H - 1; u <= n - 2 - D; ++u) {
+      const unsigned long long cnt = binom_host(u, H - 1);
+      const double c = head_cost(m, D, n, u);
+      unsigned long long run = (unsigned long long)std::max(1.0, std::floor(lane_cost / c));
+      run = std::min(run, (cnt + 31) / 32);
+      if (run < 1) run = 1;
+      for (unsigned long long r0 = 0; r0 < cnt; r0 += 32 * run) {
+        t.v = u;
+        t.r0 = r0;
+        t.run = run;
+        t.lim = cnt;
+        out.push_back(t);
+      }
+    }
+  } else if (kind != kKindMinor) {
     const int D = kind, P = m - D;
     for (int v = P - 1; v <= n - 1 - D; ++v) {
       const unsigned long long cnt = binom_host(v, P - 1);
@@ -457,6 +548,7 @@ int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* 
 }
 
 double task_cost(const BatchTask& t) {
+  if (t.kind != kKindMinor && t.shared) return (double)t.run * head_cost(t.m, t.kind, t.n, t.v);
   if (t.kind != kKindMinor) return (double)t.run * prefix_cost(t.m, t.kind, t.n - 1 - t.v);
   return (double)t.run * cost_minor(t.m);
 }

@@ -483,24 +483,20 @@ __device__ __forceinline__ void prefix_leaves_terms(const T* __restrict__ As, co
   }
 }
 
-// Processes one prefix c[0..m-D-1] (last column v): factors it, reduces every
-// later column to its D-entry Schur complement and forms the D x D leaf
-// determinants with the sign of Eq. (1), adding them to acc.pre (the caller
-// commits or drops them).  D = 2: det = z1[0] z2[1] - z1[1] z2[0].  D = 3:
-// det = z1 . (z2 x z3), the cross product formed once per pair (c2, c3).
+// Leaf phase of one factored prefix c[0..m-D-1] (last column v): reduces
+// every later column to its D-entry Schur complement and forms the D x D
+// leaf determinants with the sign of Eq. (1), adding them to acc.pre (the
+// caller commits or drops them).  D = 2: det = z1[0] z2[1] - z1[1] z2[0].
+// D = 3: det = z1 . (z2 x z3), the cross product formed once per pair.
 // `zb` is this lane's column buffer.  Returns the growth flag of the mixed
 // mode: largest prefix pivot, or 2^(D-1) max|z| (a bound for the last D
 // pivots under partial pivoting), above `thr`, or a non-finite scale.
 template <typename T, int M, int D, int CS, bool kTerms>
-__device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint64_t* binom, int n, int v,
-                                           const int (&c)[M - D], const ZBuf<T, D>& zb, T thr, bool act, int sub,
-                                           int lp, PrefixAcc<T>& acc, const TermsSink& ts) {
+__device__ __forceinline__ bool prefix_leaves(const T* __restrict__ As, const uint64_t* binom, int n, int v,
+                                              const int (&c)[M - D], const T (&W)[D][M - D], const int (&idx)[M],
+                                              T prod, T gmax, bool neg, const ZBuf<T, D>& zb, T thr, bool act,
+                                              int sub, int lp, PrefixAcc<T>& acc, const TermsSink& ts) {
   constexpr int P = M - D;
-  T W[D][P];
-  int idx[M];
-  T prod, gmax;
-  bool neg;
-  prefix_factor<T, M, D, CS>(As, c, W, idx, prod, gmax, neg);
   // parity of r = M(M+1)/2, of the prefix columns' share of s, and of the D
   // leaf columns' "+1" terms; the leaf columns' own parities are folded in
   // per column
@@ -521,6 +517,81 @@ __device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint6
   }
   const T growth_bound = (D == 2 ? T(2) : T(4)) * zmax;
   return !(gmax <= thr) || !(growth_bound <= thr) || !(fabs(alpha) <= static_cast<T>(FLT_MAX));
+}
+
+// Processes one prefix c[0..m-D-1] (last column v): factors it, then its
+// leaves (prefix_leaves).
+template <typename T, int M, int D, int CS, bool kTerms>
+__device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint64_t* binom, int n, int v,
+                                           const int (&c)[M - D], const ZBuf<T, D>& zb, T thr, bool act, int sub,
+                                           int lp, PrefixAcc<T>& acc, const TermsSink& ts) {
+  constexpr int P = M - D;
+  T W[D][P];
+  int idx[M];
+  T prod, gmax;
+  bool neg;
+  prefix_factor<T, M, D, CS>(As, c, W, idx, prod, gmax, neg);
+  return prefix_leaves<T, M, D, CS, kTerms>(As, binom, n, v, c, W, idx, prod, gmax, neg, zb, thr, act, sub, lp, acc,
+                                            ts);
+}
+
+// Head sharing: the prefixes whose first H = m-D-1 columns (the head) agree
+// share those H elimination steps.  The head is factored once with
+// prefix_factor at depth D+1 (W1 = -L21 L11^{-1} for the D+1 rows left);
+// appending the prefix's last column v then costs one more elimination step:
+// s = the D+1 Schur-complement entries of column v, partial pivoting among
+// them by the same compare-and-swap rule, and with l_d = s_{d+1} / s_0
+//   W[d][j] = W1[d+1][j] - l_d W1[0][j]  (j < H),   W[d][H] = -l_d.
+// Same pivots and elimination steps as factoring the prefix from scratch.
+template <typename T, int M, int D, int CS>
+__device__ __forceinline__ void prefix_extend(const T* __restrict__ As, int v, const T (&W1)[D + 1][M - D - 1],
+                                              const int (&idx1)[M], T prod1, T gmax1, bool neg1, T (&W)[D][M - D],
+                                              int (&idx)[M], T& prod, T& gmax, bool& neg) {
+  constexpr int H = M - D - 1;
+  T s[D + 1];
+  prefix_column<T, M, D + 1>(As + v * CS, W1, idx1, s);
+  T Wr[D + 1][H];
+  int ir[D + 1];
+#pragma unroll
+  for (int r = 0; r <= D; ++r) {
+    ir[r] = idx1[H + r];
+#pragma unroll
+    for (int j = 0; j < H; ++j) Wr[r][j] = W1[r][j];
+  }
+  bool ng = neg1;
+#pragma unroll
+  for (int r = 1; r <= D; ++r) {
+    const bool sw = fabs(s[r]) > fabs(s[0]);
+    const T a0 = s[0], ar = s[r];
+    s[0] = sw ? ar : a0;
+    s[r] = sw ? a0 : ar;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const T x = Wr[0][j], y = Wr[r][j];
+      Wr[0][j] = sw ? y : x;
+      Wr[r][j] = sw ? x : y;
+    }
+    const int i0 = ir[0], irr = ir[r];
+    ir[0] = sw ? irr : i0;
+    ir[r] = sw ? i0 : irr;
+    ng ^= sw;
+  }
+  const T piv = s[0];
+  const T rr = rcp_t(piv);
+  prod = prod1 * piv;
+  gmax = fmax(gmax1, fabs(piv));
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const T l = s[d + 1] * rr;
+#pragma unroll
+    for (int j = 0; j < H; ++j) W[d][j] = fma(-l, Wr[0][j], Wr[d + 1][j]);
+    W[d][H] = -l;
+  }
+#pragma unroll
+  for (int j = 0; j < H; ++j) idx[j] = idx1[j];
+#pragma unroll
+  for (int r = 0; r <= D; ++r) idx[H + r] = ir[r];
+  neg = ng;
 }
 
 // ---------------------------------------------------------------------------

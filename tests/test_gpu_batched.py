@@ -120,6 +120,21 @@ def test_batch_prefix_depths_match_oracle(depth):
         assert abs(Fraction(r["value"]) - val) <= Fraction(1e-12) * abs_sum
 
 
+@pytest.mark.parametrize("mode,tiers", [("fp64", None), ("mixed", ["pair"]), ("mixed", ["fp32"])])
+@pytest.mark.parametrize("head_sharing", [True, False])
+def test_batch_head_sharing_matches_oracle(mode, tiers, head_sharing):
+    mats = small_batch(8, 40, max_m=10, max_d=10)
+    kw = dict(head_sharing=head_sharing, task_cost={m: 5000 for m in range(1, 11)})
+    if mode == "mixed":
+        kw.update(tiers=tiers, tol=1.0 if tiers == ["fp32"] else 1e-10)
+    res, _ = run_batch(mats, mode, tuning=R().make_tuning(**kw))
+    for a, r in zip(mats, res):
+        val, abs_sum = orc.radic_det_exact(a)
+        m = a.shape[0]
+        tol = {0: 1e-12, 3: 1e-11}.get(r["tier"], 8 * m * 2.0 ** -24)
+        assert abs(float(Fraction(r["value"]) - val)) <= tol * float(abs_sum)
+
+
 def test_batch_is_deterministic():
     mats = small_batch(3, 50, max_d=12)
     tuning = R().make_tuning(tol=1.0)
