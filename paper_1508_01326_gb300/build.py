@@ -25,8 +25,12 @@ SOURCES = [
     "radic_mixed.cu",
     "radic_pair.cu",
     "radic_modp.cu",
+    "radic_modp_prefix.cu",
     "radic_noalloc.cu",
     "radic_batched.cu",
+    "radic_batched_k32.cu",
+    "radic_batched_kpair.cu",
+    "radic_batched_k64.cu",
     "radic_backward.cu",
 ]
 

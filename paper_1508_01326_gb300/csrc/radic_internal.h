@@ -133,6 +133,16 @@ size_t smem_mixed(const SinglePlan& p);
 size_t smem_pair(const SinglePlan& p);
 size_t smem_modp(const SinglePlan& p);
 
+// Persistent batched kernels per m (argument: the batched path's BatchArgs):
+// binary32 tier, pair tier (m >= 3), binary64 tier; nullptr outside 1..10.
+const void* batch_kernel_f32(int m);
+const void* batch_kernel_pair(int m);
+const void* batch_kernel_f64(int m);
+
+// Prefix kernel of the EXACT mode for (m, depth) (arguments: SingleArgs,
+// PrefixTable), or nullptr.
+const void* modp_prefix_kernel(int m, int depth, bool terms);
+
 // Binary64 fix-up kernel of the MIXED and PAIR modes (arguments: SingleArgs,
 // int main_blocks, int tier) and its dynamic shared memory.
 const void* mixed_fixup_kernel(int m);
