@@ -204,6 +204,19 @@ int radic_terms(const void* A, int m, int n, int64_t lda, int dtype, int mode,
 int radic_unrank(int n, int m, uint64_t q0, uint64_t count, uint8_t* cols,
                  const radic_options* opts, void* stream);
 
+/* A captured CUDA graph of one radic_det call on fixed buffers (opaque). */
+typedef struct radic_graph radic_graph;
+
+/* Captures one radic_det call with these arguments into a CUDA graph owned
+ * by the library; radic_graph_launch replays it on any stream (same
+ * kernels, without the per-call planning and launch latency), and
+ * radic_graph_destroy frees it.  The buffers must stay valid while the graph
+ * is used.  Errors: those of radic_det, and RADIC_ECUDA if capture fails. */
+int radic_graph_create(const void* A, int m, int n, int64_t lda, int dtype, int mode, const radic_options* opts,
+                       radic_result* out, void* workspace, size_t workspace_bytes, radic_graph** graph);
+int radic_graph_launch(radic_graph* graph, void* stream);
+int radic_graph_destroy(radic_graph* graph);
+
 /* ---- batches of matrices of uneven shape ------------------------------- */
 
 /* Host-side plan (opaque) of one batch layout, and a captured CUDA graph of
@@ -291,8 +304,11 @@ size_t radic_backward_workspace_bytes(int batch, int m, int n);
 /* Gradient of sum_b grad_out[b] * det_R(A_b) with respect to every A_b, in
  * binary64.  d det_R / d A[:, J] = (-1)^(r+s) adj(A[:, J])^T for every
  * column sequence J of Eq. (1): each minor's signed cofactors
- * det(M) inv(M)^T (from its partial-pivot LU) are scatter-added into the
- * gradient columns J.  A: device, batch matrices m x n, row-major with
+ * det(M) inv(M)^T are scatter-added into the gradient columns J.  For
+ * m >= 3 the cofactors of all minors of one (m-2)-column prefix are summed
+ * in closed form from the prefix's partial-pivot LU (block inverse of the
+ * minor); for m <= 2, and for prefixes with an exactly zero pivot, from
+ * each minor's own LU.  A: device, batch matrices m x n, row-major with
  * leading dimension lda, matrix b at A + b * stride.  grad_out: device,
  * batch values.  grad_A: device, same layout as A, overwritten.  1 <= m <= 8
  * (m > n gives a zero gradient).  Errors: RADIC_EINVAL, RADIC_EUNSUPPORTED

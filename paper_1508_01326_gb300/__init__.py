@@ -11,6 +11,7 @@ from .autograd import RadicDet, radic_det_autograd, radic_det_backward  # noqa: 
 from .api import (  # noqa: F401
     BatchGraph,
     BatchPlan,
+    DetGraph,
     det,
     make_tuning,
     parse_results,

@@ -102,6 +102,9 @@ def _declare_optional(L: ctypes.CDLL) -> None:
         "radic_batch_workspace_bytes": ([vp], sz),
         "radic_batch_upload": ([vp, vp, sz, vp], i32),
         "radic_det_batched": ([vp, vp, i32, vp, vp, sz, vp], i32),
+        "radic_graph_create": ([vp, i32, i32, i64, i32, i32, ctypes.POINTER(RadicOptions), vp, vp, sz, pp], i32),
+        "radic_graph_launch": ([vp, vp], i32),
+        "radic_graph_destroy": ([vp], i32),
         "radic_batch_graph_create": ([vp, vp, i32, vp, vp, sz, pp], i32),
         "radic_batch_graph_launch": ([vp, vp], i32),
         "radic_batch_graph_destroy": ([vp], i32),

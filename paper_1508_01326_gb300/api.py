@@ -273,6 +273,38 @@ class BatchPlan:
             pass
 
 
+class DetGraph:
+    """A captured CUDA graph of one radic_det call on fixed buffers: replaying it runs the same
+    kernels without the per-call planning and launch latency (radic_graph_create)."""
+
+    def __init__(self, A: torch.Tensor, mode="fp64", options=None, out: Optional[torch.Tensor] = None,
+                 workspace: Optional[torch.Tensor] = None):
+        _check_matrix(A)
+        m, n = A.shape
+        md = _mode(mode)
+        lib = L.lib()
+        self.A = A
+        self.out = out if out is not None else new_result(A.device)
+        self._opts = L.make_options(**options) if isinstance(options, dict) else options
+        ws_bytes = int(lib.radic_workspace_bytes(int(m), int(n), md, _opts(self._opts)))
+        self.workspace = workspace if workspace is not None else torch.empty(max(ws_bytes, 256), dtype=torch.uint8,
+                                                                             device=A.device)
+        handle = ctypes.c_void_p()
+        rc = lib.radic_graph_create(A.data_ptr(), int(m), int(n), int(A.stride(0)), _TORCH_DTYPES[A.dtype], md,
+                                    _opts(self._opts), self.out.data_ptr(), self.workspace.data_ptr(),
+                                    self.workspace.numel(), ctypes.byref(handle))
+        L.check("radic_graph_create", rc)
+        self._g = handle
+
+    def launch(self, stream=None) -> None:
+        L.check("radic_graph_launch", L.lib().radic_graph_launch(self._g, _stream(stream)))
+
+    def close(self) -> None:
+        if self._g:
+            L.lib().radic_graph_destroy(self._g)
+            self._g = None
+
+
 class BatchGraph:
     """A captured CUDA graph of one batched call on fixed buffers."""
 

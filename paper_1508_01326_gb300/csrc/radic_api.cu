@@ -3,6 +3,7 @@
 // entirely on the host before anything is enqueued.
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <string>
 #include <unordered_map>
 
@@ -509,6 +510,53 @@ int radic_unrank(int n, int m, uint64_t q0, uint64_t count, uint8_t* cols, const
   if (count == 0) return RADIC_OK;
   const int L = (opts && opts->ranks_per_task > 0) ? opts->ranks_per_task : 64;
   return launch_unrank(n, m, q0, count, cols, L, static_cast<cudaStream_t>(stream));
+}
+
+struct radic_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+int radic_graph_create(const void* A, int m, int n, int64_t lda, int dtype, int mode, const radic_options* opts,
+                       radic_result* out, void* workspace, size_t workspace_bytes, radic_graph** graph) {
+  if (!graph) return RADIC_EINVAL;
+  *graph = nullptr;
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return RADIC_ECUDA;
+  radic_graph* g = new (std::nothrow) radic_graph;
+  int rc = g ? RADIC_OK : RADIC_EINVAL;
+  if (rc == RADIC_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = RADIC_ECUDA;
+  if (rc == RADIC_OK) {
+    const int r = radic_det(A, m, n, lda, dtype, mode, opts, out, workspace, workspace_bytes, cs);
+    const cudaError_t e = cudaStreamEndCapture(cs, &g->graph);
+    if (r != RADIC_OK) rc = r;
+    else if (e != cudaSuccess) rc = RADIC_ECUDA;
+  }
+  if (rc == RADIC_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) rc = RADIC_ECUDA;
+  cudaStreamDestroy(cs);
+  if (rc != RADIC_OK) {
+    if (g) {
+      if (g->exec) cudaGraphExecDestroy(g->exec);
+      if (g->graph) cudaGraphDestroy(g->graph);
+      delete g;
+    }
+    return rc;
+  }
+  *graph = g;
+  return RADIC_OK;
+}
+
+int radic_graph_launch(radic_graph* graph, void* stream) {
+  if (!graph || !graph->exec) return RADIC_EINVAL;
+  return cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? RADIC_OK : RADIC_ECUDA;
+}
+
+int radic_graph_destroy(radic_graph* graph) {
+  if (!graph) return RADIC_OK;
+  if (graph->exec) cudaGraphExecDestroy(graph->exec);
+  if (graph->graph) cudaGraphDestroy(graph->graph);
+  delete graph;
+  return RADIC_OK;
 }
 
 }  // extern "C"

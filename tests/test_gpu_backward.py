@@ -65,7 +65,9 @@ def test_backward_singular_prefixes():
 
 def test_autograd_function_and_gradcheck():
     A = torch.from_numpy(W.uniform_matrix(5, 3, 6)).cuda().unsqueeze(0).requires_grad_(True)
-    assert torch.autograd.gradcheck(R().RadicDet.apply, (A,), eps=1e-6, atol=1e-7, rtol=1e-6)
+    # the backward adds cofactor sums with shared-memory atomics, so repeated
+    # calls agree up to the rounding of the addition order
+    assert torch.autograd.gradcheck(R().RadicDet.apply, (A,), eps=1e-6, atol=1e-7, rtol=1e-6, nondet_tol=1e-12)
     x = torch.from_numpy(W.uniform_matrix(6, 4, 8)).cuda().requires_grad_(True)
     y = R().radic_det_autograd(x)
     y.backward()

@@ -533,9 +533,11 @@ def test_plan_info_reports_the_default_mapping_and_depth():
     assert R().radic_plan_info(5, 60, "mixed")["prefix_depth"] == 2
     g = R().radic_plan_info(14, 20, "fp64")
     assert g["mapping"] == "group" and g["group_width"] == 16 and g["prefix_depth"] == 0
-    t = R().radic_plan_info(6, 20, "exact")
+    e = R().radic_plan_info(6, 20, "exact")
+    assert e["mapping"] == "prefix" and e["prefix_depth"] == 2
+    t = R().radic_plan_info(6, 20, "exact", dict(mapping="thread"))
     assert t["mapping"] == "thread" and t["threads"] == 128 and t["blocks"] >= 1
-    assert t["workspace_bytes"] == R().radic_workspace_bytes(6, 20, "exact")
+    assert t["workspace_bytes"] == R().radic_workspace_bytes(6, 20, "exact", dict(mapping="thread"))
 
 
 @pytest.mark.parametrize("mode", ["fp64", "mixed", "pair"])
@@ -555,3 +557,19 @@ def test_det_extreme_row_scales(mode):
     assert abs(float(Fraction(res["value"]) - val)) <= tol * float(abs_sum)
     assert abs(res["abs_sum"] - float(abs_sum)) <= 1e-5 * float(abs_sum)
     assert res["status"] == 0
+
+
+@pytest.mark.parametrize("mode", ["mixed", "fp64", "exact"])
+def test_graph_replay_equals_direct_call(mode):
+    a = W.integer_matrix(41, 7, 18, 3, np.int8) if mode == "exact" else W.uniform_matrix(41, 7, 18)
+    t = dev(a)
+    direct = R().parse_result(R().radic_det(t, mode=mode))
+    g = R().DetGraph(t, mode=mode)
+    g.launch()
+    g.launch()
+    torch.cuda.synchronize()
+    replay = R().parse_result(g.out)
+    g.close()
+    assert replay["value"] == direct["value"] and replay["status"] == 0
+    if mode == "exact":
+        assert replay["exact"] == direct["exact"]
