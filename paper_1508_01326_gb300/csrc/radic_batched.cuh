@@ -277,6 +277,16 @@ __device__ bool run_task(const BatchArgs& a, const BatchTask& t, const WarpSlice
 
 template <typename T>
 __device__ __forceinline__ void warp_sum(TaskAcc<T>& acc, Dd& d, double& ab) {
+  if constexpr (std::is_same<T, float>::value) {
+    // float-float tree on the binary32 pipe, widened once
+    Ff t = acc.p.tot, ta = acc.p.tot_abs;
+    warp_reduce_ff(t, ta);
+    d = Dd();
+    d.add(static_cast<double>(t.hi));
+    d.add(static_cast<double>(t.lo));
+    ab = static_cast<double>(ta.hi) + static_cast<double>(ta.lo);
+    return;
+  }
   acc.p.finish();
   d = acc.p.acc;
   ab = acc.p.abs_sum;

@@ -297,6 +297,54 @@ __device__ __forceinline__ double shfl_xor_d(double x, int off) {
   return __shfl_xor_sync(kFull, x, off);
 }
 
+// Fixed-order warp reduction of float-float lane totals (value and magnitude
+// sum) on the binary32 pipe; the warp total is valid in every lane.
+__device__ __forceinline__ void warp_reduce_ff(Ff& t, Ff& ta) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Ff o, oa;
+    o.hi = __shfl_xor_sync(kFull, t.hi, off);
+    o.lo = __shfl_xor_sync(kFull, t.lo, off);
+    oa.hi = __shfl_xor_sync(kFull, ta.hi, off);
+    oa.lo = __shfl_xor_sync(kFull, ta.lo, off);
+    t.merge(o);
+    ta.merge(oa);
+  }
+}
+
+// Block-wide fixed-order reduction of float-float lane totals and a count:
+// the warp trees stay on the binary32 pipe (binary64 runs at 1/64 of its
+// rate) and only the warps' totals are widened to binary64 two-sums.  The
+// result is valid in thread 0.  `scratch` holds 4 * (blockDim.x / 32) words.
+__device__ inline void block_reduce_ff(Ff t, Ff ta, long long& count, double* scratch, Dd& acc, double& abs_sum) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  warp_reduce_ff(t, ta);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) count += __shfl_xor_sync(kFull, count, off);
+  __syncthreads();
+  if (lane == 0) {
+    scratch[4 * warp + 0] = static_cast<double>(t.hi);
+    scratch[4 * warp + 1] = static_cast<double>(t.lo);
+    scratch[4 * warp + 2] = static_cast<double>(ta.hi) + static_cast<double>(ta.lo);
+    scratch[4 * warp + 3] = __longlong_as_double(count);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Dd d;
+    double ab = 0.0;
+    long long cnt = 0;
+    for (int w = 0; w < nw; ++w) {
+      d.add(scratch[4 * w + 0]);
+      d.add(scratch[4 * w + 1]);
+      ab += scratch[4 * w + 2];
+      cnt += __double_as_longlong(scratch[4 * w + 3]);
+    }
+    acc = d;
+    abs_sum = ab;
+    count = cnt;
+  }
+}
+
 // Block-wide reduction of (hi, lo, abs, count) in a fixed order; the result
 // is valid in thread 0.  `scratch` holds 4 * (blockDim.x / 32) words.
 __device__ inline void block_reduce_dd(Dd& acc, double& abs_sum, long long& count, double* scratch) {
