@@ -185,8 +185,14 @@ def max_over_ranks(total_ms: float, device=None) -> float:
     return float(t.item())
 
 
-def prefix_ops(m: int, n: int, D: int) -> dict:
+def prefix_ops(m: int, n: int, D: int, shared: bool = False) -> dict:
     """Operation counts of the prefix-sharing path with depth D (2 or 3).
+
+    With `shared` (head sharing of the batched path) each head of H = m-D-1
+    columns is factored once (its elimination and W1 for the D+1 rows left)
+    and each last prefix column costs one elimination step: the D+1
+    Schur-complement entries of the column, D multipliers and the D x H
+    update of W, one multiply into the pivot product.
 
     Per (m-D)-column prefix: the partial-pivot elimination of its m x (m-D)
     matrix (multipliers and FMA updates), the product of pivots and
@@ -203,6 +209,21 @@ def prefix_ops(m: int, n: int, D: int) -> dict:
     pair = {"fma": 3, "mul": 3, "add": 0} if D == 3 else {"fma": 0, "mul": 0, "add": 0}
     leaf = {"fma": D - 1, "mul": 1, "add": 2}
     tot = {"fma": 0, "mul": 0, "add": 0}
+    if shared:
+        H = P - 1
+        head = {"fma": sum((m - k - 1) * (H - k - 1) for k in range(H)) + (D + 1) * H * (H - 1) // 2,
+                "mul": sum(m - k - 1 for k in range(H)) + H, "add": 0}
+        ext = {"fma": (D + 1) * H + D * H, "mul": D + 1, "add": 0}
+        for u in range(H - 1, n - D - 1):
+            cnt = math.comb(u, H - 1)
+            for key in tot:
+                tot[key] += cnt * head[key]
+            for v in range(u + 1, n - D):
+                k = n - 1 - v
+                for key in tot:
+                    tot[key] += cnt * (ext[key] + k * col[key] + math.comb(k, 2) * pair[key] +
+                                       math.comb(k, D) * leaf[key])
+        return tot
     for v in range(P - 1, n - D):
         k = n - 1 - v
         cnt = math.comb(v, P - 1)
@@ -217,11 +238,11 @@ def prefix_flops(m: int, n: int, D: int) -> int:
     return 2 * c["fma"] + c["mul"] + c["add"]
 
 
-def pair_flops(m: int, n: int, D: int) -> int:
+def pair_flops(m: int, n: int, D: int, shared: bool = False) -> int:
     """The same operations in pairs of binary32, counted in binary32 flops of the pair
     algorithms: multiply-add 18 (exact product 7, TwoSum 6, low parts 2, Fast2Sum 3),
     multiply 10, addition 11; the absolute-value sum stays one binary32 add per leaf."""
-    c = prefix_ops(m, n, D)
+    c = prefix_ops(m, n, D, shared)
     leaves = c["add"] // 2
     return 18 * c["fma"] + 10 * c["mul"] + 11 * leaves + leaves
 
@@ -293,6 +314,18 @@ def measure_configs(R, W, torch) -> dict:
         worst = max(abs(x["value"] - w) / x["abs_sum"] for x, w in zip(rs, gold) if x["abs_sum"] > 0)
         batched[mode] = {"value": minors / (ms / 1e3), "unit": UNIT, "ms": ms, "rel_err_max": worst,
                          "routing": plan.info()}
+        if mode == "mixed":
+            # binary32 flops of the pair algorithms over the pair-tier matrices (m >= 3), with
+            # the depth the tuning chose and head sharing where the plan uses it (m-D-1 >= 5)
+            flops = 0
+            for x in mats:
+                mm, nn = x.shape
+                if 3 <= mm <= nn:
+                    v = table.get(str(mm), table.get(mm, {}))
+                    D = v.get("depth") or (3 if mm >= 6 and 2 * (nn - mm) <= 7 * mm else 2)
+                    flops += pair_flops(mm, nn, D, shared=mm - D - 1 >= 5)
+            batched[mode]["pair_flop"] = flops
+            batched[mode]["fma_frac"] = flops / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS
         plan.close()
     # one plain binary64 per-minor launch per matrix (thread mapping up to m = 8, warp groups above)
     dev = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in mats]
