@@ -355,6 +355,12 @@ def measure_configs(R, W, torch) -> dict:
     mn = 256 * math.comb(28, 6)
     out["diff_256x6x28"] = {"forward_ms": fwd, "backward_ms": bwd, "backward_minors_per_s": mn / (bwd / 1e3),
                             "forward_minors_per_s": mn / (fwd / 1e3)}
+    # mixed precision: batched mixed-router forward, pair backward
+    R.RadicDet.apply(D, "mixed")
+    fwd_m = ev_time(lambda: R.RadicDet.apply(D, "mixed"), reps=3)
+    bwd_m = ev_time(lambda: R.radic_det_backward(D, g_out, mode="pair"), reps=3)
+    out["diff_256x6x28"]["mixed"] = {"forward_ms": fwd_m, "backward_ms": bwd_m,
+                                     "backward_minors_per_s": mn / (bwd_m / 1e3)}
     return out
 
 

@@ -317,6 +317,16 @@ int radic_det_backward(const double* A, int batch, int m, int n, int64_t lda, in
                        const double* grad_out, double* grad_A, void* workspace, size_t workspace_bytes,
                        void* stream);
 
+/* radic_det_backward with the arithmetic of the per-prefix eliminations
+ * chosen by mode: RADIC_MODE_FP64 (as radic_det_backward) or RADIC_MODE_PAIR
+ * (pairs of binary32, about 48 significant bits, on the binary32 pipe; the
+ * cofactor sums are still accumulated in binary64).  m <= 2 and singular
+ * prefixes use binary64 in both modes.  Same workspace and errors, plus
+ * RADIC_EINVAL for another mode. */
+int radic_det_backward_mode(const double* A, int batch, int m, int n, int64_t lda, int64_t stride,
+                            const double* grad_out, double* grad_A, void* workspace, size_t workspace_bytes,
+                            int mode, void* stream);
+
 /* ---- allocation-free variant ------------------------------------------- */
 
 /* Capacity in bytes of the library's own static scratch array. */

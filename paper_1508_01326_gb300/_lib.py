@@ -110,6 +110,7 @@ def _declare_optional(L: ctypes.CDLL) -> None:
         "radic_batch_graph_destroy": ([vp], i32),
         "radic_backward_workspace_bytes": ([i32, i32, i32], sz),
         "radic_det_backward": ([vp, i32, i32, i32, i64, i64, vp, vp, vp, sz, vp], i32),
+        "radic_det_backward_mode": ([vp, i32, i32, i32, i64, i64, vp, vp, vp, sz, i32, vp], i32),
         "radic_det_noalloc": ([vp, i32, i32, i64, i32, vp, vp, vp], i32),
     }
     for name, (args, res) in table.items():

@@ -93,30 +93,30 @@ __device__ __forceinline__ double lu_full(double (&a)[M][M], int (&idx)[M], bool
 // X = U^{-1} L^{-1} from the packed factors in a (L unit lower, U upper):
 // first X = L^{-1} column by column (forward substitution), then, in place,
 // X = U^{-1} X (back substitution).
-template <int M>
-__device__ __forceinline__ void inverse_factors(const double (&a)[M][M], double (&X)[M][M]) {
+template <int M, typename T = double>
+__device__ __forceinline__ void inverse_factors(const T (&a)[M][M], T (&X)[M][M]) {
 #pragma unroll
   for (int j = 0; j < M; ++j) {
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-      if (i < j) X[i][j] = 0.0;
-      else if (i == j) X[i][j] = 1.0;
+      if (i < j) X[i][j] = T(0);
+      else if (i == j) X[i][j] = T(1);
       else {
-        double s = -a[i][j];
+        T s = -a[i][j];
 #pragma unroll
         for (int k = j + 1; k < i; ++k) s = fma(-a[i][k], X[k][j], s);
         X[i][j] = s;
       }
     }
   }
-  double rinv[M];
+  T rinv[M];
 #pragma unroll
-  for (int i = 0; i < M; ++i) rinv[i] = rcp_f64(a[i][i]);
+  for (int i = 0; i < M; ++i) rinv[i] = rcp_t(a[i][i]);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
 #pragma unroll
     for (int i = M - 1; i >= 0; --i) {
-      double s = X[i][j];
+      T s = X[i][j];
 #pragma unroll
       for (int k = i + 1; k < M; ++k) s = fma(-a[i][k], X[k][j], s);
       X[i][j] = s * rinv[i];
@@ -258,25 +258,64 @@ __device__ __noinline__ void minor_cofactors_scatter(const double* As, int cs, c
   }
 }
 
+// Signed cofactors of one minor read from the binary64 matrix in global
+// memory (row stride lda), added into the gradient tile G.
 template <int M>
+__device__ __noinline__ void minor_cofactors_scatter_global(const double* Ab, long long lda, const int (&c)[M],
+                                                            double* G, int n) {
+  constexpr int CSG = ColStride<double, M>::value;
+  double col[M * CSG];
+  for (int j = 0; j < M; ++j)
+    for (int i = 0; i < CSG; ++i) col[j * CSG + i] = (i < M) ? Ab[(long long)i * lda + c[j]] : 0.0;
+  int cl[M];
+  for (int j = 0; j < M; ++j) cl[j] = j;
+  double mm[M][M];
+  for (int j = 0; j < M; ++j)
+    for (int i = 0; i < M; ++i) mm[i][j] = col[j * CSG + i];
+  int idx[M];
+  bool zp;
+  const double det = lu_full<M>(mm, idx, zp);
+  const double sgn = sign_negative<M>(c) ? -1.0 : 1.0;
+  if (!zp) {
+    double B[M][M];
+    inverse_factors<M>(mm, B);
+    const double s = sgn * det;
+    for (int sl = 0; sl < M; ++sl)
+      for (int j = 0; j < M; ++j) atomicAdd(G + idx[sl] * n + c[j], s * B[j][sl]);
+  } else {
+    double cof[M][M];
+    cofactors_slow<M>(col, CSG, cl, cof);
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) atomicAdd(G + i * n + c[j], sgn * cof[i][j]);
+  }
+}
+
+__device__ __forceinline__ bool pivot_greater(double x, double y) { return mag_key(x) > mag_key(y); }
+__device__ __forceinline__ bool pivot_greater(ff x, ff y) { return fabsf(x.hi) > fabsf(y.hi); }
+__device__ __forceinline__ bool is_zero(double x) { return x == 0.0; }
+__device__ __forceinline__ bool is_zero(ff x) { return x.hi == 0.0f; }
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(ff x) { return static_cast<double>(x); }
+
+template <typename T, int M>
 __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, PrefixTable tab) {
   constexpr int D = 2, P = M - D;
-  constexpr int CS = ColStride<double, M>::value;
+  constexpr int CS = ColStride<T, M>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.n;
   const int b = blockIdx.y, chunk = blockIdx.x;
   uint64_t* binom = reinterpret_cast<uint64_t*>(smem_raw);
   size_t off = ((size_t)(n + 1) * (M + 1) * 8 + 15) / 16 * 16;
-  double* As = reinterpret_cast<double*>(smem_raw + off);
-  off += ((size_t)n * CS * 8 + 15) / 16 * 16;
+  T* As = reinterpret_cast<T*>(smem_raw + off);
+  off += ((size_t)n * CS * sizeof(T) + 15) / 16 * 16;
   double* G = reinterpret_cast<double*>(smem_raw + off);  // M x n gradient tile
   off += ((size_t)M * n * 8 + 15) / 16 * 16;
-  const ZBuf<double, D> zb(smem_raw + off, threadIdx.x, blockDim.x, n - M + D);
+  const ZBuf<T, D> zb(smem_raw + off, threadIdx.x, blockDim.x, n - M + D);
   build_binom(binom, n, M);
   const double* Ab = a.A + (long long)b * a.stride;
   for (int idx = threadIdx.x; idx < n * CS; idx += blockDim.x) {
     const int j = idx / CS, i = idx - j * CS;
-    As[idx] = (i < M) ? Ab[(long long)i * a.lda + j] : 0.0;
+    As[idx] = (i < M) ? to_elem<T>(Ab[(long long)i * a.lda + j]) : T(0);
   }
   for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) G[idx] = 0.0;
   __syncthreads();
@@ -301,7 +340,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, Pref
       for (int j = 0; j < P - 1; ++j) c[j] = head[j];
       c[P - 1] = v;
       // factor the M x P prefix: partial pivoting, L \ U packed in fa
-      double fa[M][P];
+      T fa[M][P];
 #pragma unroll
       for (int j = 0; j < P; ++j)
 #pragma unroll
@@ -310,15 +349,15 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, Pref
 #pragma unroll
       for (int i = 0; i < M; ++i) idx[i] = i;
       bool neg = false, zp = false;
-      double prod = 1.0;
+      T prod = T(1);
 #pragma unroll
       for (int kk = 0; kk < P; ++kk) {
 #pragma unroll
         for (int i = kk + 1; i < M; ++i) {
-          const bool sw = mag_key(fa[i][kk]) > mag_key(fa[kk][kk]);
+          const bool sw = pivot_greater(fa[i][kk], fa[kk][kk]);
 #pragma unroll
           for (int j = 0; j < P; ++j) {
-            const double x = fa[kk][j], y = fa[i][j];
+            const T x = fa[kk][j], y = fa[i][j];
             fa[kk][j] = sw ? y : x;
             fa[i][j] = sw ? x : y;
           }
@@ -327,13 +366,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, Pref
           idx[i] = sw ? ik : ii;
           neg ^= sw;
         }
-        const double piv = fa[kk][kk];
-        zp |= (piv == 0.0);
+        const T piv = fa[kk][kk];
+        zp |= is_zero(piv);
         prod *= piv;
-        const double rr = rcp_f64(piv);
+        const T rr = rcp_t(piv);
 #pragma unroll
         for (int i = kk + 1; i < M; ++i) {
-          const double l = fa[i][kk] * rr;
+          const T l = fa[i][kk] * rr;
           fa[i][kk] = l;
 #pragma unroll
           for (int j = kk + 1; j < P; ++j) fa[i][j] = fma(-l, fa[kk][j], fa[i][j]);
@@ -346,40 +385,40 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, Pref
             for (int j = 0; j < P; ++j) cm[j] = c[j];
             cm[P] = x;
             cm[P + 1] = y;
-            minor_cofactors_scatter<M>(As, CS, cm, G, n);
+            minor_cofactors_scatter_global<M>(Ab, a.lda, cm, G, n);
           }
       } else {
         // W = -L21 L11^{-1} (D x P) and Ainv = U11^{-1} L11^{-1} (P x P)
-        double W[D][P];
+        T W[D][P];
 #pragma unroll
         for (int d = 0; d < D; ++d) {
 #pragma unroll
           for (int j = P - 1; j >= 0; --j) {
-            double sum = -fa[P + d][j];
+            T sum = -fa[P + d][j];
 #pragma unroll
             for (int i = j + 1; i < P; ++i) sum = fma(-W[d][i], fa[i][j], sum);
             W[d][j] = sum;
           }
         }
-        double Ai[P][P];
+        T Ai[P][P];
         {
-          double top[P][P];
+          T top[P][P];
 #pragma unroll
           for (int i = 0; i < P; ++i)
 #pragma unroll
             for (int j = 0; j < P; ++j) top[i][j] = fa[i][j];
-          inverse_factors<P>(top, Ai);
+          inverse_factors<P, T>(top, Ai);
         }
         int sp = M * (M + 1) / 2 + D;
 #pragma unroll
         for (int j = 0; j < P; ++j) sp += c[j] + 1;
-        const double alpha = ((sp & 1) != neg) ? -prod : prod;
+        const T alpha = ((sp & 1) != neg) ? -prod : prod;
         // pass 1: z~ of every candidate column, their sum, and s
-        double zt0 = 0.0, zt1 = 0.0, ssum = 0.0;
+        T zt0 = T(0), zt1 = T(0), ssum = T(0);
         for (int q = 0; q < k; ++q) {
           const int col = v + 1 + q;
-          double z[D];
-          prefix_column<double, M, D>(As + col * CS, W, idx, z);
+          T z[D];
+          prefix_column<T, M, D>(As + col * CS, W, idx, z);
           if (col & 1) {
             z[0] = -z[0];
             z[1] = -z[1];
@@ -390,29 +429,28 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, Pref
           zb.put(q, z);
         }
         // pass 2: candidate-column gradients and Q
-        double Q[P][D];
+        T Q[P][D];
 #pragma unroll
-        for (int i = 0; i < P; ++i) Q[i][0] = Q[i][1] = 0.0;
-        double zp0 = 0.0, zp1 = 0.0;
+        for (int i = 0; i < P; ++i) Q[i][0] = Q[i][1] = T(0);
+        T zp0 = T(0), zp1 = T(0);
         for (int q = 0; q < k; ++q) {
           const int col = v + 1 + q;
-          double z[D];
+          T z[D];
           zb.get(q, z);
-          const double h0 = zt0 - 2.0 * zp0 - z[0], h1 = zt1 - 2.0 * zp1 - z[1];
-          const double g0 = h1, g1 = -h0;  // rot(Z_>q - Z_<q)
+          const T h0 = zt0 - (zp0 + zp0) - z[0], h1 = zt1 - (zp1 + zp1) - z[1];
+          const T g0 = h1, g1 = -h0;  // rot(Z_>q - Z_<q)
           zp0 += z[0];
           zp1 += z[1];
-          const double sc = (col & 1) ? -alpha : alpha;
+          const T sc = (col & 1) ? -alpha : alpha;
           double* gcol = G + col;
 #pragma unroll
-          for (int r = 0; r < P; ++r) atomicAdd(gcol + idx[r] * n, sc * fma(W[0][r], g0, W[1][r] * g1));
-          atomicAdd(gcol + idx[P] * n, sc * g0);
-          atomicAdd(gcol + idx[P + 1] * n, sc * g1);
-          const double sgn = (col & 1) ? -1.0 : 1.0;
-          const double* xc = As + col * CS;
+          for (int r = 0; r < P; ++r) atomicAdd(gcol + idx[r] * n, to_double(sc * fma(W[0][r], g0, W[1][r] * g1)));
+          atomicAdd(gcol + idx[P] * n, to_double(sc * g0));
+          atomicAdd(gcol + idx[P + 1] * n, to_double(sc * g1));
+          const T* xc = As + col * CS;
 #pragma unroll
           for (int i = 0; i < P; ++i) {
-            const double xt = sgn * xc[idx[i]];
+            const T xt = (col & 1) ? -xc[idx[i]] : xc[idx[i]];
             Q[i][0] = fma(xt, g0, Q[i][0]);
             Q[i][1] = fma(xt, g1, Q[i][1]);
           }
@@ -420,7 +458,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, Pref
         // prefix columns: alpha [s Ainv - Ainv Q W | -Ainv Q]^T
 #pragma unroll
         for (int tt = 0; tt < P; ++tt) {
-          double R0 = 0.0, R1 = 0.0;  // (Ainv Q)[tt][:]
+          T R0 = T(0), R1 = T(0);  // (Ainv Q)[tt][:]
 #pragma unroll
           for (int u = 0; u < P; ++u) {
             R0 = fma(Ai[tt][u], Q[u][0], R0);
@@ -429,9 +467,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, Pref
           double* gcol = G + c[tt];
 #pragma unroll
           for (int r = 0; r < P; ++r)
-            atomicAdd(gcol + idx[r] * n, alpha * (ssum * Ai[tt][r] - fma(R0, W[0][r], R1 * W[1][r])));
-          atomicAdd(gcol + idx[P] * n, -alpha * R0);
-          atomicAdd(gcol + idx[P + 1] * n, -alpha * R1);
+            atomicAdd(gcol + idx[r] * n, to_double(alpha * (ssum * Ai[tt][r] - fma(R0, W[0][r], R1 * W[1][r]))));
+          atomicAdd(gcol + idx[P] * n, to_double(-(alpha * R0)));
+          atomicAdd(gcol + idx[P + 1] * n, to_double(-(alpha * R1)));
         }
       }
       if constexpr (P > 1) {
@@ -473,20 +511,21 @@ const void* bwd_kernel(int m) {
   }
 }
 
-template <int M>
+template <typename T, int M>
 const void* bwd_prefix_kernel_m() {
-  if constexpr (M >= 3) return reinterpret_cast<const void*>(&k_backward_prefix<M>);
+  if constexpr (M >= 3) return reinterpret_cast<const void*>(&k_backward_prefix<T, M>);
   else return nullptr;
 }
 
+template <typename T>
 const void* bwd_prefix_kernel(int m) {
   switch (m) {
-    case 3: return bwd_prefix_kernel_m<3>();
-    case 4: return bwd_prefix_kernel_m<4>();
-    case 5: return bwd_prefix_kernel_m<5>();
-    case 6: return bwd_prefix_kernel_m<6>();
-    case 7: return bwd_prefix_kernel_m<7>();
-    case 8: return bwd_prefix_kernel_m<8>();
+    case 3: return bwd_prefix_kernel_m<T, 3>();
+    case 4: return bwd_prefix_kernel_m<T, 4>();
+    case 5: return bwd_prefix_kernel_m<T, 5>();
+    case 6: return bwd_prefix_kernel_m<T, 6>();
+    case 7: return bwd_prefix_kernel_m<T, 7>();
+    case 8: return bwd_prefix_kernel_m<T, 8>();
     default: return nullptr;
   }
 }
@@ -530,7 +569,7 @@ void bwd_prefix_plan(int batch, int m, int n, int sms, int* chunks, PrefixTable*
   *tab = t;
 }
 
-size_t bwd_prefix_smem(int m, int n) {
+size_t bwd_prefix_smem(int m, int n) {  // binary64 and pair elements are both 8 bytes
   const int cs = ((m + 1) / 2) * 2;
   size_t off = ((size_t)(n + 1) * (m + 1) * 8 + 15) / 16 * 16;
   off += ((size_t)n * cs * 8 + 15) / 16 * 16;
@@ -578,8 +617,16 @@ size_t radic_backward_workspace_bytes(int batch, int m, int n) {
 
 int radic_det_backward(const double* A, int batch, int m, int n, int64_t lda, int64_t stride, const double* grad_out,
                        double* grad_A, void* workspace, size_t workspace_bytes, void* stream) {
+  return radic_det_backward_mode(A, batch, m, n, lda, stride, grad_out, grad_A, workspace, workspace_bytes,
+                                 RADIC_MODE_FP64, stream);
+}
+
+int radic_det_backward_mode(const double* A, int batch, int m, int n, int64_t lda, int64_t stride,
+                            const double* grad_out, double* grad_A, void* workspace, size_t workspace_bytes, int mode,
+                            void* stream) {
   if (!A || !grad_out || !grad_A || batch < 1 || m < 1 || n < 1 || n > kMaxN || lda < n || stride < (int64_t)m * lda)
     return RADIC_EINVAL;
+  if (mode != RADIC_MODE_FP64 && mode != RADIC_MODE_PAIR) return RADIC_EINVAL;
   if (m > kBwdMaxM) return RADIC_EUNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (m > n) {  // det_R is identically zero: zero gradient
@@ -606,7 +653,7 @@ int radic_det_backward(const double* A, int batch, int m, int n, int64_t lda, in
   size_t smem;
   if (m >= 3) {  // prefix-shared backward
     bwd_prefix_plan(batch, m, n, device_sm_count(), &a.chunks, &tab);
-    k = bwd_prefix_kernel(m);
+    k = (mode == RADIC_MODE_PAIR) ? bwd_prefix_kernel<ff>(m) : bwd_prefix_kernel<double>(m);
     smem = bwd_prefix_smem(m, n);
   } else {
     k = bwd_kernel(m);

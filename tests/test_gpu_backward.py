@@ -31,14 +31,15 @@ def R():
     return R_
 
 
+@pytest.mark.parametrize("mode", ["fp64", "pair"])
 @pytest.mark.parametrize("m,n", [(1, 6), (2, 5), (3, 7), (4, 9), (5, 5), (6, 10), (7, 10), (8, 11), (4, 3),
                                  (3, 14), (5, 16), (8, 13)])
-def test_backward_matches_exact_gradient(m, n):
+def test_backward_matches_exact_gradient(m, n, mode):
     rng = np.random.default_rng(100 * m + n)
     mats = rng.uniform(-1, 1, (3, m, n))
     A = torch.from_numpy(mats).cuda()
     g_out = torch.tensor([1.0, -2.5, 0.75], dtype=torch.float64, device="cuda")
-    grad = R().radic_det_backward(A, g_out).cpu().numpy()
+    grad = R().radic_det_backward(A, g_out, mode=mode).cpu().numpy()
     for b in range(3):
         if m > n:
             want = np.zeros((m, n))
@@ -48,7 +49,8 @@ def test_backward_matches_exact_gradient(m, n):
         assert np.abs(grad[b] - float(g_out[b]) * want).max() <= 1e-11 * scale * max(1.0, abs(float(g_out[b])))
 
 
-def test_backward_singular_prefixes():
+@pytest.mark.parametrize("mode", ["fp64", "pair"])
+def test_backward_singular_prefixes(mode):
     # integer entries with a repeated column and a zero column: prefixes that
     # contain both copies, or the zero column, have an exactly zero pivot and
     # take the per-minor path for their leaves
@@ -56,8 +58,8 @@ def test_backward_singular_prefixes():
     a[:, 3] = a[:, 1]
     a[:, 6] = 0.0
     mats = np.stack([a, W.integer_matrix(18, 5, 10, 4, np.int32).astype(np.float64)])
-    grad = R().radic_det_backward(torch.from_numpy(mats).cuda(), torch.ones(2, dtype=torch.float64,
-                                                                           device="cuda")).cpu().numpy()
+    grad = R().radic_det_backward(torch.from_numpy(mats).cuda(), torch.ones(2, dtype=torch.float64, device="cuda"),
+                                  mode=mode).cpu().numpy()
     for b in range(2):
         want = np.array([[float(x) for x in row] for row in orc.radic_grad_exact(mats[b], use_pfaffian=False)])
         assert np.abs(grad[b] - want).max() <= 1e-11 * max(np.abs(want).max(), 1.0)
@@ -106,3 +108,17 @@ def test_full_diff_256x6x28_forward_and_backward(diff_batch):
         minus[b, i, j] -= h
         fd = (float(R().radic_det_autograd(plus)[b]) - float(R().radic_det_autograd(minus)[b])) / (2 * h)
         assert abs(fd - grad[b, i, j]) <= 1e-6 * max(1.0, np.abs(grad[b]).max())
+
+
+def test_full_diff_256x6x28_mixed_precision(diff_batch):
+    # mixed forward (pairs of binary32 at the 1e-10 target) and pair backward
+    A = torch.from_numpy(diff_batch).cuda().requires_grad_(True)
+    vals = R().radic_det_autograd(A, precision="mixed")
+    vals.sum().backward()
+    grad = A.grad.cpu().numpy()
+    for b in (0, 128):
+        exact = orc.radic_det_pfaffian(diff_batch[b])
+        abs_sum = R().det(diff_batch[b], mode="fp64")["abs_sum"]
+        assert abs(float(vals[b].detach()) - float(exact)) <= 1e-10 * abs_sum
+    want = np.array([[float(v) for v in row] for row in orc.radic_grad_exact(diff_batch[0], use_pfaffian=True)])
+    assert np.abs(grad[0] - want).max() <= 1e-10 * np.abs(want).max()
