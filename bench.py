@@ -247,6 +247,40 @@ def pair_flops(m: int, n: int, D: int, shared: bool = False) -> int:
     return 18 * c["fma"] + 10 * c["mul"] + 11 * leaves + leaves
 
 
+def cpu_enumeration_rates(W) -> dict:
+    """The binary64 host enumeration of Eq. (1) (oracle/radic_cpu.c: Section 5 runs over OpenMP
+    threads, partial-pivot LU per minor) on every configuration, at full size where it takes
+    seconds and on stated samples elsewhere; minors per second."""
+    import numpy as np
+
+    from oracle import cpu_enum
+
+    def rate(mats, counts=None, q0s=None):
+        done, t0, th = 0, time.perf_counter(), 1
+        for i, a in enumerate(mats):
+            q0 = q0s[i] if q0s else 0
+            cnt = counts[i] if counts else math.comb(a.shape[1], a.shape[0])
+            _, _, th = cpu_enum.radic_cpu_sum(a, q0, cnt)
+            done += cnt
+        return done / (time.perf_counter() - t0), th, done
+
+    out = {}
+    r, th, done = rate([W.int_3x12().astype(np.float64)])
+    out["int_3x12"] = {"value": r, "minors": done, "sample": "full"}
+    r, th, done = rate([W.fp64_8x32()])
+    out["fp64_8x32"] = {"value": r, "minors": done, "sample": "full"}
+    r, th, done = rate([W.int8_12x40().astype(np.float64)], counts=[20_000_000], q0s=[1_000_000_000])
+    out["int8_12x40"] = {"value": r, "minors": done, "sample": "20,000,000 ranks from rank 1e9 (binary64, not exact)"}
+    sub = W.batched_4096()[::64]
+    r, th, done = rate(sub)
+    out["batched_4096"] = {"value": r, "minors": done, "sample": "every 64th matrix (64 matrices), full"}
+    r, th, done = rate(list(W.diff_256x6x28()[:8]))
+    out["diff_256x6x28"] = {"value": r, "minors": done, "sample": "first 8 matrices (forward only), full"}
+    out["threads"] = th
+    out["unit"] = UNIT
+    return out
+
+
 def golden_list(name: str) -> list:
     vals = {}
     with open(os.path.join(ROOT, "tests", "golden", "workload_exact.txt")) as f:
@@ -518,7 +552,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
         pool.terminate()
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"exact Bareiss minors of Eq. (1) for {sample} consecutive dictionary ranks "
-                         f"(from rank {ORACLE_SAMPLE_OFFSET}) of the same workload over {cores} spawn workers"}
+                         f"(from rank {ORACLE_SAMPLE_OFFSET}) of the same workload over {cores} spawn workers",
+               "fp64_enumeration": cpu_enumeration_rates(W)}
 
     if rank == 0:
         line = {

@@ -402,3 +402,33 @@ def test_planted_pfaffian_sign_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(orc, "pfaffian", lambda sk: -good(sk))
     with pytest.raises(AssertionError):
         test_closed_form_matches_definition()
+
+
+# ---------------------------------------------------------------------------
+# Binary64 host enumeration (oracle/radic_cpu.c), the timed CPU baseline
+# ---------------------------------------------------------------------------
+
+
+def test_cpu_enumeration_matches_exact_values():
+    from oracle import cpu_enum
+
+    rng = np.random.default_rng(77)
+    for m, n in [(1, 7), (2, 5), (3, 9), (5, 5), (4, 11), (6, 12), (7, 9), (3, 2)]:
+        a = rng.uniform(-1, 1, (m, n))
+        val, abs_sum = orc.radic_det_exact(a)
+        s, sa, th = cpu_enum.radic_cpu_sum(a)
+        assert th >= 1
+        assert abs(s - float(val)) <= 1e-12 * max(float(abs_sum), 1e-300)
+        assert abs(sa - float(abs_sum)) <= 1e-12 * max(float(abs_sum), 1e-300)
+
+
+def test_cpu_enumeration_rank_ranges_and_integers():
+    from oracle import cpu_enum
+
+    a = np.random.default_rng(78).integers(-9, 10, (4, 10)).astype(np.float64)
+    total = math.comb(10, 4)
+    for q0, count in [(0, 1), (17, 50), (total - 3, 10), (5, total)]:
+        terms = orc.radic_terms_exact(a, range(q0, min(q0 + count, total)))
+        s, sa, _ = cpu_enum.radic_cpu_sum(a, q0, count)
+        assert abs(s - float(sum(terms))) <= 1e-13 * float(sum(abs(t) for t in terms))
+        assert abs(sa - float(sum(abs(t) for t in terms))) <= 1e-13 * float(sum(abs(t) for t in terms))
