@@ -115,19 +115,31 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # oracle baseline (CPU, spawn pool)
 # ---------------------------------------------------------------------------
-def _oracle_chunk(args):
-    lo, hi = args
-    sys.path.insert(0, ROOT)
-    import oracle.radic_oracle as orc
+def _workload_matrix(name: str):
     from paper_1508_01326_gb300 import workloads as W
 
-    terms = orc.radic_terms_exact(W.fp64_8x32(), range(lo, hi))
+    if name == "int_3x12":
+        return W.int_3x12()
+    if name == "int8_10x24":
+        return W.int8_10x24()
+    if name == "diff_6x28":
+        return W.diff_256x6x28()[0]
+    return W.fp64_8x32()
+
+
+def _oracle_chunk(args):
+    lo, hi = args[0], args[1]
+    name = args[2] if len(args) > 2 else "fp64_8x32"
+    sys.path.insert(0, ROOT)
+    import oracle.radic_oracle as orc
+
+    terms = orc.radic_terms_exact(_workload_matrix(name), range(lo, hi))
     return hi - lo, float(sum(terms))
 
 
-def oracle_rate(pool, cores: int, sample: int, offset: int) -> float:
+def oracle_rate(pool, cores: int, sample: int, offset: int, name: str = "fp64_8x32") -> float:
     per = -(-sample // cores)
-    chunks = [(offset + i * per, min(offset + (i + 1) * per, offset + sample)) for i in range(cores)]
+    chunks = [(offset + i * per, min(offset + (i + 1) * per, offset + sample), name) for i in range(cores)]
     chunks = [c for c in chunks if c[0] < c[1]]
     t0 = time.perf_counter()
     done = sum(n for n, _ in pool.map(_oracle_chunk, chunks))
@@ -549,10 +561,18 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
     if pool is not None:
         sample = 160_000
         rate = oracle_rate(pool, cores, sample, ORACLE_SAMPLE_OFFSET)
+        # the exact oracle on the other configurations (bounded samples)
+        oracle_configs = {
+            "int_3x12": {"value": oracle_rate(pool, cores, 220, 0, "int_3x12"), "sample": "all 220 minors"},
+            "int8_10x24": {"value": oracle_rate(pool, cores, 40_000, 500_000, "int8_10x24"),
+                           "sample": "40,000 ranks from rank 500,000 of the 10x24 subcase"},
+            "diff_6x28": {"value": oracle_rate(pool, cores, 80_000, 100_000, "diff_6x28"),
+                          "sample": "80,000 ranks from rank 100,000 of the first 6x28 matrix"}}
         pool.terminate()
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"exact Bareiss minors of Eq. (1) for {sample} consecutive dictionary ranks "
                          f"(from rank {ORACLE_SAMPLE_OFFSET}) of the same workload over {cores} spawn workers",
+               "oracle_configs": oracle_configs,
                "fp64_enumeration": cpu_enumeration_rates(W)}
 
     if rank == 0:
