@@ -98,31 +98,15 @@ __device__ int stage_warp(const BatchArgs& a, const BatchTask& t, int cs, const 
   const int m = t.m, n = t.n, stride = m + 1;
   for (int idx = lane; idx < (n + 1) * stride; idx += 32) {
     const int vv = idx / stride, k = idx - vv * stride;
-    w.binom[idx] = c_binom.v[vv][k];
+    w.binom[idx] = __ldg(&c_binom.v[vv][k]);
   }
   const void* A = a.A;
   int esum = 0;
   for (int i = 0; i < m; ++i) {
     uint32_t h = 0u;
-    double xm = 0.0;
-    for (int j = lane; j < n; j += 32) {
-      const double x = load_elem(A, a.dtype, t.offset + (long long)i * n + j);
-      const uint32_t hx = hi_abs(x);
-      if (hx > h) {
-        h = hx;
-        xm = x;
-      }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const uint32_t ho = __shfl_xor_sync(kFull, h, off);
-      const double xo = __shfl_xor_sync(kFull, xm, off);
-      if (ho > h) {
-        h = ho;
-        xm = xo;
-      }
-    }
-    const int e = row_exponent(h, xm);  // the same in every lane
+    for (int j = lane; j < n; j += 32) h = max(h, hi_abs(load_elem(A, a.dtype, t.offset + (long long)i * n + j)));
+    h = __reduce_max_sync(kFull, h);
+    const int e = row_exponent_bits(h);  // the same in every lane
     esum += e;
     for (int j = lane; j < n; j += 32)
       w.As[j * cs + i] = to_elem<T>(scale_pow2(load_elem(A, a.dtype, t.offset + (long long)i * n + j), e));

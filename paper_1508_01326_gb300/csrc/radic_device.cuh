@@ -21,9 +21,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // ---------------------------------------------------------------------------
 // Binomial table (Section 4, Table 1 / Fig. 1): C(v, k) for 0 <= v, k <= 64.
 // The table is generated at compile time by the Pascal recurrence (every
-// entry is the sum of the two entries above it) and lives in constant memory;
-// each block copies the (n+1) x (kmax+1) part it needs into shared memory as
-// binom[v * (kmax + 1) + k] with one barrier.
+// entry is the sum of the two entries above it) and lives in global memory
+// (read-only): the lanes of a warp read different entries, which the constant
+// cache would serialise.  Each block copies the (n+1) x (kmax+1) part it needs
+// into shared memory as binom[v * (kmax + 1) + k] with one barrier.
 // ---------------------------------------------------------------------------
 struct BinomConst {
   unsigned long long v[kMaxN + 1][kMaxN + 1];
@@ -38,13 +39,13 @@ constexpr BinomConst make_binom_const() {
   return t;
 }
 
-static __constant__ BinomConst c_binom = make_binom_const();
+static __device__ const BinomConst c_binom = make_binom_const();
 
 __device__ inline void build_binom(uint64_t* binom, int n, int kmax) {
   const int stride = kmax + 1;
   for (int idx = threadIdx.x; idx < (n + 1) * stride; idx += blockDim.x) {
     const int v = idx / stride, k = idx - v * stride;
-    binom[idx] = c_binom.v[v][k];
+    binom[idx] = __ldg(&c_binom.v[v][k]);
   }
   __syncthreads();
 }
@@ -312,35 +313,35 @@ __device__ __forceinline__ void warp_reduce_ff(Ff& t, Ff& ta) {
   }
 }
 
-// Block-wide fixed-order reduction of float-float lane totals and a count:
-// the warp trees stay on the binary32 pipe (binary64 runs at 1/64 of its
-// rate) and only the warps' totals are widened to binary64 two-sums.  The
-// result is valid in thread 0.  `scratch` holds 4 * (blockDim.x / 32) words.
-__device__ inline void block_reduce_ff(Ff t, Ff ta, long long& count, double* scratch, Dd& acc, double& abs_sum) {
+// Block-wide fixed-order reduction of float-float lane totals and a count,
+// entirely on the binary32 pipe (binary64 runs at 1/64 of its rate): warp
+// trees, then the warps' totals in warp order.  The result is valid in thread
+// 0.  `scratch` holds 4 * (blockDim.x / 32) binary64 words.
+__device__ inline void block_reduce_ff(Ff& t, Ff& ta, long long& count, double* scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   warp_reduce_ff(t, ta);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) count += __shfl_xor_sync(kFull, count, off);
+  float* fs = reinterpret_cast<float*>(scratch);
   __syncthreads();
   if (lane == 0) {
-    scratch[4 * warp + 0] = static_cast<double>(t.hi);
-    scratch[4 * warp + 1] = static_cast<double>(t.lo);
-    scratch[4 * warp + 2] = static_cast<double>(ta.hi) + static_cast<double>(ta.lo);
-    scratch[4 * warp + 3] = __longlong_as_double(count);
+    fs[8 * warp + 0] = t.hi;
+    fs[8 * warp + 1] = t.lo;
+    fs[8 * warp + 2] = ta.hi;
+    fs[8 * warp + 3] = ta.lo;
+    scratch[4 * warp + 2] = __longlong_as_double(count);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    Dd d;
-    double ab = 0.0;
+    Ff s, sa;
     long long cnt = 0;
     for (int w = 0; w < nw; ++w) {
-      d.add(scratch[4 * w + 0]);
-      d.add(scratch[4 * w + 1]);
-      ab += scratch[4 * w + 2];
-      cnt += __double_as_longlong(scratch[4 * w + 3]);
+      s.merge(Ff{fs[8 * w + 0], fs[8 * w + 1]});
+      sa.merge(Ff{fs[8 * w + 2], fs[8 * w + 3]});
+      cnt += __double_as_longlong(scratch[4 * w + 2]);
     }
-    acc = d;
-    abs_sum = ab;
+    t = s;
+    ta = sa;
     count = cnt;
   }
 }
@@ -409,19 +410,6 @@ __device__ __forceinline__ uint32_t hi_abs(double x) {
   return static_cast<uint32_t>(__double2hiint(x)) & 0x7fffffffu;
 }
 
-// Exponent e with |x| * 2^-e in [0.5, 1) for the entry x whose hi_abs is
-// `h` (0 for a zero, infinite or NaN row maximum, as frexp's convention).
-__device__ __forceinline__ int row_exponent(uint32_t h, double x) {
-  const int be = static_cast<int>(h >> 20);
-  if (h == 0u || be == 0x7ff) return 0;
-  if (be == 0) {  // subnormal maximum: rare, take the library path
-    int e = 0;
-    frexp(x, &e);
-    return e;
-  }
-  return be - 1022;
-}
-
 // x * 2^-e, exact: one multiply by a power of two built from its bits when
 // 2^-e is a normal binary64 number, ldexp otherwise.
 __device__ __forceinline__ double scale_pow2(double x, int e) {
@@ -429,39 +417,56 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
   return ldexp(x, -e);
 }
 
+// Exponent e with |x| * 2^-e in [0.5, 1) for the row maximum x whose hi_abs
+// is h, from the bits alone (0 for a zero, infinite or NaN maximum, as
+// frexp's convention).  A subnormal maximum takes the position of the leading
+// bit of its high word: bit b there has the value 2^(b - 1042).
+__device__ __forceinline__ int row_exponent_bits(uint32_t h) {
+  const int be = static_cast<int>(h >> 20);
+  if (h == 0u || be == 0x7ff) return 0;
+  if (be == 0) return (32 - __clz(static_cast<int>(h))) - 1042;
+  return be - 1022;
+}
+
 template <typename T>
 __device__ inline int stage_scaled(const void* A, int dtype, int m, int n, long long lda, T* As, int cs,
                                    int* row_exp /* smem, m ints */) {
-  // 1. one warp per row: largest magnitude -> exponent e_i (|row| in [0.5, 1) after scaling)
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i < m; i += nw) {
-    uint32_t h = 0u;
-    double xm = 0.0;
-    for (int j = lane; j < n; j += 32) {
-      const double x = load_elem(A, dtype, (long long)i * lda + j);
-      const uint32_t hx = hi_abs(x);
-      if (hx > h) {
-        h = hx;
-        xm = x;
-      }
-    }
+  // 1. row maxima as hi_abs keys, by shared-memory atomics over all entries
+  //    at once; the first kKeep entries of every thread stay in registers
+  constexpr int kKeep = 4;
+  unsigned* row_h = reinterpret_cast<unsigned*>(row_exp);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) row_h[i] = 0u;
+  __syncthreads();
+  const int mn = m * n;
+  double keep[kKeep];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const uint32_t ho = __shfl_xor_sync(kFull, h, off);
-      const double xo = __shfl_xor_sync(kFull, xm, off);
-      if (ho > h) {
-        h = ho;
-        xm = xo;
-      }
+  for (int k = 0; k < kKeep; ++k) {
+    const int idx = threadIdx.x + k * blockDim.x;
+    keep[k] = 0.0;
+    if (idx < mn) {
+      const int i = idx / n, j = idx - i * n;
+      keep[k] = load_elem(A, dtype, (long long)i * lda + j);
+      atomicMax(&row_h[i], hi_abs(keep[k]));
     }
-    if (lane == 0) row_exp[i] = row_exponent(h, xm);
+  }
+  for (int idx = threadIdx.x + kKeep * blockDim.x; idx < mn; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    atomicMax(&row_h[i], hi_abs(load_elem(A, dtype, (long long)i * lda + j)));
   }
   __syncthreads();
   // 2. scaled copy (exact power-of-two scaling) into the column-major shared
   //    copy, padding rows zeroed for vector loads
-  for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
+#pragma unroll
+  for (int k = 0; k < kKeep; ++k) {
+    const int idx = threadIdx.x + k * blockDim.x;
+    if (idx < mn) {
+      const int i = idx / n, j = idx - i * n;
+      As[j * cs + i] = to_elem<T>(scale_pow2(keep[k], row_exponent_bits(row_h[i])));
+    }
+  }
+  for (int idx = threadIdx.x + kKeep * blockDim.x; idx < mn; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
-    As[j * cs + i] = to_elem<T>(scale_pow2(load_elem(A, dtype, (long long)i * lda + j), row_exp[i]));
+    As[j * cs + i] = to_elem<T>(scale_pow2(load_elem(A, dtype, (long long)i * lda + j), row_exponent_bits(row_h[i])));
   }
   for (int idx = threadIdx.x; idx < (cs - m) * n; idx += blockDim.x) {
     const int j = idx / (cs - m), i = m + (idx - j * (cs - m));
@@ -469,7 +474,7 @@ __device__ inline int stage_scaled(const void* A, int dtype, int m, int n, long 
   }
   __syncthreads();
   int tot = 0;
-  for (int i = 0; i < m; ++i) tot += row_exp[i];
+  for (int i = 0; i < m; ++i) tot += row_exponent_bits(row_h[i]);
   return tot;
 }
 

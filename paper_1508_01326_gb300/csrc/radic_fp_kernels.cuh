@@ -80,8 +80,8 @@ __device__ inline void write_fp_result(radic_result* out, const Dd& t, double ab
   // unit roundoff of the elimination: binary64, pairs of binary32 (about
   // 2^-46 per operation, 2^-44 allows for the renormalisations), binary32
   const double u = (tier == kModeFp64) ? 0x1p-53 : (tier == kModePair ? 0x1p-44 : 0x1p-24);
-  out->value = ldexp(t.hi + t.lo, escale);
-  out->abs_sum = ldexp(abs_sum, escale);
+  out->value = scale_pow2(t.hi + t.lo, -escale);
+  out->abs_sum = scale_pow2(abs_sum, -escale);
   out->err_est = static_cast<double>(m) * u * out->abs_sum;
   out->exact_lo = 0;
   out->exact_hi = 0;
@@ -128,6 +128,37 @@ __device__ inline void finish_fp_main(const SingleArgs& a, double* scratch, int 
       a.hdr->escale = escale;
     }
     write_fp_result(a.out, t, ab, escale, m, a.total, 0, a.hdr->status, tier);
+  }
+}
+
+// The same for the binary32-elimination prefix kernel, whose partials are
+// float-float (FfPartial): the sum over blocks stays on the binary32 pipe and
+// is widened to binary64 once.  The rounding of these merges (about 2^-46 of
+// the magnitudes added, per level) lies far below the binary32 rounding of
+// the minors that the mixed mode's error estimate states.
+__device__ inline void finish_ff_main(const SingleArgs& a, double* scratch, int escale, int m) {
+  if (!last_block(&a.hdr->ticket[0])) return;
+  const FfPartial* p = reinterpret_cast<const FfPartial*>(a.partials);
+  Ff t, ta;
+  long long fl = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(&p[b]));
+    t.merge(Ff{v.x, v.y});
+    ta.merge(Ff{v.z, v.w});
+    fl += __ldcg(&p[b].count);
+  }
+  block_reduce_ff(t, ta, fl, scratch);
+  if (threadIdx.x == 0) {
+    Dd d;  // exact widening of the pair
+    d.hi = static_cast<double>(t.hi);
+    d.lo = static_cast<double>(t.lo);
+    const double ab = static_cast<double>(ta.hi) + static_cast<double>(ta.lo);
+    a.hdr->main_hi = d.hi;
+    a.hdr->main_lo = d.lo;
+    a.hdr->main_abs = ab;
+    a.hdr->flag_total = fl;
+    a.hdr->escale = escale;
+    write_fp_result(a.out, d, ab, escale, m, a.total, 0, a.hdr->status, kModeMixed);
   }
 }
 

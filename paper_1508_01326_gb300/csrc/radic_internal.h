@@ -53,6 +53,16 @@ struct FpPartial {
   long long count;
 };
 
+// Per-block partial of the binary32-elimination prefix kernel: float-float
+// totals of the signed minors and of their magnitudes, stored in the same
+// workspace slots as FpPartial.
+struct FfPartial {
+  float hi, lo, abs_hi, abs_lo;
+  long long count;
+  long long pad;
+};
+static_assert(sizeof(FfPartial) == sizeof(FpPartial), "partials share their slots");
+
 // Per-group task table of the prefix mapping, passed by value to the kernel.
 // Group v holds the prefixes whose last column is v; a warp task covers 32
 // runs of run[v] consecutive prefixes of one group.

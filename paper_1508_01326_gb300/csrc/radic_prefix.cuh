@@ -681,18 +681,20 @@ __global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(Singl
         fl = fcnt;
       }
     }
-    Dd d;
-    double ab;
     if constexpr (std::is_same<T, float>::value) {
-      block_reduce_ff(acc.tot, acc.tot_abs, fl, sm.scratch, d, ab);
+      block_reduce_ff(acc.tot, acc.tot_abs, fl, sm.scratch);
+      if (threadIdx.x == 0)
+        reinterpret_cast<FfPartial*>(a.partials)[blockIdx.x] =
+            FfPartial{acc.tot.hi, acc.tot.lo, acc.tot_abs.hi, acc.tot_abs.lo, fl, 0};
+      finish_ff_main(a, sm.scratch, escale, M);
     } else {
       acc.finish();
-      d = acc.acc;
-      ab = acc.abs_sum;
+      Dd d = acc.acc;
+      double ab = acc.abs_sum;
       block_reduce_dd(d, ab, fl, sm.scratch);
+      if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{d.hi, d.lo, ab, fl};
+      finish_fp_main<kMixed>(a, sm.scratch, escale, M, tier_of<T, kMixed>());
     }
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{d.hi, d.lo, ab, fl};
-    finish_fp_main<kMixed>(a, sm.scratch, escale, M, tier_of<T, kMixed>());
   }
 }
 
