@@ -76,20 +76,25 @@ int plan_prefix(SinglePlan pl, const radic_options& d, int sms, int per_sm, unsi
   for (int v = t.v_lo; v <= t.v_hi; ++v) {
     // Lanes per prefix: a prefix with many candidate columns costs far more
     // than a lane's share of the launch (the leaves grow like C(k, D)), so
-    // its leaves are split over LP lanes of the warp, each of which repeats
-    // the factorisation and the column reductions.  LP is the smallest power
-    // of two that brings a lane's cost down to the mean per-lane work.
+    // its column reductions and leaves are split over LP lanes of the warp,
+    // each of which repeats the factorisation.  LP is the smallest power of
+    // two that brings a lane's cost down to a target near the mean per-lane
+    // work.
     int lp = 1;
     if (d.lanes_per_prefix > 0) {
       lp = d.lanes_per_prefix;
     } else if (D == 3) {
       // Only depth 3 (its leaves grow like C(k, 3); splitting depth-2
-      // prefixes measured slower).  Target: twice the mean lane work when
-      // that is large, four times when the launch is small and the repeated
-      // factorisations would dominate (measured on the shapes of
-      // prefix_auto_depth).
+      // prefixes measured slower).  Target with binary32 elimination: 1.4
+      // times the mean lane work when that is large, three times when the
+      // launch is small and the repeated factorisations would dominate.
+      // Binary64 and pair leaves keep their pipes busy, so there the balance
+      // of the warps' shares matters more than the repeated work: the mean
+      // itself.  (Measured on the shapes of prefix_auto_depth, warps drawing
+      // tasks from the shared counter.)
       const double mean = 4.0 * per_lane;
-      const double target = (mean >= 1000.0 ? 2.0 : 4.0) * mean;
+      const double tf = (pl.mode == kModeMixed) ? (mean >= 1000.0 ? 1.4 : 3.0) : 1.0;
+      const double target = tf * mean;
       const double red = prefix_cost_shared(m, D, n - 1 - v), split = cost[v] - red;
       while (lp < 32 && red + split / lp > target) lp *= 2;
     }

@@ -104,19 +104,39 @@ __host__ __device__ constexpr int tier_of() {
   return !kMixed ? kModeFp64 : (std::is_same<T, ff>::value ? kModePair : kModeMixed);
 }
 
+constexpr int kFinishUnroll = 8;
+
 template <bool kMixed>
 __device__ inline void finish_fp_main(const SingleArgs& a, double* scratch, int escale, int m, int tier) {
   if (!last_block(&a.hdr->ticket[0])) return;
   Dd t;
   double ab = 0.0;
   long long fl = 0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    Dd o;
-    o.hi = __ldcg(&a.partials[b].hi);
-    o.lo = __ldcg(&a.partials[b].lo);
-    t.merge(o);
-    ab += __ldcg(&a.partials[b].abs_sum);
-    fl += __ldcg(&a.partials[b].count);
+  // partials b = tid, tid + blockDim, ... in that order; kFinishUnroll of
+  // them are loaded before any is added, so that their L2 round trips overlap
+  const int nb = gridDim.x, bd = blockDim.x;
+  for (int b0 = threadIdx.x; b0 < nb; b0 += kFinishUnroll * bd) {
+    double2 v[kFinishUnroll];
+    double va[kFinishUnroll];
+    long long vc[kFinishUnroll];
+#pragma unroll
+    for (int u = 0; u < kFinishUnroll; ++u) {
+      const int b = b0 + u * bd;
+      v[u] = b < nb ? __ldcg(reinterpret_cast<const double2*>(&a.partials[b])) : make_double2(0.0, 0.0);
+      va[u] = b < nb ? __ldcg(&a.partials[b].abs_sum) : 0.0;
+      vc[u] = b < nb ? __ldcg(&a.partials[b].count) : 0ll;
+    }
+#pragma unroll
+    for (int u = 0; u < kFinishUnroll; ++u) {
+      if (b0 + u * bd < nb) {
+        Dd o;
+        o.hi = v[u].x;
+        o.lo = v[u].y;
+        t.merge(o);
+        ab += va[u];
+        fl += vc[u];
+      }
+    }
   }
   block_reduce_dd(t, ab, fl, scratch);
   if (threadIdx.x == 0) {
@@ -141,11 +161,24 @@ __device__ inline void finish_ff_main(const SingleArgs& a, double* scratch, int 
   const FfPartial* p = reinterpret_cast<const FfPartial*>(a.partials);
   Ff t, ta;
   long long fl = 0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    const float4 v = __ldcg(reinterpret_cast<const float4*>(&p[b]));
-    t.merge(Ff{v.x, v.y});
-    ta.merge(Ff{v.z, v.w});
-    fl += __ldcg(&p[b].count);
+  const int nb = gridDim.x, bd = blockDim.x;
+  for (int b0 = threadIdx.x; b0 < nb; b0 += kFinishUnroll * bd) {
+    float4 v[kFinishUnroll];
+    long long vc[kFinishUnroll];
+#pragma unroll
+    for (int u = 0; u < kFinishUnroll; ++u) {
+      const int b = b0 + u * bd;
+      v[u] = b < nb ? __ldcg(reinterpret_cast<const float4*>(&p[b])) : make_float4(0.f, 0.f, 0.f, 0.f);
+      vc[u] = b < nb ? __ldcg(&p[b].count) : 0ll;
+    }
+#pragma unroll
+    for (int u = 0; u < kFinishUnroll; ++u) {
+      if (b0 + u * bd < nb) {
+        t.merge(Ff{v[u].x, v[u].y});
+        ta.merge(Ff{v[u].z, v[u].w});
+        fl += vc[u];
+      }
+    }
   }
   block_reduce_ff(t, ta, fl, scratch);
   if (threadIdx.x == 0) {

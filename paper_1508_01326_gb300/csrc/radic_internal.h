@@ -43,7 +43,7 @@ struct WsHeader {
   long long flag_total;     // MIXED: flagged minors or prefixes seen by the main kernel
   int escale;               // exponent of the row scaling
   int pad;
-  long long reserved[1];
+  unsigned long long next_task;  // prefix kernels: tasks handed out after each warp's first
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
 
@@ -171,10 +171,11 @@ inline double prefix_cost(int m, int D, int k) {
 }
 
 // The part of prefix_cost that every lane sharing one prefix repeats: the
-// factorisation and the k column reductions.
+// factorisation (depth 3 lanes split the k column reductions as well as the
+// leaves; depth 2 does not split prefixes).
 inline double prefix_cost_shared(int m, int D, int k) {
   const int P = m - D;
-  return (double)m * P * P + (double)k * (m + 2.0 * D * P);
+  return (double)m * P * P + (D == 3 ? 0.0 : (double)k * (m + 2.0 * D * P));
 }
 
 // Default prefix depth for an m x n matrix.  Depth 3 divides the number of

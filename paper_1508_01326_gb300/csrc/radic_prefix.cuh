@@ -84,6 +84,12 @@ struct ZBuf<T, 3> {
   int stride, plane;
   __device__ ZBuf(void* base, int lane, int stride_, int kcap)
       : p(static_cast<T*>(base) + lane), stride(stride_), plane(kcap * stride_) {}
+  // the buffer of the lane `d` positions away
+  __device__ __forceinline__ ZBuf shifted(int d) const {
+    ZBuf b = *this;
+    b.p += d;
+    return b;
+  }
   __device__ __forceinline__ void get(int q, T (&y)[3]) const {
     const T* e = p + q * stride;
     y[0] = e[0];
@@ -341,7 +347,11 @@ __device__ __forceinline__ void leaf_column(const T* __restrict__ As, int col, c
 // takes the leaves whose second-to-last column from the buffer is
 // congruent to sub modulo lp (and sub 0 those inside a block); every lane
 // computes all columns' z.
-template <typename T, int M, int D, int CS>
+//
+// kCoop: the buffer already holds every column's z (written by the lanes
+// sharing the prefix, see prefix_leaves); the block's columns are read from
+// it instead of being reduced here.
+template <typename T, int M, int D, int CS, bool kCoop>
 __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, int v, int k, const T (&W)[D][M - D],
                                                       const int (&idx)[M], T alpha, const ZBuf<T, D>& zb, bool act,
                                                       int sub, int lp, PrefixAcc<T>& acc, T& zmax) {
@@ -351,7 +361,11 @@ __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, 
 #pragma unroll
     for (int b = 0; b < LB; ++b) {
       if (q + b < k) {  // the same k in every lane of a warp
-        leaf_column<T, M, D, CS>(As, v + 1 + q + b, W, idx, alpha, z[b], zmax);
+        if constexpr (kCoop) {
+          zb.get(q + b, z[b]);
+        } else {
+          leaf_column<T, M, D, CS>(As, v + 1 + q + b, W, idx, alpha, z[b], zmax);
+        }
       } else {
 #pragma unroll
         for (int d = 0; d < D; ++d) z[b][d] = T(0);
@@ -428,11 +442,28 @@ __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, 
 #pragma unroll
     for (int b = 0; b < LB; ++b) {
       if (q + b < k) {
-        zb.put(q + b, z[b]);
+        if constexpr (!kCoop) zb.put(q + b, z[b]);
         if (act) acc.add_column(cs[b], ca[b]);
       }
     }
   }
+}
+
+// Largest value over the aligned group of lp lanes (lp a power of two).
+__device__ __forceinline__ float group_max(float x, int lp) {
+  for (int off = 1; off < lp; off <<= 1) x = fmaxf(x, __shfl_xor_sync(kFull, x, off));
+  return x;
+}
+__device__ __forceinline__ double group_max(double x, int lp) {
+  for (int off = 1; off < lp; off <<= 1) x = fmax(x, __shfl_xor_sync(kFull, x, off));
+  return x;
+}
+__device__ __forceinline__ ff group_max(ff x, int lp) {
+  for (int off = 1; off < lp; off <<= 1) {
+    const ff o(__shfl_xor_sync(kFull, x.hi, off), __shfl_xor_sync(kFull, x.lo, off));
+    x = fmax(x, o);
+  }
+  return x;
 }
 
 // Leaf phase with per-leaf output (terms of the parity tests): one column at
@@ -513,7 +544,26 @@ __device__ __forceinline__ bool prefix_leaves(const T* __restrict__ As, const ui
     prefix_leaves_terms<T, M, D, CS>(As, binom, n, v, k, W, idx, alpha, rank_prefix, zb, act, sub, lp, acc, zmax,
                                      ts);
   } else {
-    prefix_leaves_blocked<T, M, D, CS>(As, v, k, W, idx, alpha, zb, act, sub, lp, acc, zmax);
+    if constexpr (D == 3) {
+      // Two phases.  The lp lanes sharing the prefix split its column
+      // reductions: lane `sub` reduces the columns q = sub (mod lp) into the
+      // group's buffer (the slots of the group's first lane); then each lane
+      // forms its share of the leaves from all of them (W and the row order
+      // are no longer live there).  Every lane ends with the group's largest
+      // |z| for the growth flag.
+      const ZBuf<T, D> zg = zb.shifted(-sub);
+      for (int q = sub; q < k; q += lp) {
+        T z[D];
+        leaf_column<T, M, D, CS>(As, v + 1 + q, W, idx, alpha, z, zmax);
+        zg.put(q, z);
+      }
+      zmax = group_max(zmax, lp);
+      __syncwarp();
+      prefix_leaves_blocked<T, M, D, CS, true>(As, v, k, W, idx, alpha, zg, act, sub, lp, acc, zmax);
+      __syncwarp();  // the buffer is rewritten by the group's next prefix
+    } else {
+      prefix_leaves_blocked<T, M, D, CS, false>(As, v, k, W, idx, alpha, zb, act, sub, lp, acc, zmax);
+    }
   }
   const T growth_bound = (D == 2 ? T(2) : T(4)) * zmax;
   return !(gmax <= thr) || !(growth_bound <= thr) || !(fabs(alpha) <= static_cast<T>(FLT_MAX));
@@ -631,8 +681,20 @@ __global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(Singl
   if constexpr (kMixed && !kTerms) flist = a.flag_ranks + gwarp * (unsigned long long)a.flag_cap;
   TermsSink ts{static_cast<double*>(a.terms), a.q0, a.count, sm.binom[n * bs + M], escale};
 
-  for (unsigned long long t = gwarp; t < tab.total_tasks; t += nwarps) {
-    int v = tab.v_lo;
+  // Tasks are numbered heaviest group first (ascending v: the most candidate
+  // columns).  A warp's first task is its own index; each later one comes
+  // from a counter in the workspace header, fetched while the current task
+  // runs, so that warps that drew light tasks take more of them.  The
+  // per-term launches have no workspace and stride by the number of warps.
+  // A warp's task numbers only grow, so its group search resumes where the
+  // previous task's ended.
+  unsigned long long t = gwarp;
+  int v = tab.v_lo;
+  while (t < tab.total_tasks) {
+    unsigned long long t_next = t + nwarps;
+    if constexpr (!kTerms) {
+      if (lane == 0) t_next = nwarps + atomicAdd(&a.hdr->next_task, 1ull);
+    }
     while (v < tab.v_hi && t >= tab.task_start[v + 1]) ++v;
     const unsigned long long runlen = tab.run[v], cnt = tab.count[v];
     // lanes [grp * lp, grp * lp + lp) share each prefix of one run
@@ -671,6 +733,7 @@ __global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(Singl
         if (r0 + it + 1 < r1) successor<P - 1>(head, v);
       }
     }
+    t = kTerms ? t_next : __shfl_sync(kFull, t_next, 0);
   }
   if constexpr (!kTerms) {
     long long fl = 0;
