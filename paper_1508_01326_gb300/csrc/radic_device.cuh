@@ -56,24 +56,57 @@ __device__ inline void build_binom(uint64_t* binom, int n, int kmax) {
 // combinatorial number system: with r = C(n,m) - 1 - q, position i takes the
 // largest v with C(v, m-i) <= r, sets j_i = n - 1 - v and subtracts C(v, m-i).
 // ---------------------------------------------------------------------------
+// k! in binary32 (exact up to k = 13; k <= 34 stays finite).
+__host__ __device__ constexpr float fact_f(int k) {
+  float f = 1.0f;
+  for (int j = 2; j <= k; ++j) f *= static_cast<float>(j);
+  return f;
+}
+
+// Largest w <= v - 1 with C(w, k) <= r.  The search starts at the estimate
+// w ~ (k! r)^(1/k) + (k-1)/2 (from C(w, k) ~ (w - (k-1)/2)^k / k!, which the
+// AM-GM inequality shows is an upper bound) and then steps through the
+// table to the exact value, so that the estimate only sets the number of
+// steps (usually none or one) and never the result.  *b receives C(w, k).
+template <int K>
+__device__ __forceinline__ int unrank_pos(uint64_t r, int v, const uint64_t* binom, int bstride, uint64_t* b) {
+  const float x = exp2f((__log2f(static_cast<float>(r)) + __log2f(fact_f(K))) * (1.0f / K)) + 0.5f * (K - 1);
+  int w = static_cast<int>(fminf(x, static_cast<float>(v - 1)));  // r = 0 gives (k-1)/2
+  w = max(w, K - 1);
+  // both neighbours of the estimate in one round trip
+  uint64_t bw = binom[w * bstride + K];
+  uint64_t b1 = (w + 1 < v) ? binom[(w + 1) * bstride + K] : 0ull;
+  if (bw > r) {
+    do {  // C(k-1, k) = 0 ends this
+      --w;
+      bw = binom[w * bstride + K];
+    } while (bw > r);
+  } else {
+    while (w + 1 < v && b1 <= r) {
+      ++w;
+      bw = b1;
+      if (w + 1 < v) b1 = binom[(w + 1) * bstride + K];
+    }
+  }
+  *b = bw;
+  return w;
+}
+
+template <int M, int I = 0>
+__device__ __forceinline__ void unrank_from(uint64_t r, int v, int n, const uint64_t* binom, int bstride,
+                                            int (&c)[M]) {
+  if constexpr (I < M) {
+    uint64_t b;
+    const int w = unrank_pos<M - I>(r, v, binom, bstride, &b);
+    c[I] = n - 1 - w;
+    unrank_from<M, I + 1>(r - b, w, n, binom, bstride, c);
+  }
+}
+
 template <int M>
 __device__ __forceinline__ void unrank(uint64_t q, int n, const uint64_t* binom, int bstride,
                                        int (&c)[M]) {
-  uint64_t r = binom[n * bstride + M] - 1 - q;
-  int v = n;
-#pragma unroll
-  for (int i = 0; i < M; ++i) {
-    const int k = M - i;
-    int w = v - 1;
-    uint64_t b = binom[w * bstride + k];
-    while (b > r) {
-      --w;
-      b = binom[w * bstride + k];
-    }
-    c[i] = n - 1 - w;
-    r -= b;
-    v = w;
-  }
+  unrank_from<M>(binom[n * bstride + M] - 1 - q, n, n, binom, bstride, c);
 }
 
 // Dynamic-m form for the group mapping (c has capacity G >= m).
