@@ -341,12 +341,12 @@ __device__ __forceinline__ void leaf_column(const T* __restrict__ As, int col, c
 // taken LB at a time (q, q+1, ...).  For each block, the leaves whose other
 // D-1 columns lie before the block read those columns' z from the buffer
 // once for the whole block; leaves with two or three columns inside the
-// block are formed from registers.  Leaf sums are kept per column and added
-// to acc in column order.  Columns past k in the last block are zero and
-// their sums are discarded.  When `lp` lanes share the prefix, lane `sub`
-// takes the leaves whose second-to-last column from the buffer is
-// congruent to sub modulo lp (and sub 0 those inside a block); every lane
-// computes all columns' z.
+// block are formed from registers.  Leaf sums are kept per column, and a
+// block's column sums are added together to acc in block order.  Columns
+// past k in the last block are zero, and so are their leaves.  When `lp`
+// lanes share the prefix, lane `sub` takes the leaves whose second-to-last
+// column from the buffer is congruent to sub modulo lp (and sub 0 those
+// inside a block).
 //
 // kCoop: the buffer already holds every column's z (written by the lanes
 // sharing the prefix, see prefix_leaves); the block's columns are read from
@@ -392,8 +392,8 @@ __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, 
         }
       }
     } else {
-      // (q1, q2, q + b), q1 < q2 < q: y1 . (y2 x z_b)
-      for (int q2 = sub; q2 < q; q2 += lp) {
+      // (q1, q2, q + b), q1 < q2 < q: y1 . (y2 x z_b); q2 = 0 has no q1
+      for (int q2 = (sub == 0 ? lp : sub); q2 < q; q2 += lp) {
         T y2[3];
         zb.get(q2, y2);
         T w[LB][3];
@@ -439,11 +439,19 @@ __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, 
         }
       }
     }
+    // the block's column sums (columns past k hold zeros) enter the
+    // prefix sum together
+    T bsum = cs[0], babs = ca[0];
 #pragma unroll
-    for (int b = 0; b < LB; ++b) {
-      if (q + b < k) {
-        if constexpr (!kCoop) zb.put(q + b, z[b]);
-        if (act) acc.add_column(cs[b], ca[b]);
+    for (int b = 1; b < LB; ++b) {
+      bsum += cs[b];
+      babs += ca[b];
+    }
+    if (act) acc.add_column(bsum, babs);
+    if constexpr (!kCoop) {
+#pragma unroll
+      for (int b = 0; b < LB; ++b) {
+        if (q + b < k) zb.put(q + b, z[b]);
       }
     }
   }
@@ -652,9 +660,13 @@ __device__ __forceinline__ void prefix_extend(const T* __restrict__ As, int v, c
 #ifndef RADIC_PREFIX_MIN_BLOCKS_F32
 #define RADIC_PREFIX_MIN_BLOCKS_F32 1
 #endif
+#ifndef RADIC_PREFIX_MIN_BLOCKS_FF
+#define RADIC_PREFIX_MIN_BLOCKS_FF 1
+#endif
 template <typename T>
 __host__ __device__ constexpr int prefix_min_blocks() {
-  return std::is_same<T, float>::value ? RADIC_PREFIX_MIN_BLOCKS_F32 : 1;
+  return std::is_same<T, float>::value ? RADIC_PREFIX_MIN_BLOCKS_F32
+                                       : (std::is_same<T, ff>::value ? RADIC_PREFIX_MIN_BLOCKS_FF : 1);
 }
 
 template <typename T, int M, int D, bool kMixed, bool kTerms>
