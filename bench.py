@@ -38,6 +38,11 @@ MINORS = math.comb(N, M)
 FLOP_PER_MINOR = 2 * ((M - 1) * M * (2 * M - 1) // 6) + (M - 1) * M // 2 + (M - 1)  # 2*FMA + mul = 315
 # Binary32 FMA peak from unit counts and the maximum clock: 152 SMs x 128 lanes x 2 flop x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# headline kernel, averaged over the 66 launches of the ncu launch list of
+# `bench.py --headline-only --no-cpu-baseline --steps 20 --warmup 5`; to be set
+# back to None whenever that kernel changes until it is captured again.
+HEADLINE_DRAM_BYTES = 75.3e3
 WORKLOAD = (f"fp64_8x32: one 8x32 binary64 matrix, entries uniform[-1,1) from numpy PCG64 seed 2, "
             f"C(32,8)={MINORS} minors")
 ORACLE_SAMPLE_OFFSET = 1_000_000
@@ -589,7 +594,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
             "rel_err": res_head["rel_err"], "flagged": res_head["flagged"],
             **side,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": HEADLINE_DRAM_BYTES,
                          "kernel": f"k_fp_prefix<float,8,{depth['mixed']},mixed>", "kernel_ms": kern_mean_ms,
                          "flop_per_launch": flops,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (derived)"},
