@@ -114,7 +114,17 @@ typedef struct radic_options {
   int32_t lanes_per_prefix; /* PREFIX mapping: lanes of a warp that share the
                                leaves of one prefix (1, 2, 4, ..., 32; 0:
                                per prefix group, from the plan's cost model) */
-  int64_t reserved[2];
+  int32_t deterministic;    /* PREFIX mapping, floating-point modes: 0
+                               (default) = after its first task a warp draws
+                               the next from a counter, which evens out the
+                               warps' work; which warp sums which prefixes then
+                               varies, so repeated calls can differ in the last
+                               bits of value and abs_sum (far below err_est).
+                               1 = every warp takes a fixed share of the
+                               tasks: repeated calls give identical bits.
+                               The exact mode is exact either way. */
+  int32_t reserved32;
+  int64_t reserved[1];
 } radic_options;
 
 /* Device-resident result of one determinant (16 eight-byte words). */

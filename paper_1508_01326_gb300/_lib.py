@@ -30,7 +30,9 @@ class RadicOptions(ctypes.Structure):
         ("kernel_events", ctypes.c_void_p),
         ("prefix_depth", ctypes.c_int32),
         ("lanes_per_prefix", ctypes.c_int32),
-        ("reserved", ctypes.c_int64 * 2),
+        ("deterministic", ctypes.c_int32),
+        ("reserved32", ctypes.c_int32),
+        ("reserved", ctypes.c_int64 * 1),
     ]
 
 
@@ -128,7 +130,7 @@ def check(fn: str, code: int) -> None:
 def make_options(mapping: str | int = 0, group_width: int = 0, ranks_per_task: int = 0,
                  threads_per_block: int = 0, blocks: int = 0, flag_capacity: int = 0,
                  growth_threshold: float = 0.0, kernel_events: int = 0, prefix_depth: int = 0,
-                 lanes_per_prefix: int = 0) -> RadicOptions:
+                 lanes_per_prefix: int = 0, deterministic: bool = False) -> RadicOptions:
     o = RadicOptions()
     o.mapping = MAPPINGS[mapping] if isinstance(mapping, str) else int(mapping)
     o.group_width = group_width
@@ -140,4 +142,5 @@ def make_options(mapping: str | int = 0, group_width: int = 0, ranks_per_task: i
     o.kernel_events = kernel_events or None
     o.prefix_depth = prefix_depth
     o.lanes_per_prefix = lanes_per_prefix
+    o.deterministic = 1 if deterministic else 0
     return o

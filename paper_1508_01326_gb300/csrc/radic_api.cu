@@ -63,6 +63,7 @@ int plan_prefix(SinglePlan pl, const radic_options& d, int sms, int per_sm, unsi
   PrefixTable& t = pl.ptab;
   t.v_lo = P - 1;
   t.v_hi = n - 1 - D;
+  t.dynamic = d.deterministic ? 0 : 1;
   double total_cost = 0.0;
   double cost[kMaxN] = {0};
   for (int v = t.v_lo; v <= t.v_hi; ++v) {

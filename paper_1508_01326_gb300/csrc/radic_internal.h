@@ -73,6 +73,7 @@ struct PrefixTable {
   unsigned long long run[kMaxN];           // prefixes per lane group in one task
   unsigned long long task_start[kMaxN];    // first task index of group v
   int lanes[kMaxN];                        // lanes sharing one prefix in group v (1..32, power of 2)
+  int dynamic;                             // warps draw later tasks from the header counter
 };
 
 // Launch plan of one single-matrix call (computed identically by

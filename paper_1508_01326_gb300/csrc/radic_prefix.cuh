@@ -697,7 +697,8 @@ __global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(Singl
   // columns).  A warp's first task is its own index; each later one comes
   // from a counter in the workspace header, fetched while the current task
   // runs, so that warps that drew light tasks take more of them.  The
-  // per-term launches have no workspace and stride by the number of warps.
+  // per-term launches (no workspace) and deterministic plans stride by the
+  // number of warps instead.
   // A warp's task numbers only grow, so its group search resumes where the
   // previous task's ended.
   unsigned long long t = gwarp;
@@ -705,7 +706,7 @@ __global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(Singl
   while (t < tab.total_tasks) {
     unsigned long long t_next = t + nwarps;
     if constexpr (!kTerms) {
-      if (lane == 0) t_next = nwarps + atomicAdd(&a.hdr->next_task, 1ull);
+      if (tab.dynamic && lane == 0) t_next = nwarps + atomicAdd(&a.hdr->next_task, 1ull);
     }
     while (v < tab.v_hi && t >= tab.task_start[v + 1]) ++v;
     const unsigned long long runlen = tab.run[v], cnt = tab.count[v];
@@ -745,7 +746,7 @@ __global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(Singl
         if (r0 + it + 1 < r1) successor<P - 1>(head, v);
       }
     }
-    t = kTerms ? t_next : __shfl_sync(kFull, t_next, 0);
+    t = (kTerms || !tab.dynamic) ? t_next : __shfl_sync(kFull, t_next, 0);
   }
   if constexpr (!kTerms) {
     long long fl = 0;

@@ -382,6 +382,21 @@ def test_det_is_deterministic():
         assert v1 == v2
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "pair"])
+def test_prefix_task_schedules(mode):
+    # 8 x 32: more warp tasks than warps.  A fixed task share per warp
+    # (deterministic) gives the same bits on every call; tasks drawn from the
+    # counter (default) change only the rounding of the sums.
+    a = dev(W.fp64_8x32())
+    fixed = [R().parse_result(R().radic_det(a, mode=mode, options=dict(deterministic=True))) for _ in range(3)]
+    for r in fixed[1:]:
+        assert (r["value"], r["abs_sum"]) == (fixed[0]["value"], fixed[0]["abs_sum"])
+    for _ in range(3):
+        r = R().parse_result(R().radic_det(a, mode=mode))
+        assert abs(r["value"] - fixed[0]["value"]) <= 1e-13 * fixed[0]["abs_sum"]
+        assert abs(r["abs_sum"] - fixed[0]["abs_sum"]) <= 1e-13 * fixed[0]["abs_sum"]
+
+
 @pytest.mark.parametrize("key", ["thread", "g16", "prefix2", "prefix3", "prefix3_lp8", "prefix3_lp32"])
 def test_mixed_growth_flag_recomputes_in_binary64(key):
     # Partial pivoting grows the last column of this minor to 2^(m-1) times
