@@ -68,9 +68,16 @@ enum { RADIC_I8 = 0, RADIC_I32 = 1, RADIC_F32 = 2, RADIC_F64 = 3 };
  *           exceeds the threshold, or whose result is not finite, are
  *           recomputed in binary64; sums are compensated (float-float per
  *           run of ranks, then binary64 two-sum across runs and blocks).
- *  EXACT -- integer inputs only: LU modulo 31-bit primes (as many as a
- *           Hadamard bound needs, at most RADIC_MAX_PRIMES) and Chinese
- *           remaindering to a signed 128-bit integer, bit-exact.
+ *  EXACT -- LU modulo 31-bit primes (as many as a Hadamard bound needs, at
+ *           most RADIC_MAX_PRIMES) and Chinese remaindering to a signed
+ *           128-bit integer, bit-exact.  Integer inputs directly; binary32
+ *           and binary64 inputs (radic_det only) as the dyadic rationals they
+ *           are: row i is scaled by 2^-e_i, e_i the exponent of the lowest
+ *           set bit among its nonzero entries, to an integer row, and the
+ *           result is the integer times 2^exact_exp, exact_exp = sum_i e_i.
+ *           Inputs with many significant bits per row (for instance random
+ *           binary64 values) exceed the prime budget: status
+ *           RADIC_EOVERFLOW.  A non-finite entry: status RADIC_EINVAL.
  *  PAIR  -- the MIXED scheme with the elimination carried out in pairs of
  *           binary32 numbers (hi + lo, about 48 significant bits, on the
  *           binary32 pipe): PREFIX mapping, 3 <= m <= 10; flagged prefixes
@@ -139,7 +146,9 @@ typedef struct radic_result {
   int64_t status;   /* RADIC_OK, RADIC_EOVERFLOW, RADIC_ETIMEOUT ...           */
   int64_t n_primes; /* EXACT: primes used                                      */
   int64_t tier;     /* mode that produced value (batched router decision)      */
-  int64_t reserved[6];
+  int64_t exact_exp;/* EXACT: det_R(A) = (exact_hi:exact_lo) * 2^exact_exp
+                       (0 for integer inputs; see RADIC_MODE_EXACT)            */
+  int64_t reserved[5];
 } radic_result;
 
 /* ---- general ------------------------------------------------------------ */
@@ -184,9 +193,9 @@ int radic_plan_info(int m, int n, int mode, const radic_options* opts, int64_t* 
  * combined in a fixed order by the last block (tree sum of Section 6).
  * Calls on different streams need separate workspaces.
  * Errors: RADIC_EINVAL (m or n out of range, lda < n, NULL A or out,
- * unknown dtype/mode, EXACT with a real dtype), RADIC_EWORKSPACE,
- * RADIC_ECUDA.  Device: out->status = RADIC_EOVERFLOW when the exact value
- * could exceed the prime budget. */
+ * unknown dtype/mode), RADIC_EWORKSPACE, RADIC_ECUDA.  Device:
+ * out->status = RADIC_EOVERFLOW when the exact value could exceed the prime
+ * budget, RADIC_EINVAL when EXACT meets a non-finite real entry. */
 int radic_det(const void* A, int m, int n, int64_t lda, int dtype, int mode,
               const radic_options* opts, radic_result* out, void* workspace,
               size_t workspace_bytes, void* stream);
@@ -200,8 +209,8 @@ int radic_det(const void* A, int m, int n, int64_t lda, int dtype, int mode,
  *        residues in [0, p), prime-major in the order of radic_primes; only
  *        the first K rows are written, K being the number of primes
  *        radic_det uses for this A (radic_result.n_primes).
- * No workspace.  Errors: RADIC_EINVAL (as radic_det, or a rank outside
- * [0, C(n,m))), RADIC_ECUDA. */
+ * No workspace.  Errors: RADIC_EINVAL (as radic_det, EXACT with a real
+ * dtype, or a rank outside [0, C(n,m))), RADIC_ECUDA. */
 int radic_terms(const void* A, int m, int n, int64_t lda, int dtype, int mode,
                 const radic_options* opts, uint64_t q0, uint64_t count,
                 void* terms, void* stream);

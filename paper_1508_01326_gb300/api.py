@@ -145,6 +145,7 @@ def parse_result(buf: torch.Tensor) -> dict:
         "status": int(w[7]),
         "n_primes": int(w[8]),
         "tier": int(w[9]),
+        "exact_exp": int(w[10]),
     }
 
 
@@ -160,7 +161,9 @@ def det(A, mode="fp64", options=None, stream=None) -> dict:
     if res["status"] != 0:
         raise L.RadicError("radic_det (device)", res["status"])
     if _mode(mode) == L.MODES["exact"]:
-        res["value_exact"] = Fraction(res["exact"])
+        # det_R(A) = exact * 2^exact_exp (the exponent is 0 for integer inputs)
+        e = res["exact_exp"]
+        res["value_exact"] = Fraction(res["exact"]) * (Fraction(2) ** e)
     return res
 
 

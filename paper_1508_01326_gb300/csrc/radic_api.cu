@@ -283,7 +283,8 @@ __global__ void k_zero_result(radic_result* out, int tier) {
   out->status = RADIC_OK;
   out->n_primes = (tier == kModeExact) ? 1 : 0;
   out->tier = tier;
-  for (int i = 0; i < 6; ++i) out->reserved[i] = 0;
+  out->exact_exp = 0;
+  for (int i = 0; i < 5; ++i) out->reserved[i] = 0;
 }
 
 template <int M>
@@ -428,7 +429,6 @@ int radic_plan_info(int m, int n, int mode, const radic_options* opts, int64_t* 
 int radic_det(const void* A, int m, int n, int64_t lda, int dtype, int mode, const radic_options* opts,
               radic_result* out, void* workspace, size_t workspace_bytes, void* stream) {
   if (!A || !out || lda < n || !valid_dtype(dtype)) return RADIC_EINVAL;
-  if (mode == kModeExact && (dtype == kF32 || dtype == kF64)) return RADIC_EINVAL;
   SinglePlan p;
   const unsigned long long total = (m >= 1 && n >= 1 && m <= n && n <= kMaxN) ? binom_host(n, m) : 0ull;
   const int rc = make_plan(m, n, mode, opts, total, &p);

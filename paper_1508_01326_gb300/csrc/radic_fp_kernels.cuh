@@ -90,7 +90,8 @@ __device__ inline void write_fp_result(radic_result* out, const Dd& t, double ab
   out->status = status;
   out->n_primes = 0;
   out->tier = tier;
-  for (int i = 0; i < 6; ++i) out->reserved[i] = 0;
+  out->exact_exp = 0;
+  for (int i = 0; i < 5; ++i) out->reserved[i] = 0;
 }
 
 // Last block of the main kernel: sums the per-block partials in block order

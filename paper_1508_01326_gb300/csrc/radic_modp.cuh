@@ -80,6 +80,7 @@ __host__ __device__ inline size_t modp_smem_bytes(int n, int m, int cs, int thre
   off += ((size_t)m * n * 4 + 15) / 16 * 16;
   off += (size_t)(threads / 32) * kMaxPrimes * 4;
   off += 64 + kMaxPrimes * sizeof(Mont);
+  off += (size_t)kMaxM * 4;  // row exponents of floating-point inputs
   return off;
 }
 
@@ -88,8 +89,9 @@ struct ModpSmem {
   uint32_t* As;  // prime k at As + k * n * cs
   uint32_t* rows;
   uint32_t* scratch;
-  int* misc;
+  int* misc;  // [0] primes the bound needs, [1] total row exponent
   Mont* mont;
+  int* row_e;  // floating-point inputs: row i times 2^-row_e[i] is integer
   __device__ ModpSmem(unsigned char* base, int n, int m, int cs, int threads) {
     size_t off = ((size_t)(n + 1) * (m + 1) * 8 + 15) / 16 * 16;
     binom = reinterpret_cast<uint64_t*>(base);
@@ -102,12 +104,100 @@ struct ModpSmem {
     misc = reinterpret_cast<int*>(base + off);
     off += 64;
     mont = reinterpret_cast<Mont*>(base + off);
+    off += kMaxPrimes * sizeof(Mont);
+    row_e = reinterpret_cast<int*>(base + off);
   }
 };
 
 __device__ __forceinline__ long long load_int(const void* A, int dtype, long long idx) {
   return dtype == kI8 ? static_cast<long long>(static_cast<const int8_t*>(A)[idx])
                       : static_cast<long long>(static_cast<const int32_t*>(A)[idx]);
+}
+
+// ---------------------------------------------------------------------------
+// Floating-point inputs.  A binary64 number (binary32 widens to it exactly)
+// is +-mant * 2^t with an integer mant < 2^53, so every entry is a dyadic
+// rational.  Row i times 2^-e_i, with e_i the exponent of the lowest set bit
+// over the row's nonzero entries, is an integer row; every minor is linear
+// in each row, so det_R(A) = 2^(sum_i e_i) det_R(M) with M that integer
+// matrix, and det_R(M) is found exactly by the modular path.
+// ---------------------------------------------------------------------------
+struct FpBits {
+  uint64_t mant;
+  int t;
+  bool neg, finite;
+};
+__device__ __forceinline__ FpBits fp_bits(double x) {
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const int E = static_cast<int>((b >> 52) & 0x7ffu);
+  const uint64_t f = b & ((1ull << 52) - 1ull);
+  FpBits r;
+  r.neg = (b >> 63) != 0;
+  r.finite = E != 0x7ff;
+  r.mant = E ? (f | (1ull << 52)) : f;
+  r.t = E ? E - 1075 : -1074;
+  return r;
+}
+__device__ __forceinline__ double load_fp(const void* A, int dtype, long long idx) {
+  return dtype == kF32 ? static_cast<double>(static_cast<const float*>(A)[idx]) : static_cast<const double*>(A)[idx];
+}
+__device__ __forceinline__ bool is_fp_dtype(int dtype) { return dtype == kF32 || dtype == kF64; }
+
+// 2^k mod p, k >= 0 (square and multiply).
+__device__ inline uint64_t pow2_mod(int k, uint64_t p) {
+  uint64_t r = 1, b = 2 % p;
+  while (k) {
+    if (k & 1) r = r * b % p;
+    b = b * b % p;
+    k >>= 1;
+  }
+  return r % p;
+}
+
+// Residue of the integer x * 2^-e modulo p (e at most the exponent of x's
+// lowest set bit, so that the shift below drops only zeros).
+__device__ inline uint32_t fp_residue(double x, int e, uint32_t p) {
+  const FpBits f = fp_bits(x);
+  if (f.mant == 0) return 0u;
+  uint64_t r;
+  if (f.t >= e) {
+    r = (f.mant % p) * pow2_mod(f.t - e, p) % p;
+  } else {
+    r = (f.mant >> (e - f.t)) % p;
+  }
+  return (f.neg && r) ? static_cast<uint32_t>(p - r) : static_cast<uint32_t>(r);
+}
+
+// Row exponents e_i (into row_e) and, per row, the bits of a bound on the
+// Euclidean norm of the integer row: |entry| < 2^(top_i + 1 - e_i) with top_i
+// the exponent of the highest set bit, so ||M_i|| < sqrt(n) 2^(top_i + 1 - e_i).
+// A zero row has e_i = 0 and no bits (all its minors are zero).  Sets
+// *nonfinite (shared) when an entry is infinite or NaN.
+__device__ inline void fp_row_scales(const void* A, int dtype, int m, int n, long long lda, int* row_e,
+                                     double* row_bits, int* nonfinite) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < m; i += nw) {
+    int lo = 0x7fffffff, hi = -0x7fffffff;
+    bool bad = false;
+    for (int j = lane; j < n; j += 32) {
+      const FpBits f = fp_bits(load_fp(A, dtype, (long long)i * lda + j));
+      if (!f.finite) {
+        bad = true;
+      } else if (f.mant) {
+        lo = min(lo, f.t + __ffsll(static_cast<long long>(f.mant)) - 1);
+        hi = max(hi, f.t + 63 - __clzll(static_cast<long long>(f.mant)));
+      }
+    }
+    lo = __reduce_min_sync(kFull, lo);
+    hi = __reduce_max_sync(kFull, hi);
+    bad = __any_sync(kFull, bad);
+    if (lane == 0) {
+      const bool zero = hi == -0x7fffffff;
+      row_e[i] = zero ? 0 : lo;
+      row_bits[i] = zero ? 0.0 : static_cast<double>(hi + 1 - lo) + 0.5 * log2(static_cast<double>(n));
+      if (bad) *nonfinite = 1;
+    }
+  }
 }
 
 // Number of primes for |det_R(A)| <= C(n,m) prod_i ||row_i||_2 (Hadamard's
@@ -139,12 +229,35 @@ __device__ inline int stage_modp(const SingleArgs& a, const ModpSmem& sm, int m,
   const int n = a.n;
   build_binom(sm.binom, n, m);
   if (threadIdx.x < kMaxPrimes) sm.mont[threadIdx.x] = make_mont(prime_at(threadIdx.x));
+  const bool fp = is_fp_dtype(a.dtype);
   {
     // the rows scratch (m x n words) is free until the residues are staged
     double* row_sq = reinterpret_cast<double*>(sm.rows);
     const double cnt = static_cast<double>(sm.binom[n * (m + 1) + m]);
-    const int need = primes_needed(a.A, a.dtype, m, n, a.lda, log2(fmax(cnt, 1.0)), row_sq);
-    if (threadIdx.x == 0) sm.misc[0] = need;
+    if (fp) {
+      if (threadIdx.x == 0) sm.misc[2] = 0;
+      __syncthreads();
+      fp_row_scales(a.A, a.dtype, m, n, a.lda, sm.row_e, row_sq, &sm.misc[2]);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double bits = log2(fmax(cnt, 1.0));
+        int esum = 0;
+        for (int i = 0; i < m; ++i) {
+          bits += row_sq[i];
+          esum += sm.row_e[i];
+        }
+        const int k = static_cast<int>(ceil((bits + 2.0) / 30.99));
+        sm.misc[0] = k < 1 ? 1 : k;
+        sm.misc[1] = esum;
+        if (sm.misc[2]) atomicExch(&a.hdr->status, RADIC_EINVAL);  // an entry is not finite
+      }
+    } else {
+      const int need = primes_needed(a.A, a.dtype, m, n, a.lda, log2(fmax(cnt, 1.0)), row_sq);
+      if (threadIdx.x == 0) {
+        sm.misc[0] = need;
+        sm.misc[1] = 0;
+      }
+    }
   }
   __syncthreads();
   *needed = sm.misc[0];
@@ -153,9 +266,13 @@ __device__ inline int stage_modp(const SingleArgs& a, const ModpSmem& sm, int m,
     const uint32_t p = prime_at(k);
     for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
       const int i = idx / n, j = idx - i * n;
-      long long v = load_int(a.A, a.dtype, (long long)i * a.lda + j) % (long long)p;
-      if (v < 0) v += p;
-      sm.rows[idx] = static_cast<uint32_t>(v);
+      if (fp) {
+        sm.rows[idx] = fp_residue(load_fp(a.A, a.dtype, (long long)i * a.lda + j), sm.row_e[i], p);
+      } else {
+        long long v = load_int(a.A, a.dtype, (long long)i * a.lda + j) % (long long)p;
+        if (v < 0) v += p;
+        sm.rows[idx] = static_cast<uint32_t>(v);
+      }
     }
     __syncthreads();
     // rows <- U rows (unit upper: row i += sum_{l > i} U_il row_l), ascending i
@@ -303,7 +420,7 @@ __device__ inline uint64_t powmod64(uint64_t b, uint64_t e, uint64_t p) {
 
 // Garner reconstruction of the signed value in (-P/2, P/2].
 __device__ inline void crt_write(radic_result* out, const uint32_t* res, int K, int needed, int status,
-                                 unsigned long long total) {
+                                 unsigned long long total, int escale) {
   uint64_t v[kMaxPrimes];
   for (int i = 0; i < K; ++i) {
     const uint64_t p = prime_at(i);
@@ -330,7 +447,7 @@ __device__ inline void crt_write(radic_result* out, const uint32_t* res, int K, 
   const unsigned __int128 mag = negv ? static_cast<unsigned __int128>(-sx) : static_cast<unsigned __int128>(sx);
   const double val = ldexp(static_cast<double>(static_cast<uint64_t>(mag >> 64)), 64) +
                      static_cast<double>(static_cast<uint64_t>(mag));
-  out->value = negv ? -val : val;
+  out->value = ldexp(negv ? -val : val, escale);
   out->abs_sum = 0.0;
   out->err_est = 0.0;
   out->minors = static_cast<long long>(total);
@@ -338,7 +455,8 @@ __device__ inline void crt_write(radic_result* out, const uint32_t* res, int K, 
   out->status = (needed > kMaxPrimes) ? RADIC_EOVERFLOW : status;
   out->n_primes = K;
   out->tier = kModeExact;
-  for (int i = 0; i < 6; ++i) out->reserved[i] = 0;
+  out->exact_exp = escale;
+  for (int i = 0; i < 5; ++i) out->reserved[i] = 0;
 }
 
 // Last-block epilogue shared by both mappings.
@@ -352,7 +470,7 @@ __device__ inline void finish_modp(const SingleArgs& a, const ModpSmem& sm, uint
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
       for (int k = 0; k < K; ++k) t[k] = add_mod(t[k], __ldcg(&a.modp_partials[b * kMaxPrimes + k]), prime_at(k));
     block_reduce_modp(t, K, sm.scratch);
-    if (threadIdx.x == 0) crt_write(a.out, t, K, needed, __ldcg(&a.hdr->status), a.total);
+    if (threadIdx.x == 0) crt_write(a.out, t, K, needed, __ldcg(&a.hdr->status), a.total, sm.misc[1]);
   }
 }
 

@@ -61,8 +61,9 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.radic_det(None, 3, 5, 5, 3, 0, None, dummy, dummy, 1 << 20, None) == 1
     # lda < n
     assert lib.radic_det(dummy, 3, 5, 4, 3, 0, None, dummy, dummy, 1 << 20, None) == 1
-    # exact mode with a real dtype
-    assert lib.radic_det(dummy, 3, 5, 5, 3, 2, None, dummy, dummy, 1 << 20, None) == 1
+    # per-term exact residues of a real dtype (radic_det takes real inputs in
+    # the exact mode, radic_terms does not)
+    assert lib.radic_terms(dummy, 3, 5, 5, 3, 2, None, 0, 1, dummy, None) == 1
     # unknown dtype, unknown mode
     assert lib.radic_det(dummy, 3, 5, 5, 9, 0, None, dummy, dummy, 1 << 20, None) == 1
     assert lib.radic_det(dummy, 3, 5, 5, 3, 7, None, dummy, dummy, 1 << 20, None) == 1

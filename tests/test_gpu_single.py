@@ -353,6 +353,49 @@ def test_det_exact_small(m, n, dtype, bound, mapping):
     assert res["value"] == float(val)
 
 
+def _dyadic(seed, m, n, dtype):
+    # small integers times per-entry and per-row powers of two: binary32 and
+    # binary64 hold them exactly, and the scaled integer rows stay short
+    rng = np.random.default_rng(seed)
+    k = rng.integers(-60, 61, (m, n))
+    s = rng.integers(0, 5, (m, n))
+    r = rng.integers(-6, 7, (m, 1))
+    return (k * np.ldexp(1.0, -s) * np.ldexp(1.0, r)).astype(dtype)
+
+
+@pytest.mark.parametrize("key", ["auto", "thread", "g16", "prefix2", "prefix3", "prefix3_lp8"])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("m,n", [(1, 6), (3, 12), (6, 14), (8, 13)])
+def test_det_exact_real_inputs(m, n, dtype, key):
+    # Exact mode on real inputs: the integer matrix of the row-scaled entries
+    # times 2^exact_exp, against the oracle's rational value
+    if key.startswith("prefix") and m <= OPTS[key]["prefix_depth"]:
+        pytest.skip("prefix mapping: m > prefix depth")
+    a = _dyadic(700 + m * n, m, n, dtype)
+    val, _ = orc.radic_det_exact(a.astype(np.float64))
+    res = R().det(a, mode="exact", options=None if key == "auto" else OPTS[key])
+    assert res["status"] == 0
+    assert res["value_exact"] == val
+    assert res["value"] == float(val)
+
+
+def test_det_exact_real_inputs_limits():
+    # random binary64 entries carry ~53 significant bits per entry: beyond
+    # the prime budget, reported as RADIC_EOVERFLOW; a non-finite entry is
+    # RADIC_EINVAL on the device
+    out = R().radic_det(dev(W.uniform_matrix(5, 6, 12)), mode="exact")
+    assert R().parse_result(out)["status"] == 2
+    a = _dyadic(5, 4, 9, np.float64)
+    a[2, 3] = np.inf
+    out = R().radic_det(dev(a), mode="exact")
+    assert R().parse_result(out)["status"] == 1
+    # an all-zero row: every minor is zero
+    a = _dyadic(6, 4, 9, np.float64)
+    a[1] = 0.0
+    res = R().parse_result(R().radic_det(dev(a), mode="exact"))
+    assert res["status"] == 0 and res["exact"] == 0
+
+
 def test_det_square_and_row_special_cases():
     rng = np.random.default_rng(9)
     for size in [1, 2, 5, 8]:
