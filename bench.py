@@ -42,7 +42,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # headline kernel, averaged over the 66 launches of the ncu launch list of
 # `bench.py --headline-only --no-cpu-baseline --steps 20 --warmup 5`; to be set
 # back to None whenever that kernel changes until it is captured again.
-HEADLINE_DRAM_BYTES = 75.3e3
+HEADLINE_DRAM_BYTES = 76.2e3
 WORKLOAD = (f"fp64_8x32: one 8x32 binary64 matrix, entries uniform[-1,1) from numpy PCG64 seed 2, "
             f"C(32,8)={MINORS} minors")
 ORACLE_SAMPLE_OFFSET = 1_000_000
