@@ -231,6 +231,34 @@ def test_exact_conversion_of_floats():
     assert Fraction(mat[0][0], den) == Fraction(float(np.float32(0.1)))
 
 
+def test_row_power_of_two_scaling_of_real_inputs():
+    # Every term of Eq. (1) is a determinant, linear in each row, so scaling
+    # row i by 2^-e_i multiplies det_R by 2^-e_i.  With e_i the exponent of
+    # the lowest set bit of row i's nonzero entries the scaled rows are
+    # integers: det_R(A) = 2^(sum e_i) det_R(M), the reading the exact mode
+    # uses for binary32 and binary64 inputs.  A dropped or doubled exponent,
+    # or a wrongly signed one, fails here.
+    rng = np.random.default_rng(11)
+    for m, n in [(1, 4), (2, 5), (3, 7), (4, 8)]:
+        k = rng.integers(-30, 31, (m, n))
+        s = rng.integers(0, 6, (m, n))
+        r = rng.integers(-5, 6, (m, 1))
+        a = k * np.ldexp(1.0, -s) * np.ldexp(1.0, r)
+        e = []
+        for i in range(m):
+            lows = []
+            for x in a[i]:
+                f = Fraction(float(x))
+                if f != 0:
+                    lows.append((f.numerator & -f.numerator).bit_length() - 1 - (f.denominator.bit_length() - 1))
+            e.append(min(lows) if lows else 0)
+        mat = [[int(Fraction(float(a[i, j])) / Fraction(2) ** e[i]) for j in range(n)] for i in range(m)]
+        assert all(Fraction(float(a[i, j])) == mat[i][j] * Fraction(2) ** e[i] for i in range(m) for j in range(n))
+        want, _ = orc.radic_det_exact(np.array(mat, dtype=np.int64))
+        got, _ = orc.radic_det_exact(a)
+        assert got == Fraction(want) * Fraction(2) ** sum(e)
+
+
 # ---------------------------------------------------------------------------
 # Pfaffian closed form
 # ---------------------------------------------------------------------------
