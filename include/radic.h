@@ -56,7 +56,7 @@ enum {
   RADIC_ECUDA = 3,       /* a CUDA runtime call failed                         */
   RADIC_ETIMEOUT = 4,    /* a bounded device-side wait gave up                 */
   RADIC_EWORKSPACE = 5,  /* workspace pointer null/misaligned or too small     */
-  RADIC_EUNSUPPORTED = 6 /* valid request this build does not implement        */
+  RADIC_EUNSUPPORTED = 6 /* valid request the library does not implement       */
 };
 
 /* Element type of A. */
