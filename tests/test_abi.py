@@ -41,6 +41,49 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def test_struct_layouts_match_header(tmp_path):
+    # The binding's ctypes structures against the header compiled as C: the
+    # offset of every field and the size of every structure.
+    import shutil
+    import subprocess
+
+    from paper_1508_01326_gb300 import _lib as L
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"radic_options": L.RadicOptions, "radic_batch_tuning": L.RadicBatchTuning}
+    lines = ['#include <stdio.h>', '#include "radic.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append('  printf("radic_result size %zu\\n", sizeof(radic_result));')
+    for fname in ["value", "abs_sum", "err_est", "exact_lo", "exact_hi", "minors", "flagged", "status", "n_primes",
+                  "tier", "exact_exp"]:
+        lines.append(f'  printf("radic_result {fname} %zu\\n", offsetof(radic_result, {fname}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-x", "c", "-std=c11", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = {}
+    for row in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        sname, field, value = row.split()
+        got[(sname, field)] = int(value)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+    # the binding reads radic_result as 16 eight-byte words (parse_result)
+    assert got[("radic_result", "size")] == 8 * L.RESULT_WORDS
+    order = ["value", "abs_sum", "err_est", "exact_lo", "exact_hi", "minors", "flagged", "status", "n_primes", "tier",
+             "exact_exp"]
+    for word, fname in enumerate(order):
+        assert got[("radic_result", fname)] == 8 * word, fname
+
+
 def test_host_only_calls(lib):
     assert lib.radic_version() >= 10000
     assert lib.radic_status_string(0) == b"ok"
