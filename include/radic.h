@@ -181,6 +181,20 @@ size_t radic_workspace_bytes(int m, int n, int mode, const radic_options* opts);
 #define RADIC_PLAN_INFO_COUNT 8
 int radic_plan_info(int m, int n, int mode, const radic_options* opts, int64_t* info, int count);
 
+/* Host-only view of the prefix mapping's task table (the Section 5 split of
+ * the minors into contiguous runs, here runs of prefixes grouped by their
+ * last column v), planned for `sms` SMs with `blocks_per_sm` resident blocks
+ * instead of the current device: no GPU is touched.  opts->mapping is taken
+ * as RADIC_MAP_PREFIX.  info (host, count >= 8 + 4n int64): [0] prefix depth
+ * D, [1] warp tasks, [2] blocks, [3] v_lo, [4] v_hi, [5] 1 when warps draw
+ * tasks from the counter, [6..7] 0; then for every v four entries at
+ * 8 + 4v: prefixes whose last column is v (C(v, m-D-1)), prefixes per lane
+ * group in one task, lanes per prefix, first task of the group (0 outside
+ * v_lo..v_hi).  Errors: RADIC_EINVAL, RADIC_EUNSUPPORTED as radic_det's
+ * planning. */
+int radic_prefix_plan_host(int m, int n, int mode, const radic_options* opts, int sms, int blocks_per_sm,
+                           int64_t* info, int count);
+
 /* det_R(A) of one m x n matrix (Eq. (1)).
  * A:        device, m x n, row-major with leading dimension lda, type dtype.
  * out:      device, one radic_result, fully overwritten.

@@ -19,6 +19,7 @@ from .api import (  # noqa: F401
     parse_result,
     radic_det,
     radic_plan_info,
+    prefix_plan_host,
     radic_primes,
     radic_status_string,
     radic_terms,

@@ -78,6 +78,21 @@ def radic_plan_info(m: int, n: int, mode="fp64", options=None) -> dict:
     return info
 
 
+def prefix_plan_host(m: int, n: int, mode="mixed", options=None, sms: int = 152, blocks_per_sm: int = 3) -> dict:
+    """The prefix mapping's task table for a given SM count and residency, planned on the host
+    only (radic_prefix_plan_host): depth, tasks, blocks, and per last prefix column v the prefix
+    count, run length, lanes per prefix and first task."""
+    count = 8 + 4 * int(n)
+    buf = (ctypes.c_int64 * count)()
+    L.check("radic_prefix_plan_host", L.lib().radic_prefix_plan_host(int(m), int(n), _mode(mode), _opts(options),
+                                                                     int(sms), int(blocks_per_sm), buf, count))
+    v_lo, v_hi = int(buf[3]), int(buf[4])
+    groups = {v: {"count": int(buf[8 + 4 * v]), "run": int(buf[9 + 4 * v]), "lanes": int(buf[10 + 4 * v]),
+                  "task_start": int(buf[11 + 4 * v])} for v in range(v_lo, v_hi + 1)}
+    return {"depth": int(buf[0]), "tasks": int(buf[1]), "blocks": int(buf[2]), "v_lo": v_lo, "v_hi": v_hi,
+            "dynamic": bool(buf[5]), "groups": groups}
+
+
 def new_result(device=None) -> torch.Tensor:
     """Device buffer for one radic_result (sixteen int64 words)."""
     return torch.empty(L.RESULT_WORDS, dtype=torch.int64, device=device or "cuda")

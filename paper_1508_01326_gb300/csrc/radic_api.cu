@@ -134,7 +134,8 @@ int plan_prefix(SinglePlan pl, const radic_options& d, int sms, int per_sm, unsi
 
 // Plans a launch over `units` ranks (C(n,m) for radic_det, `count` for
 // radic_terms).  Returns a RADIC_* code.
-int make_plan_uncached(int m, int n, int mode, const radic_options* o, unsigned long long units, SinglePlan* p);
+int make_plan_uncached(int m, int n, int mode, const radic_options* o, unsigned long long units, SinglePlan* p,
+                       int sms_given = 0, int per_sm_given = 0);
 
 // Plans are pure functions of (device, shape, mode, options, units); repeated
 // calls on one shape (the common case when serving) reuse the plan instead of
@@ -172,7 +173,10 @@ int make_plan(int m, int n, int mode, const radic_options* o, unsigned long long
   return rc;
 }
 
-int make_plan_uncached(int m, int n, int mode, const radic_options* o, unsigned long long units, SinglePlan* p) {
+// sms_given / per_sm_given > 0 replace the device's SM count and the
+// occupancy query (host-only planning).
+int make_plan_uncached(int m, int n, int mode, const radic_options* o, unsigned long long units, SinglePlan* p,
+                       int sms_given, int per_sm_given) {
   if (m < 1 || m > kMaxM || n < 1 || n > kMaxN || !valid_mode(mode)) return RADIC_EINVAL;
   radic_options d;
   std::memset(&d, 0, sizeof(d));
@@ -219,8 +223,8 @@ int make_plan_uncached(int m, int n, int mode, const radic_options* o, unsigned 
   pl.events = d.kernel_events;
   pl.smem = smem_of(pl);
 
-  const int sms = device_sm_count();
-  const int per_sm = blocks_per_sm(pl);
+  const int sms = sms_given > 0 ? sms_given : device_sm_count();
+  const int per_sm = per_sm_given > 0 ? per_sm_given : blocks_per_sm(pl);
   if (sms <= 0) return RADIC_ECUDA;
   if (per_sm <= 0) return RADIC_EUNSUPPORTED;
   // Work split of Section 5: K processors (threads, or lane groups) each take
@@ -423,6 +427,34 @@ int radic_plan_info(int m, int n, int mode, const radic_options* opts, int64_t* 
   v[6] = (int64_t)p.smem;
   v[7] = (int64_t)p.ws_bytes;
   for (int i = 0; i < count; ++i) info[i] = v[i];
+  return RADIC_OK;
+}
+
+int radic_prefix_plan_host(int m, int n, int mode, const radic_options* opts, int sms, int blocks_per_sm,
+                           int64_t* info, int count) {
+  if (!info || sms < 1 || blocks_per_sm < 1 || count < 8 + 4 * n) return RADIC_EINVAL;
+  if (m < 1 || n < 1 || n > kMaxN || m > n) return RADIC_EINVAL;
+  radic_options d;
+  std::memset(&d, 0, sizeof(d));
+  if (opts) d = *opts;
+  d.mapping = RADIC_MAP_PREFIX;
+  SinglePlan p;
+  const int rc = make_plan_uncached(m, n, mode, &d, binom_host(n, m), &p, sms, blocks_per_sm);
+  if (rc != RADIC_OK) return rc;
+  const PrefixTable& t = p.ptab;
+  for (int i = 0; i < count; ++i) info[i] = 0;
+  info[0] = p.depth;
+  info[1] = static_cast<int64_t>(t.total_tasks);
+  info[2] = p.blocks;
+  info[3] = t.v_lo;
+  info[4] = t.v_hi;
+  info[5] = t.dynamic;
+  for (int v = t.v_lo; v <= t.v_hi; ++v) {
+    info[8 + 4 * v + 0] = static_cast<int64_t>(t.count[v]);
+    info[8 + 4 * v + 1] = static_cast<int64_t>(t.run[v]);
+    info[8 + 4 * v + 2] = t.lanes[v];
+    info[8 + 4 * v + 3] = static_cast<int64_t>(t.task_start[v]);
+  }
   return RADIC_OK;
 }
 
