@@ -297,6 +297,22 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
                             const radic_batch_tuning* tuning, radic_batch_plan** plan);
 int radic_batch_plan_destroy(radic_batch_plan* plan);
 
+/* Host-only view of the tasks radic_batch_plan_create would make for the
+ * same arguments (routing, task split and task order), without a GPU: the
+ * Section 5 split of each matrix's ranks into contiguous runs, one run per
+ * lane, 32 lanes per task.  tasks (host, capacity rows of eight int64):
+ * matrix b, tier (RADIC_MODE_MIXED for binary32, _PAIR, _FP64), kind (0: per
+ * minor, else the prefix depth D), shared (1: units are heads, the first
+ * m-D-1 prefix columns), group (last prefix or head column; 0 per minor),
+ * r0 (first unit of lane 0), run (units per lane), lim (end of the group's
+ * unit range: C(v, m-D-1) prefixes, C(u, m-D-2) heads or C(n,m) ranks).
+ * Lane l of a task takes units [r0 + l*run, min(r0 + (l+1)*run, lim)).
+ * *n_tasks receives the total; rows past capacity are not written.  Errors
+ * as radic_batch_plan_create's planning (RADIC_EINVAL, RADIC_EUNSUPPORTED). */
+int radic_batch_plan_tasks_host(const int32_t* m, const int32_t* n, const int64_t* offsets, int batch, int mode,
+                                const radic_batch_tuning* tuning, int64_t* tasks, int64_t capacity,
+                                int64_t* n_tasks);
+
 /* Workspace bytes the plan needs (256-byte aligned device memory). */
 size_t radic_batch_workspace_bytes(const radic_batch_plan* plan);
 

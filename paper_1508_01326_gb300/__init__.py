@@ -20,6 +20,7 @@ from .api import (  # noqa: F401
     radic_det,
     radic_plan_info,
     prefix_plan_host,
+    batch_tasks_host,
     radic_primes,
     radic_status_string,
     radic_terms,

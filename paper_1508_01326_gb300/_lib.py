@@ -103,6 +103,7 @@ def _declare_optional(L: ctypes.CDLL) -> None:
         "radic_plan_info": ([i32, i32, i32, ctypes.POINTER(RadicOptions), ctypes.POINTER(i64), i32], i32),
         "radic_prefix_plan_host": ([i32, i32, i32, ctypes.POINTER(RadicOptions), i32, i32, ctypes.POINTER(i64), i32],
                                    i32),
+        "radic_batch_plan_tasks_host": ([vp, vp, vp, i32, i32, vp, ctypes.POINTER(i64), i64, ctypes.POINTER(i64)], i32),
         "radic_batch_workspace_bytes": ([vp], sz),
         "radic_batch_upload": ([vp, vp, sz, vp], i32),
         "radic_det_batched": ([vp, vp, i32, vp, vp, sz, vp], i32),

@@ -217,6 +217,32 @@ def make_tuning(kind=None, task_cost=None, tol=0.0, growth_threshold=0.0, blocks
     return t
 
 
+BATCH_TASK_KEYS = ["b", "tier", "kind", "shared", "group", "r0", "run", "lim"]
+
+
+def batch_tasks_host(shapes, mode="mixed", tuning=None) -> list:
+    """The tasks radic_batch_plan_create would make for these shapes, planned on the host only
+    (radic_batch_plan_tasks_host): one dict per task with BATCH_TASK_KEYS, in task order."""
+    shapes = [(int(m), int(n)) for m, n in shapes]
+    batch = len(shapes)
+    ms = (ctypes.c_int32 * batch)(*[m for m, _ in shapes])
+    ns = (ctypes.c_int32 * batch)(*[n for _, n in shapes])
+    offs, acc = [], 0
+    for m, n in shapes:
+        offs.append(acc)
+        acc += m * n
+    off = (ctypes.c_int64 * batch)(*offs)
+    tun = ctypes.byref(tuning) if tuning is not None else None
+    lib = L.lib()
+    total = ctypes.c_int64(0)
+    L.check("radic_batch_plan_tasks_host",
+            lib.radic_batch_plan_tasks_host(ms, ns, off, batch, _mode(mode), tun, None, 0, ctypes.byref(total)))
+    buf = (ctypes.c_int64 * (8 * max(total.value, 1)))()
+    L.check("radic_batch_plan_tasks_host",
+            lib.radic_batch_plan_tasks_host(ms, ns, off, batch, _mode(mode), tun, buf, total.value, ctypes.byref(total)))
+    return [dict(zip(BATCH_TASK_KEYS, [int(x) for x in buf[8 * i:8 * i + 8]])) for i in range(total.value)]
+
+
 class BatchPlan:
     """A plan for a batch of matrices (shapes and packing fixed), with its workspace.
 

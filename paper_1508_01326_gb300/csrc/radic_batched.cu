@@ -223,15 +223,11 @@ int enqueue(const radic_batch_plan* pl, const void* A, int dtype, radic_result* 
 
 }  // namespace
 
-extern "C" {
-
-int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* offsets, int batch, int mode,
-                            const radic_batch_tuning* tuning, radic_batch_plan** plan) {
-  if (!plan || batch < 1 || !m || !n || !offsets) return RADIC_EINVAL;
-  if (mode != RADIC_MODE_FP64 && mode != RADIC_MODE_MIXED) return RADIC_EUNSUPPORTED;
-  *plan = nullptr;
-  radic_batch_plan* pl = new (std::nothrow) radic_batch_plan;
-  if (!pl) return RADIC_EINVAL;
+namespace {
+// Host part of the plan: routing of every matrix to a tier, its tasks, and
+// their order.  Returns a RADIC_* code; `pl` is filled on success.
+int plan_tasks(radic_batch_plan* pl, const int32_t* m, const int32_t* n, const int64_t* offsets, int batch, int mode,
+               const radic_batch_tuning* tuning) {
   pl->batch = batch;
   pl->mode = mode;
   if (tuning && tuning->tol > 0.0) pl->tol = tuning->tol;
@@ -241,10 +237,8 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
   pl->offset.resize(batch);
   pl->tier.resize(batch);
   for (int b = 0; b < batch; ++b) {
-    if (m[b] < 1 || n[b] < 1 || m[b] > kBatchMaxM || n[b] > kMaxN || offsets[b] < 0) {
-      delete pl;
+    if (m[b] < 1 || n[b] < 1 || m[b] > kBatchMaxM || n[b] > kMaxN || offsets[b] < 0)
       return m[b] > kBatchMaxM && m[b] <= kMaxM ? RADIC_EUNSUPPORTED : RADIC_EINVAL;
-    }
     pl->shape[2 * b] = m[b];
     pl->shape[2 * b + 1] = n[b];
     pl->offset[b] = offsets[b];
@@ -299,6 +293,27 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
     pl->pair32[m] = i;
   }
   for (const BatchTask& t : pl->t32) pl->tasks_pair += (t.tier == kModePair);
+  return RADIC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+
+int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* offsets, int batch, int mode,
+                            const radic_batch_tuning* tuning, radic_batch_plan** plan) {
+  if (!plan || batch < 1 || !m || !n || !offsets) return RADIC_EINVAL;
+  if (mode != RADIC_MODE_FP64 && mode != RADIC_MODE_MIXED) return RADIC_EUNSUPPORTED;
+  *plan = nullptr;
+  radic_batch_plan* pl = new (std::nothrow) radic_batch_plan;
+  if (!pl) return RADIC_EINVAL;
+  {
+    const int rc = plan_tasks(pl, m, n, offsets, batch, mode, tuning);
+    if (rc != RADIC_OK) {
+      delete pl;
+      return rc;
+    }
+  }
   // per-matrix task lists in task order (fixed summation order)
   std::vector<std::vector<int>> per(batch);
   for (size_t i = 0; i < pl->t32.size(); ++i) per[pl->t32[i].b].push_back((int)i);
@@ -393,6 +408,34 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
   pl->off_shape = take((size_t)2 * batch * sizeof(int));
   pl->ws_bytes = off;
   *plan = pl;
+  return RADIC_OK;
+}
+
+int radic_batch_plan_tasks_host(const int32_t* m, const int32_t* n, const int64_t* offsets, int batch, int mode,
+                                const radic_batch_tuning* tuning, int64_t* tasks, int64_t capacity,
+                                int64_t* n_tasks) {
+  if (batch < 1 || !m || !n || !offsets || !n_tasks || capacity < 0 || (capacity > 0 && !tasks)) return RADIC_EINVAL;
+  if (mode != RADIC_MODE_FP64 && mode != RADIC_MODE_MIXED) return RADIC_EUNSUPPORTED;
+  radic_batch_plan pl;
+  const int rc = plan_tasks(&pl, m, n, offsets, batch, mode, tuning);
+  if (rc != RADIC_OK) return rc;
+  *n_tasks = (int64_t)(pl.t32.size() + pl.t64.size());
+  int64_t i = 0;
+  for (const std::vector<BatchTask>* list : {&pl.t32, &pl.t64}) {
+    for (const BatchTask& t : *list) {
+      if (i >= capacity) return RADIC_OK;
+      int64_t* r = tasks + 8 * i;
+      r[0] = t.b;
+      r[1] = t.tier;
+      r[2] = t.kind;
+      r[3] = t.shared;
+      r[4] = t.v;
+      r[5] = (int64_t)t.r0;
+      r[6] = (int64_t)t.run;
+      r[7] = (int64_t)t.lim;
+      ++i;
+    }
+  }
   return RADIC_OK;
 }
 

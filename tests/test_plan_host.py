@@ -79,3 +79,103 @@ def test_prefix_plan_options():
     # depth 3 needs a prefix of at least one column
     with pytest.raises(R.RadicError):
         R.prefix_plan_host(3, 10, "mixed", options=dict(prefix_depth=3))
+
+
+# ---------------------------------------------------------------------------
+# Batched path: routing and the split of every matrix's ranks into tasks
+# ---------------------------------------------------------------------------
+
+
+def _check_batch_tasks(tasks, shapes):
+    from collections import defaultdict
+
+    by_b = defaultdict(list)
+    for t in tasks:
+        by_b[t["b"]].append(t)
+    for b, (m, n) in enumerate(shapes):
+        ts = by_b.get(b, [])
+        if m > n:
+            assert not ts  # det_R = 0 with no minors
+            continue
+        kinds = {(t["tier"], t["kind"], t["shared"]) for t in ts}
+        assert len(kinds) == 1, (b, kinds)
+        _, kind, shared = kinds.pop()
+        groups = defaultdict(list)
+        for t in ts:
+            groups[t["group"]].append(t)
+        total = 0
+        for g, gl in groups.items():
+            lim = gl[0]["lim"]
+            assert all(t["lim"] == lim for t in gl)
+            # 32 lanes per task, lane l takes [r0 + l*run, r0 + (l+1)*run) clipped at lim:
+            # the tasks of a group tile [0, lim) without gaps or overlaps
+            pos = 0
+            for lo, hi in sorted((t["r0"], min(t["r0"] + 32 * t["run"], lim)) for t in gl):
+                assert lo == pos and hi > lo, (b, g)
+                pos = hi
+            assert pos == lim
+            if kind == 0:
+                assert lim == math.comb(n, m)
+                total += lim
+            elif shared:
+                H = m - kind - 1
+                assert lim == math.comb(g, H - 1)
+                total += lim * sum(math.comb(n - 1 - v, kind) for v in range(g + 1, n - kind))
+            else:
+                P = m - kind
+                assert lim == math.comb(g, P - 1)
+                total += lim * math.comb(n - 1 - g, kind)
+        assert total == math.comb(n, m), (b, m, n)
+
+
+def _expected_tier(m, n, tol):
+    # the router's rule: binary32 when 2.5e-6 / sqrt(C) meets tol, pairs (m >= 3)
+    # when 1e-11 / sqrt(C) does, binary64 otherwise
+    c = math.comb(n, m)
+    if 2.5e-6 / math.sqrt(c) <= tol:
+        return 1
+    if m >= 3 and 1e-11 / math.sqrt(c) <= tol:
+        return 3
+    return 0
+
+
+@pytest.mark.parametrize("tol", [1e-10, 1e-8, 1e-4])
+def test_batch_tasks_cover_every_minor_once(tol):
+    from paper_1508_01326_gb300 import workloads as W
+
+    shapes = [x.shape for x in W.batched_4096()[::4]] + [(4, 3), (1, 7), (2, 2), (10, 30), (9, 29)]
+    tasks = R.batch_tasks_host(shapes, mode="mixed", tuning=R.make_tuning(tol=tol))
+    _check_batch_tasks(tasks, shapes)
+    tiers = {t["b"]: t["tier"] for t in tasks}
+    for b, (m, n) in enumerate(shapes):
+        if m <= n:
+            assert tiers[b] == _expected_tier(m, n, tol), (m, n)
+    # low-tier tasks come first (binary32 then pairs for each m), binary64 after
+    split = [t["tier"] for t in tasks]
+    first64 = split.index(0) if 0 in split else len(split)
+    assert all(x != 0 for x in split[:first64]) and all(x == 0 for x in split[first64:])
+
+
+def test_batch_tasks_binary64_mode_and_options():
+    shapes = [(m, n) for m in range(1, 11) for n in range(m, m + 14, 3)]
+    plain = R.batch_tasks_host(shapes, mode="fp64")
+    _check_batch_tasks(plain, shapes)
+    assert {t["tier"] for t in plain} == {0}
+    # head sharing on (m - D - 1 >= 5) and off
+    on = R.batch_tasks_host(shapes, mode="fp64", tuning=R.make_tuning())
+    off = R.batch_tasks_host(shapes, mode="fp64", tuning=R.make_tuning(head_sharing=False))
+    assert any(t["shared"] for t in on) and not any(t["shared"] for t in off)
+    _check_batch_tasks(on, shapes)
+    _check_batch_tasks(off, shapes)
+    # per-m depth and per-minor overrides
+    forced = R.batch_tasks_host(shapes, mode="mixed",
+                                tuning=R.make_tuning(prefix_depth={6: 2, 9: 3}, kind={4: "thread"}, tol=1e-4))
+    _check_batch_tasks(forced, shapes)
+    for t in forced:
+        m = shapes[t["b"]][0]
+        if m == 6:
+            assert t["kind"] == 2
+        if m == 9:
+            assert t["kind"] == 3
+        if m == 4 and t["tier"] == 1:
+            assert t["kind"] == 0
