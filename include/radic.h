@@ -394,7 +394,9 @@ int radic_det_backward_mode(const double* A, int batch, int m, int n, int64_t ld
  * device looks up that array's device address (cudaGetSymbolAddress, with
  * that device current) and caches it; make that first call before any
  * stream capture.  The call itself allocates nothing: no cudaMalloc,
- * cudaFree or allocating library routine.
+ * cudaFree or allocating library routine.  The cached address lives as long
+ * as the device's primary context: after cudaDeviceReset on a device, do not
+ * call radic_det_noalloc on that device again in the same process.
  *
  * All calls on one device share the array and it keeps the last call's
  * contents; each call clears the part that must start at zero.  Calls that

@@ -181,9 +181,13 @@ __device__ __forceinline__ bool sign_negative_dyn(const int (&c)[G], int m) {
 }
 
 // ---------------------------------------------------------------------------
-// Reciprocals.  Hardware approximation refined by Newton-Raphson iterations
-// x <- x + x (1 - d x) (quadratic convergence); a zero pivot gives 0 so that
-// the elimination of an all-zero column stays finite.
+// Reciprocals; a zero pivot gives 0 so that the elimination of an all-zero
+// column stays finite.  Binary64: the hardware approximation refined by two
+// Newton-Raphson iterations x <- x + x (1 - d x) (quadratic convergence).
+// Binary32: the hardware approximation alone, not refined (the PTX ISA
+// states at most one unit in the last place for rcp.approx.f32); the error
+// bounds of the binary32 path count a multiplier formed with it as three
+// binary32 roundings.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float rcp_f32(float d) {
   float r;

@@ -3,7 +3,10 @@
 // that cannot allocate device memory when they need a determinant (device
 // memory owned by another allocator or a fixed pool, or loops that cannot
 // take an allocation's synchronisation).  The array is looked up once per
-// device and cached; calls on one device share it and must not overlap.
+// device and cached; calls on one device share it and must not overlap.  A
+// cudaDeviceReset (or any teardown of the device's primary context) unloads
+// the module that holds the array, so the cached address is then stale: a
+// process that resets a device must not call radic_det_noalloc on it again.
 #include <mutex>
 
 #include "radic_internal.h"
@@ -43,8 +46,10 @@ extern "C" int radic_det_noalloc(const void* A, int m, int n, int64_t lda, int d
                                  radic_result* out, void* stream) {
   if (!A || !out || lda < n) return RADIC_EINVAL;
   if (m >= 1 && n >= 1 && m <= n) {
+    // A plan that cannot be made (size 0) falls through to radic_det, which
+    // reports the planning error (RADIC_EUNSUPPORTED, RADIC_ECUDA, ...)
+    // before it touches the scratch array.
     const size_t need = radic_workspace_bytes(m, n, RADIC_MODE_FP64, opts);
-    if (need == 0) return RADIC_EINVAL;
     if (need > RADIC_NOALLOC_SCRATCH_BYTES) return RADIC_EWORKSPACE;
   }
   void* scratch = nullptr;

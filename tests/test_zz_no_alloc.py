@@ -44,19 +44,42 @@ def _noalloc(lib, a, opts=None):
     return rc, out
 
 
+def _oracle(host):
+    """Exact det_R and sum|terms| of a workload matrix from the oracle (stored values for 8 x 32)."""
+    import oracle.radic_oracle as orc
+    from tests.conftest import golden_abs_sums, golden_values
+
+    if host.shape == (8, 32):
+        return golden_values("fp64_8x32")[0], golden_abs_sums("fp64_8x32")[0]
+    val, abs_sum = orc.radic_det_exact(host)
+    return float(val), float(abs_sum)
+
+
 def test_noalloc_matches_radic_det_on_two_calls_in_a_row(lib):
     import paper_1508_01326_gb300 as R
+    from paper_1508_01326_gb300 import _lib as L
 
     mats = [W.uniform_matrix(41, 6, 20), W.fp64_8x32(), W.uniform_matrix(41, 6, 20)]
     for host in mats:
+        want, scale = _oracle(host)
         a = torch.from_numpy(np.ascontiguousarray(host)).cuda()
         ref = R.parse_result(R.radic_det(a, mode="fp64"))
         rc, out = _noalloc(lib, a)
         assert rc == 0
         got = R.parse_result(out)
         assert got["status"] == 0 and got["minors"] == ref["minors"]
-        assert abs(got["value"] - ref["value"]) <= 1e-12 * ref["abs_sum"]
-        assert abs(got["abs_sum"] - ref["abs_sum"]) <= 1e-12 * ref["abs_sum"]
+        # against the existing entry point, and against the oracle's exact value
+        assert abs(got["value"] - ref["value"]) <= 1e-12 * scale
+        assert abs(got["abs_sum"] - scale) <= 1e-12 * scale
+        assert abs(got["value"] - want) <= 1e-12 * scale
+        # with a fixed task schedule both entry points run the same kernels on
+        # the same data: identical bits
+        det_opts = L.make_options(deterministic=1)
+        ref_fixed = R.parse_result(R.radic_det(a, mode="fp64", options=dict(deterministic=True)))
+        rc, out = _noalloc(lib, a, det_opts)
+        assert rc == 0
+        fixed = R.parse_result(out)
+        assert (fixed["value"], fixed["abs_sum"]) == (ref_fixed["value"], ref_fixed["abs_sum"])
 
 
 def test_noalloc_rejects_plans_beyond_its_scratch(lib):
