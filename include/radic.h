@@ -126,7 +126,7 @@ typedef struct radic_options {
                                the next from a counter, which evens out the
                                warps' work; which warp sums which prefixes then
                                varies, so repeated calls can differ in the last
-                               bits of value and abs_sum (far below err_est).
+                               bits of value and abs_sum (far below err_bound).
                                1 = every warp takes a fixed share of the
                                tasks: repeated calls give identical bits.
                                The exact mode is exact either way. */
@@ -138,7 +138,15 @@ typedef struct radic_options {
 typedef struct radic_result {
   double value;     /* det_R(A) rounded to binary64 (EXACT: from exact value)  */
   double abs_sum;   /* sum over J of |det(A[:, J])| in the mode's arithmetic   */
-  double err_est;   /* a-priori error estimate m * u * abs_sum (not a bound)   */
+  double err_bound; /* floating-point modes: an upper bound on
+                       |value - det_R(A)| for A as given (before the final
+                       rounding of value to binary64 it also covers), from
+                       running error analysis of the eliminations actually
+                       performed (first order, safeguarded: every pivot's
+                       radius below 2^-12 of its magnitude, else the
+                       minor is redone in binary64 or bounded by Hadamard's
+                       inequality) and of the summations; +inf or NaN when
+                       no bound could be formed.  EXACT: 0.               */
   int64_t exact_lo; /* EXACT: low 64 bits of det_R(A), two's complement int128 */
   int64_t exact_hi; /* EXACT: high 64 bits                                     */
   int64_t minors;   /* C(n, m), or 0 when m > n                                */
@@ -274,6 +282,11 @@ typedef struct radic_batch_tuning {
                               head (first m-D-1 columns) once for all its
                               prefixes (0: on, -1: off)                      */
   int32_t reserved[5];
+  void* kernel_events;     /* optional: two cudaEvent_t recorded on the call's
+                              stream right before and right after the launch
+                              of the plan's dominant kernel, the low-tier
+                              kernel with the most estimated work (profiling
+                              hook; see radic_batch_plan_info [12..14])       */
 } radic_batch_tuning;
 
 /* Builds the plan of `batch` matrices: matrix b is m[b] x n[b], row-major
@@ -321,9 +334,13 @@ size_t radic_batch_workspace_bytes(const radic_batch_plan* plan);
  * [2] matrices binary32, [3] matrices binary64, [4] minors binary32,
  * [5] minors binary64, [6] largest persistent grid binary32, [7] same for
  * binary64, [8] tasks pairs, [9] matrices pairs, [10] minors pairs,
- * [11] largest persistent grid pairs.  RADIC_EINVAL on a null pointer or a
- * count outside 0..RADIC_BATCH_INFO_COUNT. */
-#define RADIC_BATCH_INFO_COUNT 12
+ * [11] largest persistent grid pairs, [12] kernel launches per call,
+ * [13] m and [14] task path of the dominant kernel (0 per minor, 1 prefix
+ * depth 2, 2 prefix depth 3, 3 and 4 the same with head sharing) and [15]
+ * its tier (RADIC_MODE_MIXED for binary32, RADIC_MODE_PAIR, or -1 when the
+ * plan has no low-tier work).  RADIC_EINVAL on a null pointer or a count
+ * outside 0..RADIC_BATCH_INFO_COUNT. */
+#define RADIC_BATCH_INFO_COUNT 16
 int radic_batch_plan_info(const radic_batch_plan* plan, int64_t* info, int count);
 
 /* Copies the plan's task tables into `workspace` (once per workspace, before

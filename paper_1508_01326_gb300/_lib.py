@@ -50,6 +50,7 @@ class RadicBatchTuning(ctypes.Structure):
         ("tiers", ctypes.c_int32),
         ("head_sharing", ctypes.c_int32),
         ("reserved", ctypes.c_int32 * 5),
+        ("kernel_events", ctypes.c_void_p),
     ]
 
 _lib = None

@@ -153,7 +153,7 @@ def parse_result(buf: torch.Tensor) -> dict:
     return {
         "value": float(f[0]),
         "abs_sum": float(f[1]),
-        "err_est": float(f[2]),
+        "err_bound": float(f[2]),
         "exact": exact,
         "minors": int(w[5]),
         "flagged": int(w[6]),
@@ -191,13 +191,15 @@ TIERS = {"fp32": 1, "pair": 2}
 
 
 def make_tuning(kind=None, task_cost=None, tol=0.0, growth_threshold=0.0, blocks_per_sm=0,
-                prefix_depth=None, tiers=None, head_sharing=True) -> "L.RadicBatchTuning":
+                prefix_depth=None, tiers=None, head_sharing=True, kernel_events=0) -> "L.RadicBatchTuning":
     """Batched-path tuning: `kind`, `task_cost` and `prefix_depth` map m to a mapping name, a task size
     and a prefix depth (2 or 3); `tiers` lists the low tiers the mixed router may use ("fp32",
     "pair"; default both; binary64 is always available); `head_sharing` factors each prefix head
-    once for all its prefixes."""
+    once for all its prefixes; `kernel_events` is the address of two cudaEvent_t recorded around
+    the dominant kernel."""
     t = L.RadicBatchTuning()
     t.head_sharing = 0 if head_sharing else -1
+    t.kernel_events = kernel_events or None
     if tiers is not None:
         mask = 0
         for name in tiers:
@@ -277,7 +279,8 @@ class BatchPlan:
         self._graphs = []
 
     INFO_KEYS = ["tasks_fp32", "tasks_fp64", "matrices_fp32", "matrices_fp64", "minors_fp32", "minors_fp64",
-                 "blocks_fp32", "blocks_fp64", "tasks_pair", "matrices_pair", "minors_pair", "blocks_pair"]
+                 "blocks_fp32", "blocks_fp64", "tasks_pair", "matrices_pair", "minors_pair", "blocks_pair",
+                 "launches", "dominant_m", "dominant_path", "dominant_tier"]
 
     def info(self) -> dict:
         buf = (ctypes.c_int64 * len(self.INFO_KEYS))()

@@ -79,7 +79,7 @@ def autotune(mats: List[np.ndarray], mode: str = "mixed", tol: float = 1e-10, dt
     """Returns (tuning struct, table {m: {"kind", "depth", "task_cost", "ms"}}) for this batch."""
     path = path or cache_path()
     dev = torch.cuda.get_device_name()
-    key = f"{dev}|{mode}|{tol:g}|{np.dtype(dtype).name}|v2"
+    key = f"{dev}|{mode}|{tol:g}|{np.dtype(dtype).name}|v3"
     cache = _load(path)
     table: Dict[str, dict] = dict(cache.get(key, {}))
     by_m: Dict[int, List[np.ndarray]] = {}
@@ -89,12 +89,9 @@ def autotune(mats: List[np.ndarray], mode: str = "mixed", tol: float = 1e-10, dt
     for m, group in sorted(by_m.items()):
         if str(m) in table and not force:
             continue
-        # is any matrix of this m routed to the binary32 tier?  (same rule as the plan)
-        import math
-
-        tier_fp32 = mode == "mixed" and any(
-            a.shape[0] <= a.shape[1] and 2.5e-6 / math.sqrt(math.comb(a.shape[1], a.shape[0])) <= tol
-            for a in group)
+        # is any matrix of this m routed to the binary32 tier?  (the plan's
+        # first-tier rule: binary32 when its bound envelope 1e-4 meets tol)
+        tier_fp32 = mode == "mixed" and tol >= 1e-4 and any(a.shape[0] <= a.shape[1] for a in group)
         best = None
         for kind, depth, cost in candidates(m, tier_fp32, costs):
             tun = api.make_tuning(kind={m: kind}, task_cost={m: cost}, prefix_depth={m: depth}, tol=tol)

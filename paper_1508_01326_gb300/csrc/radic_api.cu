@@ -279,7 +279,7 @@ void layout_workspace(SinglePlan& pl) {
 __global__ void k_zero_result(radic_result* out, int tier) {
   out->value = 0.0;
   out->abs_sum = 0.0;
-  out->err_est = 0.0;
+  out->err_bound = 0.0;
   out->exact_lo = 0;
   out->exact_hi = 0;
   out->minors = 0;

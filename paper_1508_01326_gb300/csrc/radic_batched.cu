@@ -26,21 +26,27 @@ struct radic_batch_plan {
   std::vector<int> shape;            // m, n per matrix
   std::vector<long long> offset;
   std::vector<int> tier;
-  std::vector<BatchTask> t32, t64;   // t32: binary32 and pair tasks; sorted by m, tier, cost (largest first)
-  int begin32[kBatchMaxM + 2] = {0}, begin64[kBatchMaxM + 2] = {0};  // task ranges per m
-  int pair32[kBatchMaxM + 1] = {0};  // first pair task of m in t32 (binary32 tasks of m before it)
+  // t32: binary32 and pair tasks, t64: binary64 tasks; both sorted by group
+  // (m, task path), then tier (binary32 before pairs), then cost (largest first)
+  std::vector<BatchTask> t32, t64;
+  int g32[kGroups + 1] = {0}, g64[kGroups + 1] = {0};  // task ranges per group
+  int gpair[kGroups] = {0};  // first pair task of the group in t32 (binary32 tasks before it)
   std::vector<int> csr_ptr, csr_idx;
   int max_n = 1, max_m = 1;
-  int blocks32[kBatchMaxM + 1] = {0}, blocks64[kBatchMaxM + 1] = {0}, blocksp[kBatchMaxM + 1] = {0};
+  // persistent grid of each group's kernel per queue (0 binary32, 1 pairs, 2 binary64)
+  int blocks[3][kGroups] = {{0}};
   int slice32[kBatchMaxM + 1] = {0}, slice64[kBatchMaxM + 1] = {0}, slicep[kBatchMaxM + 1] = {0};  // per warp
   double tol = 1e-10, growth = 64.0;
   int tiers = 3;  // allowed low tiers: bit 0 binary32, bit 1 pairs
   // workspace layout
   size_t off_t32 = 0, off_t64 = 0, off_slots = 0, off_flagged = 0, off_escale = 0, off_csr_ptr = 0,
-         off_csr_idx = 0, off_tier = 0, off_shape = 0, ws_bytes = 0;
+         off_csr_idx = 0, off_tier = 0, off_shape = 0, off_rerouted = 0, ws_bytes = 0;
   long long n_fp32_matrices = 0, n_fp64_matrices = 0, n_pair_matrices = 0;
   unsigned long long minors32 = 0, minors64 = 0, minors_pair = 0;
   int tasks_pair = 0;
+  int launches = 0;                      // kernel launches per call
+  int dom_queue = -1, dom_group = -1;    // the low-tier kernel with the most estimated work
+  void* events = nullptr;                // optional cudaEvent_t[2] around it
 };
 
 struct radic_batch_graph {
@@ -150,13 +156,23 @@ int persistent_blocks(const void* k, int slice_bytes, int sms) {
   return nb * sms;
 }
 
+const void* group_kernel(int queue, int g) {
+  const int m = g / kPaths, path = g % kPaths;
+  return queue == 0 ? batch_kernel_f32(m, path) : queue == 1 ? batch_kernel_pair(m, path) : batch_kernel_f64(m, path);
+}
+
 int enqueue(const radic_batch_plan* pl, const void* A, int dtype, radic_result* out, void* workspace, cudaStream_t s) {
   unsigned char* ws = static_cast<unsigned char*>(workspace);
-  if (cudaMemsetAsync(ws, 0, 256, s) != cudaSuccess) return RADIC_ECUDA;
+  if (cudaMemsetAsync(ws, 0, kBatchHeaderBytes, s) != cudaSuccess) return RADIC_ECUDA;
+  if (cudaMemsetAsync(ws + pl->off_rerouted, 0, (size_t)pl->batch * sizeof(int), s) != cudaSuccess)
+    return RADIC_ECUDA;
   BatchArgs a;
   std::memset(&a, 0, sizeof(a));
   a.A = A;
   a.dtype = dtype;
+  a.tol = pl->tol;
+  for (int g = 0; g < kGroups; ++g) a.flag_base_g[g] = pl->g32[g];
+  a.rerouted = reinterpret_cast<int*>(ws + pl->off_rerouted);
   a.n_tasks32 = (int)pl->t32.size();
   a.tasks32 = reinterpret_cast<const BatchTask*>(ws + pl->off_t32);
   a.tasks64 = reinterpret_cast<const BatchTask*>(ws + pl->off_t64);
@@ -165,56 +181,67 @@ int enqueue(const radic_batch_plan* pl, const void* A, int dtype, radic_result* 
   a.escale = reinterpret_cast<int*>(ws + pl->off_escale);
   a.hdr = reinterpret_cast<BatchHeader*>(ws);
   a.growth = pl->growth;
-  // binary32 and pair tiers, one persistent kernel per tier and m present
-  for (int m = 1; m <= kBatchMaxM; ++m) {
-    a.flag_base = pl->begin32[m];
-    a.begin64 = pl->begin64[m];
-    a.end64 = pl->begin64[m + 1];
-    a.begin32 = pl->begin32[m];
-    a.end32 = pl->pair32[m];
-    if (a.end32 > a.begin32) {
-      a.slice_bytes = pl->slice32[m];
-      void* params[] = {&a};
-      if (cudaLaunchKernel(batch_kernel_f32(m), dim3(pl->blocks32[m]), dim3(kBatchThreads), params,
-                           (size_t)pl->slice32[m] * (kBatchThreads / 32), s) != cudaSuccess)
-        return RADIC_ECUDA;
-    }
-    a.begin32 = pl->pair32[m];
-    a.end32 = pl->begin32[m + 1];
-    if (a.end32 > a.begin32) {
-      a.slice_bytes = pl->slicep[m];
-      void* params[] = {&a};
-      if (cudaLaunchKernel(batch_kernel_pair(m), dim3(pl->blocksp[m]), dim3(kBatchThreads), params,
-                           (size_t)pl->slicep[m] * (kBatchThreads / 32), s) != cudaSuccess)
-        return RADIC_ECUDA;
-    }
-  }
-  // binary64 tier (and the flagged binary32 and pair tasks), one kernel per m present
-  for (int m = 1; m <= kBatchMaxM; ++m) {
-    a.flag_base = pl->begin32[m];
-    a.begin32 = pl->begin32[m];
-    a.end32 = pl->begin32[m + 1];
-    a.begin64 = pl->begin64[m];
-    a.end64 = pl->begin64[m + 1];
-    if (a.end64 > a.begin64 || a.end32 > a.begin32) {
-      a.slice_bytes = pl->slice64[m];
-      void* params[] = {&a};
-      if (cudaLaunchKernel(batch_kernel_f64(m), dim3(pl->blocks64[m]), dim3(kBatchThreads), params,
-                           (size_t)pl->slice64[m] * (kBatchThreads / 32), s) != cudaSuccess)
-        return RADIC_ECUDA;
-    }
+  cudaEvent_t* ev = static_cast<cudaEvent_t*>(pl->events);
+  // inside a stream capture the events become event-record nodes of the graph
+  // (recorded at every replay) only with the external flag
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (ev && cudaStreamIsCapturing(s, &cap) != cudaSuccess) return RADIC_ECUDA;
+  const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  auto launch = [&](int queue, int g, int slice) {
+    a.group = g;
+    a.queue = queue;
+    a.slice_bytes = slice;
+    void* params[] = {&a};
+    const bool dom = ev && queue == pl->dom_queue && g == pl->dom_group;
+    if (dom && cudaEventRecordWithFlags(ev[0], s, ev_flags) != cudaSuccess) return false;
+    if (cudaLaunchKernel(group_kernel(queue, g), dim3(pl->blocks[queue][g]), dim3(kBatchThreads), params,
+                         (size_t)slice * (kBatchThreads / 32), s) != cudaSuccess)
+      return false;
+    return !dom || cudaEventRecordWithFlags(ev[1], s, ev_flags) == cudaSuccess;
+  };
+  // binary32 and pair tiers, one persistent kernel per tier and group present
+  for (int g = 0; g < kGroups; ++g) {
+    const int m = g / kPaths;
+    a.flag_base = pl->g32[g];
+    a.begin64 = pl->g64[g];
+    a.end64 = pl->g64[g + 1];
+    a.begin32 = pl->g32[g];
+    a.end32 = pl->gpair[g];
+    if (a.end32 > a.begin32 && !launch(0, g, pl->slice32[m])) return RADIC_ECUDA;
+    a.begin32 = pl->gpair[g];
+    a.end32 = pl->g32[g + 1];
+    if (a.end32 > a.begin32 && !launch(1, g, pl->slicep[m])) return RADIC_ECUDA;
   }
   ReduceArgs r;
   r.csr_ptr = reinterpret_cast<const int*>(ws + pl->off_csr_ptr);
   r.csr_idx = reinterpret_cast<const int*>(ws + pl->off_csr_idx);
   r.tier = reinterpret_cast<const int*>(ws + pl->off_tier);
+  r.rerouted = a.rerouted;
   r.shape = reinterpret_cast<const int*>(ws + pl->off_shape);
   r.slots = a.slots;
   r.escale = a.escale;
   r.out = out;
   r.batch = pl->batch;
-  void* rparams[] = {&r};
   const unsigned blocks = (unsigned)((pl->batch * 32 + 127) / 128);
+  // a-posteriori check of the low tiers: matrices whose error bound misses
+  // tol are redone by the binary64 kernels below
+  if (!pl->t32.empty()) {
+    void* cparams[] = {&a, &r};
+    if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_batch_check), dim3(blocks > 0 ? blocks : 1), dim3(128),
+                         cparams, 0, s) != cudaSuccess)
+      return RADIC_ECUDA;
+  }
+  // binary64 tier (and the flagged or rerouted binary32 and pair tasks), one
+  // kernel per group present
+  for (int g = 0; g < kGroups; ++g) {
+    a.flag_base = pl->g32[g];
+    a.begin32 = pl->g32[g];
+    a.end32 = pl->g32[g + 1];
+    a.begin64 = pl->g64[g];
+    a.end64 = pl->g64[g + 1];
+    if ((a.end64 > a.begin64 || a.end32 > a.begin32) && !launch(2, g, pl->slice64[g / kPaths])) return RADIC_ECUDA;
+  }
+  void* rparams[] = {&r};
   if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_batch_reduce), dim3(blocks > 0 ? blocks : 1), dim3(128),
                        rparams, 0, s) != cudaSuccess)
     return RADIC_ECUDA;
@@ -245,17 +272,16 @@ int plan_tasks(radic_batch_plan* pl, const int32_t* m, const int32_t* n, const i
     pl->max_n = std::max(pl->max_n, (int)n[b]);
     pl->max_m = std::max(pl->max_m, (int)m[b]);
     const unsigned long long c = (m[b] <= n[b]) ? binom_host(n[b], m[b]) : 0ull;
-    // Routing: elimination errors behave like independent rounding per
-    // minor, so the error relative to sum|terms| falls like K / sqrt(C(n,m)).
-    // Over 4096 random N(0,1) matrices (m 2..10, n-m 1..20) K stayed below
-    // 2.1e-6 for binary32 elimination (median 1.2e-7); a matrix goes to the
-    // binary32 tier only when K = 2.5e-6 meets the target, else to pairs
-    // when K = 1e-11 does, else to binary64.
+    // Routing: the first tier of a matrix is the cheapest whose error bound
+    // relative to sum|terms| usually meets the target: binary32 elimination
+    // when kBinary32BoundK <= tol, else pairs (m >= 3) when kPairBoundK <=
+    // tol, else binary64.  The constants are envelopes of the bounds measured
+    // on random matrices; the device then checks every matrix's own bound
+    // (k_batch_check) and redoes in binary64 those that miss tol.
     int tier = kModeFp64;
     if (mode == RADIC_MODE_MIXED && c > 0) {
-      const double rs = 1.0 / std::sqrt((double)c);
-      if ((pl->tiers & 1) && kBinary32ErrorK * rs <= pl->tol) tier = kModeMixed;
-      else if ((pl->tiers & 2) && m[b] >= 3 && kPairErrorK * rs <= pl->tol) tier = kModePair;
+      if ((pl->tiers & 1) && kBinary32BoundK <= pl->tol) tier = kModeMixed;
+      else if ((pl->tiers & 2) && m[b] >= 3 && kPairBoundK <= pl->tol) tier = kModePair;
     }
     pl->tier[b] = tier;
     if (tier == kModeMixed) {
@@ -270,27 +296,28 @@ int plan_tasks(radic_batch_plan* pl, const int32_t* m, const int32_t* n, const i
     }
     make_tasks(*pl, b, tier, tuning);
   }
-  // per m and tier (binary32 before pairs), largest tasks first
-  // (longest-processing-time order for each queue)
-  auto order = [](const BatchTask& x, const BatchTask& y) {
-    if (x.m != y.m) return x.m < y.m;
+  // per group (m, task path) and tier (binary32 before pairs), largest tasks
+  // first (longest-processing-time order for each queue)
+  auto gid = [](const BatchTask& t) { return group_of(t.m, path_of(t.kind, t.shared)); };
+  auto order = [&](const BatchTask& x, const BatchTask& y) {
+    if (gid(x) != gid(y)) return gid(x) < gid(y);
     if (x.tier != y.tier) return x.tier == kModeMixed;
     return task_cost(x) > task_cost(y);
   };
   std::stable_sort(pl->t32.begin(), pl->t32.end(), order);
   std::stable_sort(pl->t64.begin(), pl->t64.end(), order);
-  for (int m = 0; m <= kBatchMaxM + 1; ++m) {
-    pl->begin32[m] = (int)(std::lower_bound(pl->t32.begin(), pl->t32.end(), m,
-                                            [](const BatchTask& t, int mm) { return t.m < mm; }) -
-                           pl->t32.begin());
-    pl->begin64[m] = (int)(std::lower_bound(pl->t64.begin(), pl->t64.end(), m,
-                                            [](const BatchTask& t, int mm) { return t.m < mm; }) -
-                           pl->t64.begin());
+  for (int g = 0; g <= kGroups; ++g) {
+    pl->g32[g] = (int)(std::lower_bound(pl->t32.begin(), pl->t32.end(), g,
+                                        [&](const BatchTask& t, int gg) { return gid(t) < gg; }) -
+                       pl->t32.begin());
+    pl->g64[g] = (int)(std::lower_bound(pl->t64.begin(), pl->t64.end(), g,
+                                        [&](const BatchTask& t, int gg) { return gid(t) < gg; }) -
+                       pl->t64.begin());
   }
-  for (int m = 0; m <= kBatchMaxM; ++m) {
-    int i = pl->begin32[m];
-    while (i < pl->begin32[m + 1] && pl->t32[i].tier == kModeMixed) ++i;
-    pl->pair32[m] = i;
+  for (int g = 0; g < kGroups; ++g) {
+    int i = pl->g32[g];
+    while (i < pl->g32[g + 1] && pl->t32[i].tier == kModeMixed) ++i;
+    pl->gpair[g] = i;
   }
   for (const BatchTask& t : pl->t32) pl->tasks_pair += (t.tier == kModePair);
   return RADIC_OK;
@@ -341,18 +368,17 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
       n64[t.m] = std::max(n64[t.m], t.n);
       if (t.kind != kKindMinor) d64[t.m] = std::max(d64[t.m], t.kind);
     }
-    auto slice = [](int m, int n, int depth, int cs, int elem) {
-      size_t b = ((size_t)(n + 1) * (m + 1) * 8 + 15) / 16 * 16;
-      b += ((size_t)n * cs * elem + 31) / 32 * 32;
+    auto slice = [](int m, int n, int depth, int cs, int elem, bool dbl) {
+      size_t b = slice_bytes_before_zbuf(n, m, cs, elem, dbl);
       if (depth > 0) b += zbuf_bytes(n - m + depth, 32, depth, elem);
       return (int)align_up(b, 32);
     };
     for (int m = 1; m <= kBatchMaxM; ++m) {
       n64[m] = std::max(n64[m], std::max(n32[m], np[m]));
       d64[m] = std::max(d64[m], std::max(d32[m], dp[m]));
-      if (n32[m] > 0) pl->slice32[m] = slice(m, n32[m], d32[m], ((m + 3) / 4) * 4, 4);
-      if (np[m] > 0) pl->slicep[m] = slice(m, np[m], dp[m], ((m + 1) / 2) * 2, 8);
-      if (n64[m] > 0) pl->slice64[m] = slice(m, n64[m], d64[m], ((m + 1) / 2) * 2, 8);
+      if (n32[m] > 0) pl->slice32[m] = slice(m, n32[m], d32[m], ((m + 3) / 4) * 4, 4, false);
+      if (np[m] > 0) pl->slicep[m] = slice(m, np[m], dp[m], ((m + 1) / 2) * 2, 8, true);
+      if (n64[m] > 0) pl->slice64[m] = slice(m, n64[m], d64[m], ((m + 1) / 2) * 2, 8, false);
     }
   }
   const int sms = device_sm_count();
@@ -361,37 +387,46 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
     return RADIC_ECUDA;
   }
   const int occ = (tuning && tuning->blocks_per_sm > 0) ? tuning->blocks_per_sm : 0;
-  for (int m = 1; m <= kBatchMaxM; ++m) {
-    const bool has32 = pl->pair32[m] > pl->begin32[m];
-    const bool hasp = pl->begin32[m + 1] > pl->pair32[m];
-    const bool has64 = pl->begin64[m + 1] > pl->begin64[m] || has32 || hasp;
-    if (hasp) {
-      pl->blocksp[m] = persistent_blocks(batch_kernel_pair(m), pl->slicep[m], sms);
-      if (occ > 0) pl->blocksp[m] = std::min(pl->blocksp[m], occ * sms);
-      if (pl->blocksp[m] <= 0) {
-        delete pl;
-        return RADIC_EUNSUPPORTED;
-      }
-    }
-    if (has32) {
-      pl->blocks32[m] = persistent_blocks(batch_kernel_f32(m), pl->slice32[m], sms);
-      if (occ > 0) pl->blocks32[m] = std::min(pl->blocks32[m], occ * sms);
-      if (pl->blocks32[m] <= 0) {
-        delete pl;
-        return RADIC_EUNSUPPORTED;
-      }
-    }
-    if (has64) {
-      pl->blocks64[m] = persistent_blocks(batch_kernel_f64(m), pl->slice64[m], sms);
-      if (occ > 0) pl->blocks64[m] = std::min(pl->blocks64[m], occ * sms);
-      if (pl->blocks64[m] <= 0) {
+  for (int g = 0; g < kGroups; ++g) {
+    const int m = g / kPaths;
+    const bool has32 = pl->gpair[g] > pl->g32[g];
+    const bool hasp = pl->g32[g + 1] > pl->gpair[g];
+    const bool has64 = pl->g64[g + 1] > pl->g64[g] || has32 || hasp;
+    const bool need[3] = {has32, hasp, has64};
+    const int slice[3] = {pl->slice32[m], pl->slicep[m], pl->slice64[m]};
+    for (int q = 0; q < 3; ++q) {
+      if (!need[q]) continue;
+      pl->blocks[q][g] = persistent_blocks(group_kernel(q, g), slice[q], sms);
+      if (occ > 0) pl->blocks[q][g] = std::min(pl->blocks[q][g], occ * sms);
+      if (pl->blocks[q][g] <= 0) {
         delete pl;
         return RADIC_EUNSUPPORTED;
       }
     }
   }
+  // launches per call, and the dominant low-tier kernel (most estimated work)
+  {
+    double best = -1.0;
+    for (int g = 0; g < kGroups; ++g) {
+      const int ranges[2][2] = {{pl->g32[g], pl->gpair[g]}, {pl->gpair[g], pl->g32[g + 1]}};
+      for (int q = 0; q < 2; ++q) {
+        if (ranges[q][1] <= ranges[q][0]) continue;
+        ++pl->launches;
+        double c = 0.0;
+        for (int i = ranges[q][0]; i < ranges[q][1]; ++i) c += task_cost(pl->t32[i]);
+        if (c > best) {
+          best = c;
+          pl->dom_queue = q;
+          pl->dom_group = g;
+        }
+      }
+      if (pl->g64[g + 1] > pl->g64[g] || pl->g32[g + 1] > pl->g32[g]) ++pl->launches;
+    }
+    pl->launches += 1 + (pl->t32.empty() ? 0 : 1);  // reduce, check
+    if (tuning) pl->events = tuning->kernel_events;
+  }
   // workspace layout
-  size_t off = 256;
+  size_t off = kBatchHeaderBytes;
   auto take = [&](size_t bytes) {
     const size_t o = off;
     off = align_up(off + bytes, 256);
@@ -406,6 +441,7 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
   pl->off_csr_idx = take(pl->csr_idx.size() * sizeof(int));
   pl->off_tier = take((size_t)batch * sizeof(int));
   pl->off_shape = take((size_t)2 * batch * sizeof(int));
+  pl->off_rerouted = take((size_t)batch * sizeof(int));
   pl->ws_bytes = off;
   *plan = pl;
   return RADIC_OK;
@@ -456,10 +492,10 @@ int radic_batch_plan_info(const radic_batch_plan* plan, int64_t* info, int count
   v[4] = (int64_t)plan->minors32;
   v[5] = (int64_t)plan->minors64;
   int64_t b32 = 0, b64 = 0, bp = 0;
-  for (int m = 1; m <= kBatchMaxM; ++m) {
-    b32 = std::max<int64_t>(b32, plan->blocks32[m]);
-    b64 = std::max<int64_t>(b64, plan->blocks64[m]);
-    bp = std::max<int64_t>(bp, plan->blocksp[m]);
+  for (int g = 0; g < kGroups; ++g) {
+    b32 = std::max<int64_t>(b32, plan->blocks[0][g]);
+    bp = std::max<int64_t>(bp, plan->blocks[1][g]);
+    b64 = std::max<int64_t>(b64, plan->blocks[2][g]);
   }
   v[6] = b32;
   v[7] = b64;
@@ -467,6 +503,10 @@ int radic_batch_plan_info(const radic_batch_plan* plan, int64_t* info, int count
   v[9] = plan->n_pair_matrices;
   v[10] = (int64_t)plan->minors_pair;
   v[11] = bp;
+  v[12] = plan->launches;
+  v[13] = plan->dom_group >= 0 ? plan->dom_group / kPaths : 0;
+  v[14] = plan->dom_group >= 0 ? plan->dom_group % kPaths : 0;
+  v[15] = plan->dom_queue < 0 ? -1 : (plan->dom_queue == 0 ? RADIC_MODE_MIXED : RADIC_MODE_PAIR);
   for (int i = 0; i < count; ++i) info[i] = v[i];
   return RADIC_OK;
 }

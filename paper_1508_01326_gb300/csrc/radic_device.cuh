@@ -12,6 +12,7 @@
 #include <type_traits>
 
 #include "radic_internal.h"
+#include "radic_bound.cuh"
 #include "radic_ff.cuh"
 
 namespace radic {
@@ -257,6 +258,204 @@ __device__ __forceinline__ T lu_det(T (&a)[M][M], T& gmax) {
   return neg ? -det : det;
 }
 
+// lu_det with running error radii (radic_bound.cuh), kept in binary32 for
+// both element types (registers: one radius per entry).  Returns the
+// determinant; bnd receives an upper bound on its error and bad whether a
+// pivot's enclosure reached zero (then bnd is not valid and the caller
+// falls back to Hadamard's inequality or to binary64).  Binary32 radii do
+// not represent values below 2^-126: for binary64 minors the bound does not
+// cover entries below about 2^-70 of their row's largest one.
+template <typename T, int M>
+__device__ __forceinline__ T lu_det_b(T (&a)[M][M], T& gmax, float& bnd, bool& bad,
+                                      float u_in = static_cast<float>(BoundTraits<T>::u_in)) {
+  constexpr float u = static_cast<float>(BoundTraits<T>::u);
+  constexpr float c_div = static_cast<float>(BoundTraits<T>::c_div);
+  float ra[M][M];
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int j = 0; j < M; ++j) ra[i][j] = u_in * static_cast<float>(fabs(a[i][j]));
+  T det = T(1);
+  bool neg = false;
+  float rel = 0.0f;
+  float hs = 0.0f;  // binary64: bound on |det| from the step where a pivot failed
+  bad = false;
+  gmax = T(0);
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+#pragma unroll
+    for (int i = k + 1; i < M; ++i) {
+      const bool sw = mag_key(a[i][k]) > mag_key(a[k][k]);
+#pragma unroll
+      for (int j = k; j < M; ++j) {
+        const T x = a[k][j], y = a[i][j];
+        a[k][j] = sw ? y : x;
+        a[i][j] = sw ? x : y;
+        const float rx = ra[k][j], ry = ra[i][j];
+        ra[k][j] = sw ? ry : rx;
+        ra[i][j] = sw ? rx : ry;
+      }
+      neg ^= sw;
+    }
+    const T piv = a[k][k];
+    const float ap = static_cast<float>(fabs(piv)), rp = ra[k][k];
+    const float ipm = ap > 0.0f ? __frcp_ru(ap) : 0.0f;        // 1 / |p|
+    const float ipd = ap > rp ? __frcp_ru(__fsub_rd(ap, rp)) : 0.0f;  // 1 / (|p| - r_p)
+    if constexpr (sizeof(T) == 8) {
+      if (k < M - 1 && !bad && pivot_unbounded(ap, rp)) {
+        // det = prod_{kk<k} p_kk det(S), S the remaining Schur complement
+        // with entries in [|s| - r, |s| + r]: Hadamard's inequality on the
+        // enclosure of S (the factor covers the binary32 roundings here)
+        float h = 1.0f + static_cast<float>(M * M + 4 * M) * 0x1p-23f;
+#pragma unroll
+        for (int kk = 0; kk < k; ++kk) h *= static_cast<float>(fabs(a[kk][kk])) + ra[kk][kk];
+#pragma unroll
+        for (int j = k; j < M; ++j) {
+          float c2 = 0.0f;
+#pragma unroll
+          for (int i = k; i < M; ++i) {
+            const float e = static_cast<float>(fabs(a[i][j])) + ra[i][j];
+            c2 = fmaf(e, e, c2);
+          }
+          h *= sqrtf(c2);
+        }
+        hs = h;
+      }
+    }
+    det *= piv;
+    gmax = fmax(gmax, fabs(piv));
+    if (k == M - 1) {
+      if (bad) break;
+      // the last pivot divides nothing: a singular minor is bounded by
+      // prod (|p_k| + r_k) instead
+      if (pivot_unbounded(ap, rp) || ap == 0.0f) {
+        float pr = 1.0f;
+#pragma unroll
+        for (int kk = 0; kk < M - 1; ++kk) pr *= static_cast<float>(fabs(a[kk][kk])) + ra[kk][kk];
+        bnd = pr * (ap + rp) * (1.0f + static_cast<float>(M) * u) * 1.0000002f + static_cast<float>(M) * u *
+              static_cast<float>(fabs(det));
+        return neg ? -det : det;
+      }
+      rel = fmaf(1.0f + rel, rp * ipm, rel);
+      break;
+    }
+    bad |= pivot_unbounded(ap, rp);
+    rel = fmaf(1.0f + rel, rp * ipm, rel);
+    T r;
+    if constexpr (sizeof(T) == 8) r = rcp_f64(piv);
+    else r = rcp_f32(piv);
+#pragma unroll
+    for (int i = k + 1; i < M; ++i) {
+      const T l = a[i][k] * r;
+      const float al = static_cast<float>(fabs(l));
+      const float rl = (ra[i][k] + al * rp) * ipd + c_div * u * al;
+#pragma unroll
+      for (int j = k + 1; j < M; ++j) {
+        const float ax = static_cast<float>(fabs(a[k][j])), old = static_cast<float>(fabs(a[i][j]));
+        a[i][j] = fma(-l, a[k][j], a[i][j]);
+        ra[i][j] += al * ra[k][j] + (ax + ra[k][j]) * rl + u * (al * ax + old);
+      }
+    }
+  }
+  rel = fmaf(1.0f + rel, static_cast<float>(M - 1) * u * 1.01f, rel);
+  bnd = rel * static_cast<float>(fabs(det)) * 1.0000001f;
+  // a failed pivot: |computed - exact| <= |computed| + |exact|, the latter
+  // bounded above (binary64 only; the other arithmetics flag the minor)
+  if (sizeof(T) == 8 && bad) bnd = static_cast<float>(fabs(det)) * 1.0000002f + hs;
+  return neg ? -det : det;
+}
+
+// Partial-pivot LU of an m x m row-major binary64 matrix in local memory
+// (m <= MC; the slow paths: binary64 redo of flagged minors, minors of a
+// prefix whose enclosure failed), with running error radii in binary64
+// (radic_bound.cuh; exact division, so a multiplier counts one rounding).
+// *bnd receives an upper bound on the error of the determinant.  The last
+// pivot divides nothing, so its enclosure may reach zero (a singular minor):
+// then the product bound prod (|p_k| + r_k) is used.  When an earlier pivot
+// p_K's enclosure reaches zero, det = prod_{k<K} p_k det(S) with S the
+// remaining Schur complement, so |det| <= prod_{k<K} (|p_k| + r_k) times
+// Hadamard's bound of S's enclosure, prod_j ||(|s_j| + r_j)||, and the error
+// is at most that plus |computed det| (cn: unused, kept for the callers).
+template <int MC>
+__device__ double lu_det_local(double (&a)[MC * MC], int m, const double* cn, double* bnd) {
+  (void)cn;
+  constexpr double u = 0x1p-53;
+  double ra[MC * MC];
+  for (int i = 0; i < m * MC; ++i) ra[i] = 0.0;
+  double det = 1.0, rel = 0.0, pa = 1.0, pr = 1.0;  // pa = prod |p_k|, pr = prod (|p_k| + r_k)
+  double hs = 0.0;                                   // bound on |det| once a pivot failed
+  bool neg = false, bad = false, last_open = false;
+  for (int k = 0; k < m; ++k) {
+    int p = k;
+    double best = fabs(a[k * MC + k]);
+    for (int i = k + 1; i < m; ++i) {
+      const double v = fabs(a[i * MC + k]);
+      if (v > best) {
+        best = v;
+        p = i;
+      }
+    }
+    if (p != k) {
+      for (int j = 0; j < m; ++j) {
+        const double t = a[k * MC + j];
+        a[k * MC + j] = a[p * MC + j];
+        a[p * MC + j] = t;
+        const double tr = ra[k * MC + j];
+        ra[k * MC + j] = ra[p * MC + j];
+        ra[p * MC + j] = tr;
+      }
+      neg = !neg;
+    }
+    const double piv = a[k * MC + k], ap = fabs(piv), rp = ra[k * MC + k];
+    if (k < m - 1 && !bad && pivot_unbounded(ap, rp)) {
+      // Hadamard's bound of the remaining Schur complement's enclosure
+      hs = pr;
+      for (int j = k; j < m; ++j) {
+        double c2 = 0.0;
+        for (int i = k; i < m; ++i) {
+          const double e = fabs(a[i * MC + j]) + ra[i * MC + j];
+          c2 += e * e;
+        }
+        hs *= sqrt(c2) * (1.0 + 0x1p-50);
+      }
+      bad = true;
+    }
+    det *= piv;
+    pa *= ap;
+    pr *= ap + rp;
+    if (k == m - 1) {
+      last_open = pivot_unbounded(ap, rp);
+      if (!last_open && ap > 0.0) rel = (1.0 + rel) * (rp / ap) + rel;
+      break;
+    }
+    if (piv == 0.0) {  // an exactly zero column below the diagonal: singular
+      det = 0.0;
+      break;
+    }
+    rel = (1.0 + rel) * (rp / ap) + rel;
+    const double ipd = bad ? 0.0 : 1.0 / (ap - rp);  // radii are not used once bad
+    for (int i = k + 1; i < m; ++i) {
+      const double l = a[i * MC + k] / piv, al = fabs(l);
+      const double rl = (ra[i * MC + k] + al * rp) * ipd + u * al;
+      for (int j = k + 1; j < m; ++j) {
+        const double x = a[k * MC + j], ax = fabs(x), old = fabs(a[i * MC + j]);
+        a[i * MC + j] = fma(-l, x, a[i * MC + j]);
+        ra[i * MC + j] += al * ra[k * MC + j] + (ax + ra[k * MC + j]) * rl + u * (al * ax + old);
+      }
+    }
+  }
+  const double rnd = (m - 1) * u * 1.01;  // rounding of the product of pivots
+  if (bad) {
+    *bnd = (fabs(det) + hs) * (1.0 + 0x1p-50);
+  } else if (last_open) {
+    *bnd = (pr * (1.0 + rnd) + fabs(det) * rnd) * (1.0 + 0x1p-50);
+  } else {
+    *bnd = ((1.0 + rel) * (1.0 + rnd) - 1.0) * fabs(det) * (1.0 + 0x1p-50);
+  }
+  (void)pa;
+  return neg ? -det : det;
+}
+
 // Gather the minor A[:, c] from the column-major shared copy (column j of A
 // at As + j * CS, CS = padded column stride) into registers.
 template <typename T, int M, int CS>
@@ -350,42 +549,55 @@ __device__ __forceinline__ void warp_reduce_ff(Ff& t, Ff& ta) {
   }
 }
 
-// Block-wide fixed-order reduction of float-float lane totals and a count,
-// entirely on the binary32 pipe (binary64 runs at 1/64 of its rate): warp
-// trees, then the warps' totals in warp order.  The result is valid in thread
-// 0.  `scratch` holds 4 * (blockDim.x / 32) binary64 words.
-__device__ inline void block_reduce_ff(Ff& t, Ff& ta, long long& count, double* scratch) {
+// Block-wide fixed-order reduction of float-float lane totals, a count and
+// the lanes' error bounds (binary64), the totals entirely on the binary32
+// pipe (binary64 runs at 1/64 of its rate): warp trees, then the warps'
+// totals in warp order.  The result is valid in thread 0.  `scratch` holds
+// kScratchWords * (blockDim.x / 32) binary64 words.
+constexpr int kScratchWords = 5;
+__device__ inline void block_reduce_ff(Ff& t, Ff& ta, long long& count, double& bnd, double* scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   warp_reduce_ff(t, ta);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) count += __shfl_xor_sync(kFull, count, off);
-  float* fs = reinterpret_cast<float*>(scratch);
+  for (int off = 16; off > 0; off >>= 1) {
+    count += __shfl_xor_sync(kFull, count, off);
+    bnd += shfl_xor_d(bnd, off);
+  }
+  double* ws = scratch + kScratchWords * warp;
+  float* fs = reinterpret_cast<float*>(ws);
   __syncthreads();
   if (lane == 0) {
-    fs[8 * warp + 0] = t.hi;
-    fs[8 * warp + 1] = t.lo;
-    fs[8 * warp + 2] = ta.hi;
-    fs[8 * warp + 3] = ta.lo;
-    scratch[4 * warp + 2] = __longlong_as_double(count);
+    fs[0] = t.hi;
+    fs[1] = t.lo;
+    fs[2] = ta.hi;
+    fs[3] = ta.lo;
+    ws[2] = __longlong_as_double(count);
+    ws[3] = bnd;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     Ff s, sa;
     long long cnt = 0;
+    double b = 0.0;
     for (int w = 0; w < nw; ++w) {
-      s.merge(Ff{fs[8 * w + 0], fs[8 * w + 1]});
-      sa.merge(Ff{fs[8 * w + 2], fs[8 * w + 3]});
-      cnt += __double_as_longlong(scratch[4 * w + 2]);
+      const double* wv = scratch + kScratchWords * w;
+      const float* fv = reinterpret_cast<const float*>(wv);
+      s.merge(Ff{fv[0], fv[1]});
+      sa.merge(Ff{fv[2], fv[3]});
+      cnt += __double_as_longlong(wv[2]);
+      b += wv[3];
     }
     t = s;
     ta = sa;
     count = cnt;
+    bnd = b;
   }
 }
 
-// Block-wide reduction of (hi, lo, abs, count) in a fixed order; the result
-// is valid in thread 0.  `scratch` holds 4 * (blockDim.x / 32) words.
-__device__ inline void block_reduce_dd(Dd& acc, double& abs_sum, long long& count, double* scratch) {
+// Block-wide reduction of (hi, lo, abs, count, bound) in a fixed order; the
+// result is valid in thread 0.  `scratch` holds kScratchWords *
+// (blockDim.x / 32) words.
+__device__ inline void block_reduce_dd(Dd& acc, double& abs_sum, long long& count, double& bnd, double* scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -395,30 +607,36 @@ __device__ inline void block_reduce_dd(Dd& acc, double& abs_sum, long long& coun
     acc.merge(o);
     abs_sum += shfl_xor_d(abs_sum, off);
     count += __shfl_xor_sync(kFull, count, off);
+    bnd += shfl_xor_d(bnd, off);
   }
+  double* ws = scratch + kScratchWords * warp;
   __syncthreads();
   if (lane == 0) {
-    scratch[4 * warp + 0] = acc.hi;
-    scratch[4 * warp + 1] = acc.lo;
-    scratch[4 * warp + 2] = abs_sum;
-    scratch[4 * warp + 3] = __longlong_as_double(count);
+    ws[0] = acc.hi;
+    ws[1] = acc.lo;
+    ws[2] = abs_sum;
+    ws[3] = __longlong_as_double(count);
+    ws[4] = bnd;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     Dd t;
-    double ab = 0.0;
+    double ab = 0.0, b = 0.0;
     long long cnt = 0;
     for (int w = 0; w < nw; ++w) {
+      const double* wv = scratch + kScratchWords * w;
       Dd o;
-      o.hi = scratch[4 * w + 0];
-      o.lo = scratch[4 * w + 1];
+      o.hi = wv[0];
+      o.lo = wv[1];
       t.merge(o);
-      ab += scratch[4 * w + 2];
-      cnt += __double_as_longlong(scratch[4 * w + 3]);
+      ab += wv[2];
+      cnt += __double_as_longlong(wv[3]);
+      b += wv[4];
     }
     acc = t;
     abs_sum = ab;
     count = cnt;
+    bnd = b;
   }
 }
 
@@ -467,7 +685,10 @@ __device__ __forceinline__ int row_exponent_bits(uint32_t h) {
 
 template <typename T>
 __device__ inline int stage_scaled(const void* A, int dtype, int m, int n, long long lda, T* As, int cs,
-                                   int* row_exp /* smem, m ints */) {
+                                   int* row_exp /* smem, m ints */, bool* exact = nullptr) {
+  // exact (optional, valid in every thread): every staged entry equals its
+  // scaled input (no rounding to T), so the error bounds start from radius 0
+  bool ex = true;
   // 1. row maxima as hi_abs keys, by shared-memory atomics over all entries
   //    at once; the first kKeep entries of every thread stay in registers
   constexpr int kKeep = 4;
@@ -498,18 +719,25 @@ __device__ inline int stage_scaled(const void* A, int dtype, int m, int n, long 
     const int idx = threadIdx.x + k * blockDim.x;
     if (idx < mn) {
       const int i = idx / n, j = idx - i * n;
-      As[j * cs + i] = to_elem<T>(scale_pow2(keep[k], row_exponent_bits(row_h[i])));
+      const double x = scale_pow2(keep[k], row_exponent_bits(row_h[i]));
+      const T t = to_elem<T>(x);
+      As[j * cs + i] = t;
+      ex &= as_double(t) == x;
     }
   }
   for (int idx = threadIdx.x + kKeep * blockDim.x; idx < mn; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
-    As[j * cs + i] = to_elem<T>(scale_pow2(load_elem(A, dtype, (long long)i * lda + j), row_exponent_bits(row_h[i])));
+    const double x = scale_pow2(load_elem(A, dtype, (long long)i * lda + j), row_exponent_bits(row_h[i]));
+    const T t = to_elem<T>(x);
+    As[j * cs + i] = t;
+    ex &= as_double(t) == x;
   }
   for (int idx = threadIdx.x; idx < (cs - m) * n; idx += blockDim.x) {
     const int j = idx / (cs - m), i = m + (idx - j * (cs - m));
     As[j * cs + i] = T(0);
   }
-  __syncthreads();
+  const int all_exact = __syncthreads_and(ex ? 1 : 0);
+  if (exact) *exact = all_exact != 0;
   int tot = 0;
   for (int i = 0; i < m; ++i) tot += row_exponent_bits(row_h[i]);
   return tot;

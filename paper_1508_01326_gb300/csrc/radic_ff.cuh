@@ -106,9 +106,29 @@ __device__ __forceinline__ ff rcp_t(ff a) {
   return fast_sum(r, r * res);
 }
 
+// A pair within 2^-47 of a binary64 value, without the binary64 pipe: the high
+// part takes the leading 24 significand bits (truncated), the low part the
+// remaining 29 bits rounded once to binary32 (error at most 2^-47 |x|), then
+// one Fast2Sum renormalises.  Values outside [2^-70, 2^100] in magnitude (and
+// zeros) take the ordinary conversion.
+__device__ __forceinline__ ff split_to_pair(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int e = static_cast<int>((b >> 52) & 0x7ffu);
+  if (e < 1023 - 70 || e > 1023 + 100) return ff(x);
+  const unsigned long long mant = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+  const unsigned int sign = static_cast<unsigned int>(b >> 63) << 31;
+  const float hi = __uint_as_float(sign | (static_cast<unsigned int>(e - 1023 + 127) << 23) |
+                                   static_cast<unsigned int>((mant >> 29) & 0x7fffffu));
+  const float scale = __uint_as_float(static_cast<unsigned int>(e - 1023 - 52 + 127) << 23);
+  float lo = __uint2float_rn(static_cast<unsigned int>(mant & ((1ull << 29) - 1ull))) * scale;
+  if (sign) lo = -lo;
+  return fast_sum(hi, lo);
+}
+
 }  // namespace pairs
 
 using pairs::ff;
+using pairs::split_to_pair;
 
 // Element conversions used when staging a matrix into shared memory.
 template <typename T>

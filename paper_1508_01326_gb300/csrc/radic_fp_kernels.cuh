@@ -41,12 +41,19 @@ inline bool allow_smem(const void* kernel, size_t bytes) {
   return true;
 }
 
-// Shared-memory layout of the floating-point kernels.
-__host__ __device__ inline size_t fp_smem_bytes(int n, int m, int cs, int elem, int threads) {
+// Shared-memory layout of the floating-point kernels: binomial table, the
+// staged matrix, row exponents, column norms (error bounds), reduction
+// scratch.
+// The pair arithmetic also keeps a binary64 copy of the staged matrix (its
+// prefixes are factored in binary64): `dbl` adds n x (m rounded up to even)
+// binary64 words.
+__host__ __device__ inline size_t fp_smem_bytes(int n, int m, int cs, int elem, int threads, bool dbl = false) {
   size_t off = ((size_t)(n + 1) * (m + 1) * 8 + 15) / 16 * 16;
   off += ((size_t)n * cs * elem + 15) / 16 * 16;
   off += ((size_t)m * 4 + 15) / 16 * 16;
-  off += (size_t)4 * (threads / 32) * 8;
+  off += ((size_t)n * 8 + 15) / 16 * 16;
+  off += (size_t)kScratchWords * (threads / 32) * 8;
+  if (dbl) off += (size_t)n * ((m + 1) / 2 * 2) * 8;
   return off;
 }
 
@@ -55,7 +62,9 @@ struct FpSmem {
   uint64_t* binom;
   T* As;
   int* row_exp;
+  Rad<T>* colnorm;
   double* scratch;
+  double* As64;  // pairs only: binary64 copy, column stride m rounded up to even
   __device__ FpSmem(unsigned char* base, int n, int m, int cs) {
     size_t off = 0;
     binom = reinterpret_cast<uint64_t*>(base);
@@ -64,9 +73,38 @@ struct FpSmem {
     off += ((size_t)n * cs * sizeof(T) + 15) / 16 * 16;
     row_exp = reinterpret_cast<int*>(base + off);
     off += ((size_t)m * 4 + 15) / 16 * 16;
+    colnorm = reinterpret_cast<Rad<T>*>(base + off);
+    off += ((size_t)n * 8 + 15) / 16 * 16;
     scratch = reinterpret_cast<double*>(base + off);
+    off += (size_t)kScratchWords * (blockDim.x / 32) * 8;
+    As64 = std::is_same<T, ff>::value ? reinterpret_cast<double*>(base + off) : nullptr;
   }
 };
+
+// Binary64 copy (column stride cs64) of a pair-staged matrix, exact.
+__device__ __forceinline__ void stage_double_copy(const ff* As, int cs, int m, int n, double* As64, int cs64, int t0,
+                                                  int nt) {
+  for (int idx = t0; idx < n * cs64; idx += nt) {
+    const int j = idx / cs64, i = idx - j * cs64;
+    As64[idx] = i < m ? as_double(As[j * cs + i]) : 0.0;
+  }
+}
+
+// ||A[:, j]||_2 of the staged matrix for every column j (column stride cs),
+// rounded up, computed by the threads [t0, t0 + nt) of the block; the caller
+// synchronises before use.
+template <typename T>
+__device__ __forceinline__ void column_norms(const T* As, int cs, int m, int n, Rad<T>* colnorm, int t0, int nt) {
+  using R = Rad<T>;
+  for (int j = t0; j < n; j += nt) {
+    R s = R(0);
+    for (int i = 0; i < m; ++i) {
+      const R a = mag(As[j * cs + i]);
+      s += a * a;
+    }
+    colnorm[j] = sqrt(s) * R(1.000001);
+  }
+}
 
 // Flag test of the mixed mode: not finite, or pivot growth above threshold.
 template <typename T>
@@ -74,15 +112,20 @@ __device__ __forceinline__ bool mixed_flag(T det, T gmax, T thr) {
   return !(fabs(det) <= static_cast<T>(FLT_MAX)) || !(gmax <= thr);
 }
 
-// Writes the final radic_result from block-ordered partial sums.
-__device__ inline void write_fp_result(radic_result* out, const Dd& t, double abs_sum, int escale, int m,
-                                       unsigned long long total, long long flagged, int status, int tier) {
-  // unit roundoff of the elimination: binary64, pairs of binary32 (about
-  // 2^-46 per operation, 2^-44 allows for the renormalisations), binary32
-  const double u = (tier == kModeFp64) ? 0x1p-53 : (tier == kModePair ? 0x1p-44 : 0x1p-24);
+// Writes the final radic_result from block-ordered partial sums.  `bound`
+// is the sum of the lanes' error bounds (scaled rows); the result's
+// err_bound adds the margin of radic_bound.cuh and the rounding of the
+// accumulation across lanes and blocks: binary64 two-sums lose at most
+// 2^-70 sum|terms| over chains of up to 2^17 additions per lane plus one
+// rounding of the value, float-float lane totals (binary32 elimination) at
+// most 2^-30 sum|terms| over up to 2^16 prefixes per lane.
+__device__ inline void write_fp_result(radic_result* out, const Dd& t, double abs_sum, double bound, int escale,
+                                       int m, unsigned long long total, long long flagged, int status, int tier) {
+  (void)m;
+  const double acc = (tier == kModeMixed ? 0x1p-30 : 0x1p-70) * abs_sum + 0x1p-52 * fabs(t.hi + t.lo);
   out->value = scale_pow2(t.hi + t.lo, -escale);
   out->abs_sum = scale_pow2(abs_sum, -escale);
-  out->err_est = static_cast<double>(m) * u * out->abs_sum;
+  out->err_bound = scale_pow2(kBoundMargin * bound + acc, -escale);
   out->exact_lo = 0;
   out->exact_hi = 0;
   out->minors = static_cast<long long>(total);
@@ -111,20 +154,21 @@ template <bool kMixed>
 __device__ inline void finish_fp_main(const SingleArgs& a, double* scratch, int escale, int m, int tier) {
   if (!last_block(&a.hdr->ticket[0])) return;
   Dd t;
-  double ab = 0.0;
+  double ab = 0.0, bd_sum = 0.0;
   long long fl = 0;
   // partials b = tid, tid + blockDim, ... in that order; kFinishUnroll of
   // them are loaded before any is added, so that their L2 round trips overlap
   const int nb = gridDim.x, bd = blockDim.x;
   for (int b0 = threadIdx.x; b0 < nb; b0 += kFinishUnroll * bd) {
     double2 v[kFinishUnroll];
-    double va[kFinishUnroll];
+    double va[kFinishUnroll], vb[kFinishUnroll];
     long long vc[kFinishUnroll];
 #pragma unroll
     for (int u = 0; u < kFinishUnroll; ++u) {
       const int b = b0 + u * bd;
       v[u] = b < nb ? __ldcg(reinterpret_cast<const double2*>(&a.partials[b])) : make_double2(0.0, 0.0);
       va[u] = b < nb ? __ldcg(&a.partials[b].abs_sum) : 0.0;
+      vb[u] = b < nb ? __ldcg(&a.partials[b].bound) : 0.0;
       vc[u] = b < nb ? __ldcg(&a.partials[b].count) : 0ll;
     }
 #pragma unroll
@@ -135,20 +179,22 @@ __device__ inline void finish_fp_main(const SingleArgs& a, double* scratch, int 
         o.lo = v[u].y;
         t.merge(o);
         ab += va[u];
+        bd_sum += vb[u];
         fl += vc[u];
       }
     }
   }
-  block_reduce_dd(t, ab, fl, scratch);
+  block_reduce_dd(t, ab, fl, bd_sum, scratch);
   if (threadIdx.x == 0) {
     if constexpr (kMixed) {
       a.hdr->main_hi = t.hi;
       a.hdr->main_lo = t.lo;
       a.hdr->main_abs = ab;
+      a.hdr->main_bnd = bd_sum;
       a.hdr->flag_total = fl;
       a.hdr->escale = escale;
     }
-    write_fp_result(a.out, t, ab, escale, m, a.total, 0, a.hdr->status, tier);
+    write_fp_result(a.out, t, ab, bd_sum, escale, m, a.total, 0, a.hdr->status, tier);
   }
 }
 
@@ -156,21 +202,24 @@ __device__ inline void finish_fp_main(const SingleArgs& a, double* scratch, int 
 // float-float (FfPartial): the sum over blocks stays on the binary32 pipe and
 // is widened to binary64 once.  The rounding of these merges (about 2^-46 of
 // the magnitudes added, per level) lies far below the binary32 rounding of
-// the minors that the mixed mode's error estimate states.
+// the minors, and write_fp_result's accumulation term covers it.
 __device__ inline void finish_ff_main(const SingleArgs& a, double* scratch, int escale, int m) {
   if (!last_block(&a.hdr->ticket[0])) return;
   const FfPartial* p = reinterpret_cast<const FfPartial*>(a.partials);
   Ff t, ta;
   long long fl = 0;
+  double bd_sum = 0.0;
   const int nb = gridDim.x, bd = blockDim.x;
   for (int b0 = threadIdx.x; b0 < nb; b0 += kFinishUnroll * bd) {
     float4 v[kFinishUnroll];
     long long vc[kFinishUnroll];
+    double vb[kFinishUnroll];
 #pragma unroll
     for (int u = 0; u < kFinishUnroll; ++u) {
       const int b = b0 + u * bd;
       v[u] = b < nb ? __ldcg(reinterpret_cast<const float4*>(&p[b])) : make_float4(0.f, 0.f, 0.f, 0.f);
       vc[u] = b < nb ? __ldcg(&p[b].count) : 0ll;
+      vb[u] = b < nb ? __ldcg(&p[b].bound) : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < kFinishUnroll; ++u) {
@@ -178,10 +227,11 @@ __device__ inline void finish_ff_main(const SingleArgs& a, double* scratch, int 
         t.merge(Ff{v[u].x, v[u].y});
         ta.merge(Ff{v[u].z, v[u].w});
         fl += vc[u];
+        bd_sum += vb[u];
       }
     }
   }
-  block_reduce_ff(t, ta, fl, scratch);
+  block_reduce_ff(t, ta, fl, bd_sum, scratch);
   if (threadIdx.x == 0) {
     Dd d;  // exact widening of the pair
     d.hi = static_cast<double>(t.hi);
@@ -190,9 +240,10 @@ __device__ inline void finish_ff_main(const SingleArgs& a, double* scratch, int 
     a.hdr->main_hi = d.hi;
     a.hdr->main_lo = d.lo;
     a.hdr->main_abs = ab;
+    a.hdr->main_bnd = bd_sum;
     a.hdr->flag_total = fl;
     a.hdr->escale = escale;
-    write_fp_result(a.out, d, ab, escale, m, a.total, 0, a.hdr->status, kModeMixed);
+    write_fp_result(a.out, d, ab, bd_sum, escale, m, a.total, 0, a.hdr->status, kModeMixed);
   }
 }
 
@@ -206,7 +257,13 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
   FpSmem<T> sm(smem_raw, a.n, M, CS);
   const int n = a.n;
   build_binom(sm.binom, n, M);
-  const int escale = stage_scaled<T>(a.A, a.dtype, M, n, a.lda, sm.As, CS, sm.row_exp);
+  bool exact_in;
+  const int escale = stage_scaled<T>(a.A, a.dtype, M, n, a.lda, sm.As, CS, sm.row_exp, &exact_in);
+  const float uin = exact_in ? 0.0f : static_cast<float>(BoundTraits<T>::u_in);
+  if constexpr (!kTerms) {
+    column_norms<T>(sm.As, CS, M, n, sm.colnorm, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
 
   const int lane = threadIdx.x & 31;
   const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
@@ -217,7 +274,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
   const T thr = static_cast<T>(a.growth);
 
   Dd acc;
-  double abs_sum = 0.0;
+  double abs_sum = 0.0, bnd = 0.0;
   int fcnt = 0;  // flagged ranks of this warp so far (warp-uniform)
   unsigned long long* flist = nullptr;
   if constexpr (kMixed && !kTerms) flist = a.flag_ranks + (g >> 5) * (unsigned long long)a.flag_cap;
@@ -230,17 +287,23 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
     int c[M];
     unrank<M>(q0, n, sm.binom, M + 1, c);
     Ff run;
-    float run_abs = 0.0f;
+    float run_abs = 0.0f, run_bnd = 0.0f;
     for (unsigned long long it = 0; it < L; ++it) {
       const unsigned long long q = q0 + it;
       const bool act = tact && q < q1;
       T mm[M][M];
       gather<T, M, CS>(sm.As, c, mm);
-      T gmax;
-      T det = lu_det<T, M>(mm, gmax);
+      T gmax, det;
+      float b = 0.0f;
+      bool bad = false;
+      if constexpr (kTerms) {
+        det = lu_det<T, M>(mm, gmax);
+      } else {
+        det = lu_det_b<T, M>(mm, gmax, b, bad, uin);
+      }
       if (sign_negative<M>(c)) det = -det;
       bool flag = false;
-      if constexpr (kMixed) flag = mixed_flag<T>(det, gmax, thr);
+      if constexpr (kMixed) flag = mixed_flag<T>(det, gmax, thr) || bad;
       if constexpr (kTerms) {
         if (act) {
           double* terms = static_cast<double*>(a.terms);
@@ -250,6 +313,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
         if (act && !flag) {
           run.add(static_cast<float>(det));
           run_abs += fabsf(static_cast<float>(det));
+          run_bnd += b;
         }
         const unsigned fm = __ballot_sync(kFull, act && flag);
         if (fm) {
@@ -263,23 +327,31 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
         if (act) {
           acc.add(static_cast<double>(det));
           abs_sum += fabs(static_cast<double>(det));
+          run_bnd += b;
         }
       }
-      if constexpr (kMixed && !kTerms) {
+      if constexpr (!kTerms) {
         if ((it & 255) == 255) {  // keep the binary32 partial sums short
-          acc.add(static_cast<double>(run.hi));
-          acc.add(static_cast<double>(run.lo));
-          abs_sum += static_cast<double>(run_abs);
-          run = Ff();
-          run_abs = 0.0f;
+          if constexpr (kMixed) {
+            acc.add(static_cast<double>(run.hi));
+            acc.add(static_cast<double>(run.lo));
+            abs_sum += static_cast<double>(run_abs);
+            run = Ff();
+            run_abs = 0.0f;
+          }
+          bnd += static_cast<double>(run_bnd);
+          run_bnd = 0.0f;
         }
       }
       if (q + 1 < q1) successor<M>(c, n);
     }
-    if constexpr (kMixed && !kTerms) {
-      acc.add(static_cast<double>(run.hi));
-      acc.add(static_cast<double>(run.lo));
-      abs_sum += static_cast<double>(run_abs);
+    if constexpr (!kTerms) {
+      if constexpr (kMixed) {
+        acc.add(static_cast<double>(run.hi));
+        acc.add(static_cast<double>(run.lo));
+        abs_sum += static_cast<double>(run_abs);
+      }
+      bnd += static_cast<double>(run_bnd);
     }
   }
   if constexpr (!kTerms) {
@@ -291,8 +363,8 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
         cnt = fcnt;
       }
     }
-    block_reduce_dd(acc, abs_sum, cnt, sm.scratch);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, cnt};
+    block_reduce_dd(acc, abs_sum, cnt, bnd, sm.scratch);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, cnt, bnd, 0.0};
     finish_fp_main<kMixed>(a, sm.scratch, escale, M, tier_of<T, kMixed>());
   }
 }
@@ -339,13 +411,88 @@ __device__ __forceinline__ T group_det(T (&x)[G], int m, int sub, int seg, T& gm
   return par ? -det : det;
 }
 
+// group_det with running error radii (binary32, one per entry of the
+// lane's row; radic_bound.cuh): the pivot row's radii travel with it by the
+// same shuffles.  bnd and bad are valid in every lane of the group.
+template <typename T, int G>
+__device__ __forceinline__ T group_det_b(T (&x)[G], int m, int sub, int seg, T& gmax, float& bnd, bool& bad,
+                                         float u_in = static_cast<float>(BoundTraits<T>::u_in)) {
+  constexpr float u = static_cast<float>(BoundTraits<T>::u);
+  constexpr float c_div = static_cast<float>(BoundTraits<T>::c_div);
+  float rx[G];
+#pragma unroll
+  for (int j = 0; j < G; ++j) rx[j] = u_in * static_cast<float>(fabs(x[j]));
+  bool alive = sub < m;
+  T det = T(1);
+  int par = 0;
+  float rel = 0.0f, pr = 1.0f;  // pr = prod (|p_k| + r_k)
+  bool last_open = false;
+  bad = false;
+  gmax = T(0);
+  const unsigned segbits = (G == 32) ? kFull : ((1u << G) - 1u);
+#pragma unroll
+  for (int k = 0; k < G; ++k) {
+    if (k >= m) break;
+    uint32_t key = alive ? ((mag_key(x[k]) & ~31u) | (uint32_t)(G - 1 - sub)) : 0u;
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) key = max(key, __shfl_xor_sync(kFull, key, off));
+    const int p = G - 1 - (int)(key & 31u);
+    const T piv = __shfl_sync(kFull, x[k], p, G);
+    const float rp = __shfl_sync(kFull, rx[k], p, G);
+    const unsigned alive_bits = (__ballot_sync(kFull, alive) >> (seg * G)) & segbits;
+    par ^= __popc(alive_bits & ((1u << p) - 1u)) & 1;
+    if (sub == p) alive = false;
+    det *= piv;
+    gmax = fmax(gmax, fabs(piv));
+    const float ap = static_cast<float>(fabs(piv));
+    pr *= ap + rp;
+    const float ipm = ap > 0.0f ? __frcp_ru(ap) : 0.0f;
+    const float ipd = ap > rp ? __frcp_ru(__fsub_rd(ap, rp)) : 0.0f;
+    if (k == m - 1) {
+      // the last pivot divides nothing: a singular minor is bounded by the
+      // product of the pivot enclosures instead
+      last_open = pivot_unbounded(ap, rp) || ap == 0.0f;
+    } else {
+      bad |= pivot_unbounded(ap, rp);
+    }
+    if (!last_open) rel = fmaf(1.0f + rel, rp * ipm, rel);
+    T r;
+    if constexpr (sizeof(T) == 8) r = rcp_f64(piv);
+    else r = rcp_f32(piv);
+    const T l = alive ? x[k] * r : T(0);
+    const float al = static_cast<float>(fabs(l));
+    const float rl = alive ? (rx[k] + al * rp) * ipd + c_div * u * al : 0.0f;
+#pragma unroll
+    for (int j = k + 1; j < G; ++j) {
+      if (j < m) {
+        const T uj = __shfl_sync(kFull, x[j], p, G);
+        const float ru = __shfl_sync(kFull, rx[j], p, G);
+        const float au = static_cast<float>(fabs(uj)), old = static_cast<float>(fabs(x[j]));
+        x[j] = fma(-l, uj, x[j]);
+        rx[j] += al * ru + (au + ru) * rl + u * (al * au + old);
+      }
+    }
+  }
+  rel = fmaf(1.0f + rel, static_cast<float>(m - 1) * u * 1.01f, rel);
+  bnd = last_open ? (pr * (1.0f + static_cast<float>(m) * u) + static_cast<float>(m) * u *
+                                                                      static_cast<float>(fabs(det))) * 1.0000002f
+                  : rel * static_cast<float>(fabs(det)) * 1.0000001f;
+  return par ? -det : det;
+}
+
 template <typename T, int G, bool kMixed, bool kTerms>
 __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.n, m = a.m;
   FpSmem<T> sm(smem_raw, n, m, m);
   build_binom(sm.binom, n, m);
-  const int escale = stage_scaled<T>(a.A, a.dtype, m, n, a.lda, sm.As, m, sm.row_exp);
+  bool exact_in;
+  const int escale = stage_scaled<T>(a.A, a.dtype, m, n, a.lda, sm.As, m, sm.row_exp, &exact_in);
+  const float uin = exact_in ? 0.0f : static_cast<float>(BoundTraits<T>::u_in);
+  if constexpr (!kTerms) {
+    column_norms<T>(sm.As, m, m, n, sm.colnorm, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
 
   const int lane = threadIdx.x & 31, sub = lane & (G - 1), seg = lane / G;
   constexpr int kSegs = 32 / G;
@@ -357,7 +504,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
   const T thr = static_cast<T>(a.growth);
 
   Dd acc;
-  double abs_sum = 0.0;
+  double abs_sum = 0.0, bnd = 0.0;
   int fcnt = 0;
   unsigned long long* flist = nullptr;
   if constexpr (kMixed && !kTerms) flist = a.flag_ranks + gwarp * (unsigned long long)a.flag_cap;
@@ -370,18 +517,31 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
     int c[G];
     unrank_dyn<G>(q0, n, m, sm.binom, m + 1, c);
     Ff run;
-    float run_abs = 0.0f;
+    float run_abs = 0.0f, run_bnd = 0.0f;
     for (unsigned long long it = 0; it < L; ++it) {
       const unsigned long long q = q0 + it;
       const bool act = tact && q < q1;
       T x[G];
 #pragma unroll
       for (int j = 0; j < G; ++j) x[j] = (j < m && sub < m) ? sm.As[c[j] * m + sub] : T(0);
-      T gmax;
-      T det = group_det<T, G>(x, m, sub, seg, gmax);
+      T gmax, det;
+      float b = 0.0f;
+      bool bad = false;
+      if constexpr (kTerms) {
+        det = group_det<T, G>(x, m, sub, seg, gmax);
+      } else {
+        det = group_det_b<T, G>(x, m, sub, seg, gmax, b, bad, uin);
+        if (bad && !kMixed) {  // Hadamard's inequality alone
+          float h = 1.0f;
+#pragma unroll
+          for (int j = 0; j < G; ++j)
+            if (j < m) h *= static_cast<float>(sm.colnorm[c[j]]);
+          b = static_cast<float>(fabs(det)) * 1.0000002f + h;
+        }
+      }
       if (sign_negative_dyn<G>(c, m)) det = -det;
       bool flag = false;
-      if constexpr (kMixed) flag = mixed_flag<T>(det, gmax, thr);
+      if constexpr (kMixed) flag = mixed_flag<T>(det, gmax, thr) || bad;
       const bool lead = act && sub == 0;
       if constexpr (kTerms) {
         if (lead) {
@@ -392,6 +552,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
         if (lead && !flag) {
           run.add(static_cast<float>(det));
           run_abs += fabsf(static_cast<float>(det));
+          run_bnd += b;
         }
         const unsigned fm = __ballot_sync(kFull, lead && flag);
         if (fm) {
@@ -405,23 +566,31 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
         if (lead) {
           acc.add(static_cast<double>(det));
           abs_sum += fabs(static_cast<double>(det));
+          run_bnd += b;
         }
       }
-      if constexpr (kMixed && !kTerms) {
+      if constexpr (!kTerms) {
         if ((it & 255) == 255) {
-          acc.add(static_cast<double>(run.hi));
-          acc.add(static_cast<double>(run.lo));
-          abs_sum += static_cast<double>(run_abs);
-          run = Ff();
-          run_abs = 0.0f;
+          if constexpr (kMixed) {
+            acc.add(static_cast<double>(run.hi));
+            acc.add(static_cast<double>(run.lo));
+            abs_sum += static_cast<double>(run_abs);
+            run = Ff();
+            run_abs = 0.0f;
+          }
+          bnd += static_cast<double>(run_bnd);
+          run_bnd = 0.0f;
         }
       }
       if (q + 1 < q1) successor_dyn<G>(c, n, m);
     }
-    if constexpr (kMixed && !kTerms) {
-      acc.add(static_cast<double>(run.hi));
-      acc.add(static_cast<double>(run.lo));
-      abs_sum += static_cast<double>(run_abs);
+    if constexpr (!kTerms) {
+      if constexpr (kMixed) {
+        acc.add(static_cast<double>(run.hi));
+        acc.add(static_cast<double>(run.lo));
+        abs_sum += static_cast<double>(run_abs);
+      }
+      bnd += static_cast<double>(run_bnd);
     }
   }
   if constexpr (!kTerms) {
@@ -433,8 +602,8 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
         cnt = fcnt;
       }
     }
-    block_reduce_dd(acc, abs_sum, cnt, sm.scratch);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, cnt};
+    block_reduce_dd(acc, abs_sum, cnt, bnd, sm.scratch);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, cnt, bnd, 0.0};
     finish_fp_main<kMixed>(a, sm.scratch, escale, m, tier_of<T, kMixed>());
   }
 }

@@ -40,6 +40,7 @@ struct WsHeader {
   int status;               // device-side status
   double main_hi, main_lo;  // MIXED: binary32 kernel total (scaled rows), two-sum form
   double main_abs;          // MIXED: its sum of |terms|
+  double main_bnd;          // MIXED: its error bound (scaled rows)
   long long flag_total;     // MIXED: flagged minors or prefixes seen by the main kernel
   int escale;               // exponent of the row scaling
   int pad;
@@ -47,10 +48,14 @@ struct WsHeader {
 };
 static_assert(sizeof(WsHeader) <= 256, "header must fit its slot");
 
-// Per-block partial of the floating-point kernels.
+// Per-block partial of the floating-point kernels: two-sum total of the
+// signed minors, sum of their magnitudes, a count, and the error bound of
+// the block's share (scaled rows).
 struct FpPartial {
   double hi, lo, abs_sum;
   long long count;
+  double bound;
+  double pad;
 };
 
 // Per-block partial of the binary32-elimination prefix kernel: float-float
@@ -59,7 +64,8 @@ struct FpPartial {
 struct FfPartial {
   float hi, lo, abs_hi, abs_lo;
   long long count;
-  long long pad;
+  double bound;
+  long long pad[2];
 };
 static_assert(sizeof(FfPartial) == sizeof(FpPartial), "partials share their slots");
 
@@ -144,11 +150,12 @@ size_t smem_mixed(const SinglePlan& p);
 size_t smem_pair(const SinglePlan& p);
 size_t smem_modp(const SinglePlan& p);
 
-// Persistent batched kernels per m (argument: the batched path's BatchArgs):
-// binary32 tier, pair tier (m >= 3), binary64 tier; nullptr outside 1..10.
-const void* batch_kernel_f32(int m);
-const void* batch_kernel_pair(int m);
-const void* batch_kernel_f64(int m);
+// Persistent batched kernels per m and task path (argument: the batched
+// path's BatchArgs): binary32 tier, pair tier (m >= 3), binary64 tier;
+// nullptr outside 1..10 or for a path that does not apply to m.
+const void* batch_kernel_f32(int m, int path);
+const void* batch_kernel_pair(int m, int path);
+const void* batch_kernel_f64(int m, int path);
 
 // Prefix kernel of the EXACT mode for (m, depth) (arguments: SingleArgs,
 // PrefixTable), or nullptr.

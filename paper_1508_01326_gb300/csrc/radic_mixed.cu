@@ -11,48 +11,16 @@ namespace radic {
 
 namespace {
 
-// Partial-pivot LU of an m x m row-major matrix in local memory (m <= MC).
 template <int MC>
-__device__ double lu_det_local(double (&a)[MC * MC], int m) {
-  double det = 1.0;
-  bool neg = false;
-  for (int k = 0; k < m; ++k) {
-    int p = k;
-    double best = fabs(a[k * MC + k]);
-    for (int i = k + 1; i < m; ++i) {
-      const double v = fabs(a[i * MC + k]);
-      if (v > best) {
-        best = v;
-        p = i;
-      }
-    }
-    if (p != k) {
-      for (int j = 0; j < m; ++j) {
-        const double t = a[k * MC + j];
-        a[k * MC + j] = a[p * MC + j];
-        a[p * MC + j] = t;
-      }
-      neg = !neg;
-    }
-    const double piv = a[k * MC + k];
-    det *= piv;
-    if (piv == 0.0) return 0.0;
-    for (int i = k + 1; i < m; ++i) {
-      const double l = a[i * MC + k] / piv;
-      for (int j = k + 1; j < m; ++j) a[i * MC + j] = fma(-l, a[k * MC + j], a[i * MC + j]);
-    }
-  }
-  return neg ? -det : det;
-}
-
-template <int MC>
-__device__ double signed_minor_f64(const FpSmem<double>& sm, int n, int m, unsigned long long q, double& absd) {
+__device__ double signed_minor_f64(const FpSmem<double>& sm, int n, int m, unsigned long long q, double& absd,
+                                   double& bnd) {
   int c[MC];
   unrank_dyn<MC>(q, n, m, sm.binom, m + 1, c);
-  double a[MC * MC];
+  double a[MC * MC], cn[MC];
+  for (int j = 0; j < m; ++j) cn[j] = sm.colnorm[c[j]];
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < m; ++j) a[i * MC + j] = sm.As[c[j] * m + i];
-  double det = lu_det_local<MC>(a, m);
+  double det = lu_det_local<MC>(a, m, cn, &bnd);
   absd = fabs(det);
   return sign_negative_dyn<MC>(c, m) ? -det : det;
 }
@@ -62,7 +30,7 @@ __device__ double signed_minor_f64(const FpSmem<double>& sm, int n, int m, unsig
 // {0..n-1}): the minors that the prefix kernel left out after flagging.
 template <int MC>
 __device__ long long prefix_leaves_f64(const FpSmem<double>& sm, int n, int m, int P, unsigned long long rp, Dd& acc,
-                                       double& abs_sum) {
+                                       double& abs_sum, double& bnd_sum) {
   long long cnt = 0;
   int cols[MC];
   // the binomial table is built for k <= m, which covers P
@@ -72,13 +40,15 @@ __device__ long long prefix_leaves_f64(const FpSmem<double>& sm, int n, int m, i
   for (int d = 0; d < D; ++d) cols[P + d] = v + 1 + d;
   if (cols[m - 1] >= n) return 0;
   for (;;) {
-    double a[MC * MC];
+    double a[MC * MC], cn[MC], b;
+    for (int j = 0; j < m; ++j) cn[j] = sm.colnorm[cols[j]];
     for (int i = 0; i < m; ++i)
       for (int j = 0; j < m; ++j) a[i * MC + j] = sm.As[cols[j] * m + i];
-    double det = lu_det_local<MC>(a, m);
+    double det = lu_det_local<MC>(a, m, cn, &b);
     if (sign_negative_dyn<MC>(cols, m)) det = -det;
     acc.add(det);
     abs_sum += fabs(det);
+    bnd_sum += b;
     ++cnt;
     int pos = m - 1;
     while (pos >= P && cols[pos] == n - m + pos) --pos;
@@ -115,11 +85,13 @@ __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_bloc
   __syncthreads();
 
   Dd acc;
-  double abs_sum = 0.0;
+  double abs_sum = 0.0, bnd = 0.0;
   long long done = 0;
   if (has_work) {
     build_binom(sm.binom, n, m);
     stage_scaled<double>(a.A, a.dtype, m, n, a.lda, sm.As, m, sm.row_exp);
+    column_norms<double>(sm.As, m, m, n, sm.colnorm, threadIdx.x, blockDim.x);
+    __syncthreads();
     if (overflow) {
       const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
       const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,9 +99,10 @@ __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_bloc
       for (unsigned long long task = g; task < a.tasks; task += nthreads) {
         const unsigned long long q0 = task * L, q1 = min(q0 + L, a.total);
         for (unsigned long long q = q0; q < q1; ++q) {
-          double absd;
-          acc.add(signed_minor_f64<MC>(sm, n, m, q, absd));
+          double absd, b;
+          acc.add(signed_minor_f64<MC>(sm, n, m, q, absd, b));
           abs_sum += absd;
+          bnd += b;
           ++done;
         }
       }
@@ -140,22 +113,23 @@ __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_bloc
         if (i < __ldcg(&a.flag_count[w])) {
           const unsigned long long e = __ldcg(&a.flag_ranks[s]);
           if (a.flag_prefix == 0) {
-            double absd;
-            acc.add(signed_minor_f64<MC>(sm, n, m, e, absd));
+            double absd, b;
+            acc.add(signed_minor_f64<MC>(sm, n, m, e, absd, b));
             abs_sum += absd;
+            bnd += b;
             ++done;
           } else {
-            done += prefix_leaves_f64<MC>(sm, n, m, a.flag_prefix, e, acc, abs_sum);
+            done += prefix_leaves_f64<MC>(sm, n, m, a.flag_prefix, e, acc, abs_sum, bnd);
           }
         }
       }
     }
   }
-  block_reduce_dd(acc, abs_sum, done, sm.scratch);
-  if (threadIdx.x == 0) a.partials2[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, done};
+  block_reduce_dd(acc, abs_sum, done, bnd, sm.scratch);
+  if (threadIdx.x == 0) a.partials2[blockIdx.x] = FpPartial{acc.hi, acc.lo, abs_sum, done, bnd, 0.0};
   if (last_block(&a.hdr->ticket[1])) {
     Dd t;
-    double ab = 0.0;
+    double ab = 0.0, bt = 0.0;
     long long flagged = 0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
       Dd o;
@@ -163,9 +137,10 @@ __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_bloc
       o.lo = __ldcg(&a.partials2[b].lo);
       t.merge(o);
       ab += __ldcg(&a.partials2[b].abs_sum);
+      bt += __ldcg(&a.partials2[b].bound);
       flagged += __ldcg(&a.partials2[b].count);
     }
-    block_reduce_dd(t, ab, flagged, sm.scratch);
+    block_reduce_dd(t, ab, flagged, bt, sm.scratch);
     if (threadIdx.x == 0) {
       if (!overflow) {
         Dd mainsum;
@@ -173,8 +148,12 @@ __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_bloc
         mainsum.lo = __ldcg(&a.hdr->main_lo);
         t.merge(mainsum);
         ab += __ldcg(&a.hdr->main_abs);
+        bt += __ldcg(&a.hdr->main_bnd);
       }
-      write_fp_result(a.out, t, ab, __ldcg(&a.hdr->escale), m, a.total, flagged, __ldcg(&a.hdr->status), tier);
+      // the main kernel's part of the accumulation term (binary32 lane
+      // totals in the binary32-elimination prefix kernel) is kept by using
+      // the tier of that kernel
+      write_fp_result(a.out, t, ab, bt, __ldcg(&a.hdr->escale), m, a.total, flagged, __ldcg(&a.hdr->status), tier);
     }
   }
 }

@@ -449,7 +449,7 @@ __device__ inline void crt_write(radic_result* out, const uint32_t* res, int K, 
                      static_cast<double>(static_cast<uint64_t>(mag));
   out->value = ldexp(negv ? -val : val, escale);
   out->abs_sum = 0.0;
-  out->err_est = 0.0;
+  out->err_bound = 0.0;
   out->minors = static_cast<long long>(total);
   out->flagged = 0;
   out->status = (needed > kMaxPrimes) ? RADIC_EOVERFLOW : status;

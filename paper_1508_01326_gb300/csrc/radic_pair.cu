@@ -34,7 +34,7 @@ const void* pick(const SinglePlan& p, bool terms) {
 
 size_t smem_pair(const SinglePlan& p) {
   const int cs = ((p.m + 1) / 2) * 2;  // ColStride of 8-byte elements
-  return prefix_smem_bytes(p.n, p.m, cs, 8, p.threads, p.depth);
+  return prefix_smem_bytes(p.n, p.m, cs, 8, p.threads, p.depth, true);
 }
 
 int blocks_per_sm_pair(const SinglePlan& p) {

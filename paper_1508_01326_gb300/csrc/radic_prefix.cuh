@@ -20,6 +20,7 @@
 
 #include <type_traits>
 
+#include "radic_bound.cuh"
 #include "radic_ff.cuh"
 #include "radic_fp_kernels.cuh"
 
@@ -109,9 +110,10 @@ __host__ __device__ inline size_t zbuf_bytes(int kcap, int lanes, int depth, int
   return (size_t)kcap * lanes * depth * elem;
 }
 
-__host__ __device__ inline size_t prefix_smem_bytes(int n, int m, int cs, int elem, int threads, int depth) {
+__host__ __device__ inline size_t prefix_smem_bytes(int n, int m, int cs, int elem, int threads, int depth,
+                                                    bool dbl = false) {
   const int kmax = n - m + depth;  // largest number of candidate columns
-  return fp_smem_bytes(n, m, cs, elem, threads) + zbuf_bytes(kmax, threads, depth, elem);
+  return fp_smem_bytes(n, m, cs, elem, threads, dbl) + zbuf_bytes(kmax, threads, depth, elem);
 }
 
 // Rank of an ascending 0-based combination in dictionary order (the inverse of
@@ -180,14 +182,118 @@ __device__ __forceinline__ void prefix_factor(const T* __restrict__ As, const in
   }
 }
 
+// A staged entry in the compute type T (pairs widen exactly to binary64).
+template <typename T, typename S>
+__device__ __forceinline__ T widen(const S& x) {
+  if constexpr (std::is_same<T, double>::value && std::is_same<S, ff>::value)
+    return static_cast<double>(x.hi) + static_cast<double>(x.lo);
+  else
+    return x;
+}
+
+// prefix_factor with running error radii (radic_bound.cuh): the same
+// elimination, plus rW, the radii of W, the relative radius of the pivot
+// product and the pivot condition.  The matrix is staged in type S and
+// factored in type T (the pair tier factors its prefixes in binary64 from
+// the pair-staged matrix); radii start at S's input rounding.
+template <typename T, int M, int D, int CS, typename S = T>
+__device__ __forceinline__ void prefix_factor_b(const S* __restrict__ As, const int (&c)[M - D], T (&W)[D][M - D],
+                                                Rad<T> (&rW)[D][M - D], int (&idx)[M], T& prod, T& gmax, bool& neg,
+                                                Rad<T>& rel_alpha, bool& bad,
+                                                float uin = BoundTraits<S>::u_in) {
+  using R = Rad<T>;
+  using B = BoundTraits<T>;
+  constexpr int P = M - D;
+  T a[M][P];
+  R ra[M][P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    const S* col = As + c[j] * CS;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      a[i][j] = widen<T>(col[i]);
+      ra[i][j] = R(uin) * mag(a[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < M; ++i) idx[i] = i;
+  neg = false;
+  prod = T(1);
+  gmax = T(0);
+  R rel = R(0);
+  bad = false;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+#pragma unroll
+    for (int i = k + 1; i < M; ++i) {
+      const bool sw = fabs(a[i][k]) > fabs(a[k][k]);
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const T x = a[k][j], y = a[i][j];
+        a[k][j] = sw ? y : x;
+        a[i][j] = sw ? x : y;
+        const R rx = ra[k][j], ry = ra[i][j];
+        ra[k][j] = sw ? ry : rx;
+        ra[i][j] = sw ? rx : ry;
+      }
+      const int ik = idx[k], ii = idx[i];
+      idx[k] = sw ? ii : ik;
+      idx[i] = sw ? ik : ii;
+      neg ^= sw;
+    }
+    const T piv = a[k][k];
+    const R ap = mag(piv), rp = ra[k][k];
+    bad |= pivot_unbounded(ap, rp);
+    const R ipm = ap > R(0) ? rcp_rad(ap) : R(0);                  // 1 / |p|
+    const R ipd = ap > rp ? rcp_rad(__fsub_rd(ap, rp)) : R(0);     // 1 / (|p| - r_p)
+    rel = fmaf(R(1) + rel, rp * ipm, rel);
+    const T r = rcp_t(piv);
+    prod *= piv;
+    gmax = fmax(gmax, fabs(piv));
+#pragma unroll
+    for (int i = k + 1; i < M; ++i) {
+      const T l = a[i][k] * r;
+      const R al = mag(l);
+      const R rl = (ra[i][k] + al * rp) * ipd + B::c_div * B::u * al;
+      a[i][k] = l;
+      ra[i][k] = rl;
+#pragma unroll
+      for (int j = k + 1; j < P; ++j) {
+        const T x = a[k][j];
+        const R ax = mag(x), old = mag(a[i][j]);
+        a[i][j] = fma(-l, x, a[i][j]);
+        ra[i][j] += al * ra[k][j] + (ax + ra[k][j]) * rl + B::u * (al * ax + old);
+      }
+    }
+  }
+  rel_alpha = fmaf(R(1) + rel, R(P > 1 ? P - 1 : 0) * B::u * R(1.01), rel);
+#pragma unroll
+  for (int rr = 0; rr < D; ++rr) {
+#pragma unroll
+    for (int j = P - 1; j >= 0; --j) {
+      T s = -a[P + rr][j];
+      R rs = ra[P + rr][j], ms = mag(s);
+#pragma unroll
+      for (int i = j + 1; i < P; ++i) {
+        const R aw = mag(W[rr][i]), aa = mag(a[i][j]);
+        s = fma(-W[rr][i], a[i][j], s);
+        rs += rW[rr][i] * (aa + ra[i][j]) + aw * ra[i][j];
+        ms += aw * aa;
+      }
+      W[rr][j] = s;
+      rW[rr][j] = rs + R(P - 1 - j) * B::u * ms;
+    }
+  }
+}
+
 // Schur complement (D entries) of column `col`, rows read in the order idx[].
-template <typename T, int M, int D>
-__device__ __forceinline__ void prefix_column(const T* __restrict__ col, const T (&W)[D][M - D], const int (&idx)[M],
+template <typename T, int M, int D, typename S = T>
+__device__ __forceinline__ void prefix_column(const S* __restrict__ col, const T (&W)[D][M - D], const int (&idx)[M],
                                               T (&z)[D]) {
   constexpr int P = M - D;
   T x[M];
 #pragma unroll
-  for (int s = 0; s < M; ++s) x[s] = col[idx[s]];
+  for (int s = 0; s < M; ++s) x[s] = widen<T>(col[idx[s]]);
 #pragma unroll
   for (int d = 0; d < D; ++d) z[d] = x[P + d];
 #pragma unroll
@@ -201,14 +307,18 @@ __device__ __forceinline__ void prefix_column(const T* __restrict__ col, const T
 // flushed per prefix for binary32.
 template <typename T>
 struct PrefixAcc;
+// Every variant also sums the error bounds of the prefixes it keeps (bnd,
+// radic_bound.cuh); a dropped prefix's bound is dropped with its terms.
 template <>
 struct PrefixAcc<double> {
   Dd acc;
   double abs_sum = 0.0;
+  double bnd = 0.0;
   __device__ __forceinline__ void add_column(double s, double a) {
     acc.add(s);
     abs_sum += a;
   }
+  __device__ __forceinline__ void add_bound(double b) { bnd += b; }
   __device__ __forceinline__ void end_prefix() {}
   __device__ __forceinline__ void finish() {}
 };
@@ -218,21 +328,26 @@ struct PrefixAcc<float> {
   // to binary64 once at the end (keeps the binary64 pipe free)
   Ff pre, tot, tot_abs;
   float pre_abs = 0.0f;
+  float pre_bnd = 0.0f, bnd = 0.0f;
   Dd acc;
   double abs_sum = 0.0;
   __device__ __forceinline__ void add_column(float s, float a) {
     pre.add(s);
     pre_abs += a;
   }
+  __device__ __forceinline__ void add_bound(float b) { pre_bnd += b; }
   __device__ __forceinline__ void end_prefix() {
     tot.merge(pre);
     tot_abs.add(pre_abs);
+    bnd += pre_bnd;
     pre = Ff();
     pre_abs = 0.0f;
+    pre_bnd = 0.0f;
   }
   __device__ __forceinline__ void drop_prefix() {
     pre = Ff();
     pre_abs = 0.0f;
+    pre_bnd = 0.0f;
   }
   __device__ __forceinline__ void finish() {
     acc.add(static_cast<double>(tot.hi));
@@ -247,6 +362,7 @@ struct PrefixAcc<ff> {
   // (one flush per prefix, off the leaf loop), binary32 pairs for |terms|
   ff pre = ff(0.0f, 0.0f);
   float pre_abs = 0.0f;
+  float pre_bnd = 0.0f, bnd = 0.0f;
   Ff tot_abs;
   Dd acc;
   double abs_sum = 0.0;
@@ -254,16 +370,20 @@ struct PrefixAcc<ff> {
     pre += s;
     pre_abs += a.hi;
   }
+  __device__ __forceinline__ void add_bound(float b) { pre_bnd += b; }
   __device__ __forceinline__ void end_prefix() {
     acc.add(static_cast<double>(pre.hi));
     acc.add(static_cast<double>(pre.lo));
     tot_abs.add(pre_abs);
+    bnd += pre_bnd;
     pre = ff(0.0f, 0.0f);
     pre_abs = 0.0f;
+    pre_bnd = 0.0f;
   }
   __device__ __forceinline__ void drop_prefix() {
     pre = ff(0.0f, 0.0f);
     pre_abs = 0.0f;
+    pre_bnd = 0.0f;
   }
   __device__ __forceinline__ void finish() {
     abs_sum = static_cast<double>(tot_abs.hi) + static_cast<double>(tot_abs.lo);
@@ -323,12 +443,82 @@ __device__ __forceinline__ T dot3(const T (&x)[3], const T (&w)[3]) {
   return fma(x[0], w[0], fma(x[1], w[1], x[2] * w[2]));
 }
 
+// Error-bound state of one prefix's leaf phase (radic_bound.cuh): the
+// symmetric sums of the candidate columns' (||z^||, radius) and the lane's
+// sum of |terms| of the prefix.  With kOn = false it does nothing.
+template <typename T, int D, int P, bool kOn>
+struct LeafBound {
+  using R = Rad<T>;
+  R rW[kOn ? D : 1][kOn ? P : 1];  // radii of W
+  R aW[kOn ? D : 1][kOn ? P : 1];  // |W|
+  R cround;                        // P u + u_in: rounding of a Schur-complement entry per unit of its terms
+  R uin;
+  LeafPoly<R, D> poly;
+  R pabs;
+  template <typename W_t>
+  __device__ __forceinline__ LeafBound(const W_t& W, const R (*rw)[P], R uin_) : uin(uin_), pabs(R(0)) {
+    if constexpr (kOn) {
+      cround = R(P) * R(BoundTraits<T>::u) + uin_;
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          rW[d][j] = rw[d][j] * (R(1) + uin_);
+          aW[d][j] = mag(W[d][j]);
+        }
+    }
+  }
+  // z: the column's computed Schur complement (before its sign and alpha),
+  // ax: the magnitudes of its column entries in the prefix's row order.
+  // |z_d - z^_d| <= sum_j rW_dj |x_j| + (P u + u_in)(|x_Bd| + sum_j |W_dj| |x_j|)
+  __device__ __forceinline__ void column(const T (&z)[D], const R (&ax)[P + D]) {
+    if constexpr (kOn) {
+      R n2 = R(0), r2 = R(0);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const R a = mag(z[d]);
+        n2 += a * a;
+        R s1 = R(0), s2 = ax[P + d];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          s1 += rW[d][j] * ax[j];
+          s2 += aW[d][j] * ax[j];
+        }
+        const R rz = s1 + cround * s2;
+        r2 += rz * rz;
+      }
+      poly.add(sqrt(n2) * R(1.0000005), sqrt(r2) * R(1.000002));
+    }
+  }
+  __device__ __forceinline__ void term_abs(const T& babs) {
+    if constexpr (kOn) pabs += mag(babs);
+  }
+};
+
 // Schur complement of candidate column `col`, with the sign of its index
 // parity and (first entry) the prefix scale alpha folded in; updates zmax.
-template <typename T, int M, int D, int CS>
+template <typename T, int M, int D, int CS, bool kB>
 __device__ __forceinline__ void leaf_column(const T* __restrict__ As, int col, const T (&W)[D][M - D],
-                                            const int (&idx)[M], T alpha, T (&z)[D], T& zmax) {
-  prefix_column<T, M, D>(As + col * CS, W, idx, z);
+                                            const int (&idx)[M], T alpha, T (&z)[D], T& zmax,
+                                            LeafBound<T, D, M - D, kB>& lb) {
+  constexpr int P = M - D;
+  const T* cp = As + col * CS;
+  T x[M];
+#pragma unroll
+  for (int s = 0; s < M; ++s) x[s] = cp[idx[s]];
+#pragma unroll
+  for (int d = 0; d < D; ++d) z[d] = x[P + d];
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) z[d] = fma(W[d][j], x[j], z[d]);
+  }
+  if constexpr (kB) {
+    Rad<T> ax[M];
+#pragma unroll
+    for (int s = 0; s < M; ++s) ax[s] = mag(x[s]);
+    lb.column(z, ax);
+  }
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     zmax = fmax(zmax, fabs(z[d]));
@@ -351,10 +541,11 @@ __device__ __forceinline__ void leaf_column(const T* __restrict__ As, int col, c
 // kCoop: the buffer already holds every column's z (written by the lanes
 // sharing the prefix, see prefix_leaves); the block's columns are read from
 // it instead of being reduced here.
-template <typename T, int M, int D, int CS, bool kCoop>
+template <typename T, int M, int D, int CS, bool kCoop, bool kB>
 __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, int v, int k, const T (&W)[D][M - D],
                                                       const int (&idx)[M], T alpha, const ZBuf<T, D>& zb, bool act,
-                                                      int sub, int lp, PrefixAcc<T>& acc, T& zmax) {
+                                                      int sub, int lp, PrefixAcc<T>& acc, T& zmax,
+                                                      LeafBound<T, D, M - D, kB>& lb) {
   constexpr int LB = leaf_block<T>();
   for (int q = 0; q < k; q += LB) {
     T z[LB][D];
@@ -364,7 +555,7 @@ __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, 
         if constexpr (kCoop) {
           zb.get(q + b, z[b]);
         } else {
-          leaf_column<T, M, D, CS>(As, v + 1 + q + b, W, idx, alpha, z[b], zmax);
+          leaf_column<T, M, D, CS>(As, v + 1 + q + b, W, idx, alpha, z[b], zmax, lb);
         }
       } else {
 #pragma unroll
@@ -392,20 +583,28 @@ __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, 
         }
       }
     } else {
-      // (q1, q2, q + b), q1 < q2 < q: y1 . (y2 x z_b); q2 = 0 has no q1
+      // (q1, q2, q + b), q1 < q2 < q: y1 . (y2 x z_b); q2 = 0 has no q1.
+      // The leaves of one (q2, b) are summed apart and then added to the
+      // column sum, so that no term passes through more than about 2k
+      // additions (the summation part of the error bound).
       for (int q2 = (sub == 0 ? lp : sub); q2 < q; q2 += lp) {
         T y2[3];
         zb.get(q2, y2);
-        T w[LB][3];
+        T w[LB][3], s2[LB];
 #pragma unroll
-        for (int b = 0; b < LB; ++b) cross3(y2, z[b], w[b]);
+        for (int b = 0; b < LB; ++b) {
+          cross3(y2, z[b], w[b]);
+          s2[b] = T(0);
+        }
 #pragma unroll 2
         for (int q1 = 0; q1 < q2; ++q1) {
           T y1[3];
           zb.get(q1, y1);
 #pragma unroll
-          for (int b = 0; b < LB; ++b) leaf_add(dot3(y1, w[b]), cs[b], ca[b]);
+          for (int b = 0; b < LB; ++b) leaf_add(dot3(y1, w[b]), s2[b], ca[b]);
         }
+#pragma unroll
+        for (int b = 0; b < LB; ++b) cs[b] += s2[b];
       }
       if constexpr (LB > 1) {
         // (q1, q + b2, q + b), q1 < q, b2 < b: y1 . (z_b2 x z_b); pair
@@ -447,7 +646,10 @@ __device__ __forceinline__ void prefix_leaves_blocked(const T* __restrict__ As, 
       bsum += cs[b];
       babs += ca[b];
     }
-    if (act) acc.add_column(bsum, babs);
+    if (act) {
+      acc.add_column(bsum, babs);
+      lb.term_abs(babs);
+    }
     if constexpr (!kCoop) {
 #pragma unroll
       for (int b = 0; b < LB; ++b) {
@@ -482,16 +684,18 @@ __device__ __forceinline__ void prefix_leaves_terms(const T* __restrict__ As, co
                                                     int k, const T (&W)[D][M - D], const int (&idx)[M], T alpha,
                                                     unsigned long long rank_prefix, const ZBuf<T, D>& zb, bool act,
                                                     int sub, int lp, PrefixAcc<T>& acc, T& zmax,
-                                                    const TermsSink& ts) {
+                                                    const TermsSink& ts, bool nan_out = false) {
   const int bs = M + 1;
   auto emit = [&](T d, unsigned long long rk) {
     rk = ts.qtot - 1 - rk;
-    if (act && rk >= ts.q0 && rk < ts.q0 + ts.count) ts.terms[rk - ts.q0] = ldexp(static_cast<double>(d), ts.escale);
+    if (act && rk >= ts.q0 && rk < ts.q0 + ts.count)
+      ts.terms[rk - ts.q0] = nan_out ? __longlong_as_double(0x7ff8000000000000ll) : ldexp(static_cast<double>(d), ts.escale);
   };
   for (int q = 0; q < k; ++q) {
     const int col = v + 1 + q;
     T z[D];
-    leaf_column<T, M, D, CS>(As, col, W, idx, alpha, z, zmax);
+    LeafBound<T, D, M - D, false> nob(W, nullptr, Rad<T>(0));
+    leaf_column<T, M, D, CS>(As, col, W, idx, alpha, z, zmax, nob);
     const unsigned long long rk_col = rank_prefix + rank_part(binom, bs, n, col, 1);
     T colsum = T(0), colabs = T(0);
     if constexpr (D == 2) {
@@ -530,11 +734,57 @@ __device__ __forceinline__ void prefix_leaves_terms(const T* __restrict__ As, co
 // `zb` is this lane's column buffer.  Returns the growth flag of the mixed
 // mode: largest prefix pivot, or 2^(D-1) max|z| (a bound for the last D
 // pivots under partial pivoting), above `thr`, or a non-finite scale.
-template <typename T, int M, int D, int CS, bool kTerms>
+// Binary64 slow path for a prefix whose enclosure reached zero (a pivot
+// indistinguishable from zero): every minor of its subtree is factored on its
+// own (lu_det_local: partial pivoting over the whole minor, with its own
+// bound).  This lane takes the minors whose middle leaf column (D = 3) or
+// first leaf column (D = 2), counted from v+1, is congruent to sub mod lp.
+template <int M, int D, int CS>
+__device__ __noinline__ void prefix_minors_f64(const double* __restrict__ As, const int (&c)[M - D], int v, int n,
+                                               int sub, int lp, PrefixAcc<double>& acc, const float* colnorm) {
+  constexpr int P = M - D;
+  const int k = n - 1 - v;
+  if (k < D) return;
+  int cols[M];
+#pragma unroll
+  for (int j = 0; j < P; ++j) cols[j] = c[j];
+  int q[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) q[d] = d;
+  for (;;) {
+    const int key = (D == 3) ? q[1] : q[0];
+    if (key % lp == sub) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) cols[P + d] = v + 1 + q[d];
+      double a[M * M], cn[M], b;
+      for (int j = 0; j < M; ++j) {
+        cn[j] = static_cast<double>(colnorm[cols[j]]);
+        for (int i = 0; i < M; ++i) a[i * M + j] = As[cols[j] * CS + i];
+      }
+      double det = lu_det_local<M>(a, M, cn, &b);
+      if (sign_negative<M>(cols)) det = -det;
+      acc.add_column(det, fabs(det));
+      acc.add_bound(b);
+    }
+    int pos = D - 1;
+    while (pos >= 0 && q[pos] == k - D + pos) --pos;
+    if (pos < 0) break;
+    ++q[pos];
+    for (int j = pos + 1; j < D; ++j) q[j] = q[j - 1] + 1;
+  }
+}
+
+template <typename T, int M, int D, int CS, bool kTerms, bool kRedo = true>
 __device__ __forceinline__ bool prefix_leaves(const T* __restrict__ As, const uint64_t* binom, int n, int v,
                                               const int (&c)[M - D], const T (&W)[D][M - D], const int (&idx)[M],
                                               T prod, T gmax, bool neg, const ZBuf<T, D>& zb, T thr, bool act,
-                                              int sub, int lp, PrefixAcc<T>& acc, const TermsSink& ts) {
+                                              int sub, int lp, PrefixAcc<T>& acc, const TermsSink& ts,
+                                              const Rad<T>* colnorm = nullptr,
+                                              const PrefixErr<Rad<T>>& pe = PrefixErr<Rad<T>>{},
+                                              const Rad<T> (*rW)[M - D] = nullptr, float uin = 0.0f) {
+  using R = Rad<T>;
+  using B = BoundTraits<T>;
+  constexpr bool kB = !kTerms;
   constexpr int P = M - D;
   // parity of r = M(M+1)/2, of the prefix columns' share of s, and of the D
   // leaf columns' "+1" terms; the leaf columns' own parities are folded in
@@ -545,12 +795,32 @@ __device__ __forceinline__ bool prefix_leaves(const T* __restrict__ As, const ui
   const T alpha = ((sp & 1) != neg) ? -prod : prod;
   T zmax = T(0);
   const int k = n - 1 - v;
+  LeafBound<T, D, P, kB> lb(W, rW, uin);
+  // binary64 without a redo pass: a prefix whose enclosure failed takes the
+  // per-minor slow path after the warp's leaf phase (its leaves there are
+  // formed but not added)
+  constexpr bool kSlow = kB && !kRedo && std::is_same<T, double>::value;
+  const bool slow = kSlow && pe.bad;
+  const bool act_in = act;
+  act = act && !slow;
   if constexpr (kTerms) {
     unsigned long long rank_prefix = 0;
 #pragma unroll
     for (int j = 0; j < P; ++j) rank_prefix += rank_part(binom, M + 1, n, c[j], M - j);
+    // modes that redo flagged prefixes mark every term of one with NaN: the
+    // growth flag needs max |z| over all of the prefix's columns first
+    bool nan_out = false;
+    if constexpr (kRedo) {
+      T zm = T(0);
+      for (int q = 0; q < k; ++q) {
+        T z[D];
+        LeafBound<T, D, P, false> nob(W, nullptr, R(0));
+        leaf_column<T, M, D, CS>(As, v + 1 + q, W, idx, alpha, z, zm, nob);
+      }
+      nan_out = !(gmax <= thr) || !((D == 2 ? T(2) : T(4)) * zm <= thr) || !(fabs(alpha) <= static_cast<T>(FLT_MAX));
+    }
     prefix_leaves_terms<T, M, D, CS>(As, binom, n, v, k, W, idx, alpha, rank_prefix, zb, act, sub, lp, acc, zmax,
-                                     ts);
+                                     ts, nan_out);
   } else {
     if constexpr (D == 3) {
       // Two phases.  The lp lanes sharing the prefix split its column
@@ -558,39 +828,94 @@ __device__ __forceinline__ bool prefix_leaves(const T* __restrict__ As, const ui
       // group's buffer (the slots of the group's first lane); then each lane
       // forms its share of the leaves from all of them (W and the row order
       // are no longer live there).  Every lane ends with the group's largest
-      // |z| for the growth flag.
+      // |z| for the growth flag, and the symmetric sums of the bound over all
+      // of the group's columns.
       const ZBuf<T, D> zg = zb.shifted(-sub);
       for (int q = sub; q < k; q += lp) {
         T z[D];
-        leaf_column<T, M, D, CS>(As, v + 1 + q, W, idx, alpha, z, zmax);
+        leaf_column<T, M, D, CS>(As, v + 1 + q, W, idx, alpha, z, zmax, lb);
         zg.put(q, z);
       }
       zmax = group_max(zmax, lp);
+      group_combine(lb.poly, lp);
       __syncwarp();
-      prefix_leaves_blocked<T, M, D, CS, true>(As, v, k, W, idx, alpha, zg, act, sub, lp, acc, zmax);
+      prefix_leaves_blocked<T, M, D, CS, true>(As, v, k, W, idx, alpha, zg, act, sub, lp, acc, zmax, lb);
       __syncwarp();  // the buffer is rewritten by the group's next prefix
     } else {
-      prefix_leaves_blocked<T, M, D, CS, false>(As, v, k, W, idx, alpha, zb, act, sub, lp, acc, zmax);
+      prefix_leaves_blocked<T, M, D, CS, false>(As, v, k, W, idx, alpha, zb, act, sub, lp, acc, zmax, lb);
+    }
+  }
+  bool bad = false;
+  if constexpr (kB) {
+    // this lane's share of the prefix's bound (radic_bound.cuh)
+    R b = (pe.rel_alpha + B::u * leaf_sum_depth(D, k, leaf_block<T>())) * lb.pabs;
+    if (sub == 0)
+      b += mag(alpha) * (R(1) + pe.rel_alpha) *
+           (lb.poly.perturbation() + R(leaf_round_coef<D>()) * B::u * lb.poly.hadamard());
+    if (act) acc.add_bound(b);
+    if constexpr (kSlow) {
+      if (slow && act_in) prefix_minors_f64<M, D, CS>(As, c, v, n, sub, lp, acc, colnorm);
+    } else if (pe.bad) {
+      bad = true;  // the caller redoes the prefix in binary64
     }
   }
   const T growth_bound = (D == 2 ? T(2) : T(4)) * zmax;
-  return !(gmax <= thr) || !(growth_bound <= thr) || !(fabs(alpha) <= static_cast<T>(FLT_MAX));
+  return bad || !(gmax <= thr) || !(growth_bound <= thr) || !(fabs(alpha) <= static_cast<T>(FLT_MAX));
+}
+
+// Pairs of binary32 factor their prefixes in binary64 (the FP64 pipe, a
+// small share of the work once amortised over the leaves): its radii are
+// those of binary64 arithmetic, far below what the same elimination in pairs
+// would carry, and the conversion of W, the pivot product and the growth
+// measure to pairs (split_to_pair, on the integer and binary32 pipes) adds
+// 2^-47 relative.
+template <int D, int P>
+__device__ __forceinline__ void prefix_to_pairs(const double (&Wd)[D][P], float (&rW)[D][P], double prodd, double gmaxd,
+                                                float& rel, ff (&W)[D][P], ff& prod, ff& gmax) {
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      W[d][j] = split_to_pair(Wd[d][j]);
+      rW[d][j] += 0x1p-47f * mag(W[d][j]);
+    }
+  prod = split_to_pair(prodd);
+  gmax = split_to_pair(gmaxd);
+  rel = fmaf(1.0f + rel, 0x1p-47f, rel);
 }
 
 // Processes one prefix c[0..m-D-1] (last column v): factors it, then its
 // leaves (prefix_leaves).
-template <typename T, int M, int D, int CS, bool kTerms>
+template <typename T, int M, int D, int CS, bool kTerms, bool kRedo = true>
 __device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint64_t* binom, int n, int v,
                                            const int (&c)[M - D], const ZBuf<T, D>& zb, T thr, bool act, int sub,
-                                           int lp, PrefixAcc<T>& acc, const TermsSink& ts) {
+                                           int lp, PrefixAcc<T>& acc, const TermsSink& ts,
+                                           const Rad<T>* colnorm = nullptr, float uin = BoundTraits<T>::u_in,
+                                           const double* As64 = nullptr) {
   constexpr int P = M - D;
   T W[D][P];
   int idx[M];
   T prod, gmax;
   bool neg;
-  prefix_factor<T, M, D, CS>(As, c, W, idx, prod, gmax, neg);
-  return prefix_leaves<T, M, D, CS, kTerms>(As, binom, n, v, c, W, idx, prod, gmax, neg, zb, thr, act, sub, lp, acc,
-                                            ts);
+  if constexpr (kTerms) {
+    prefix_factor<T, M, D, CS>(As, c, W, idx, prod, gmax, neg);
+    return prefix_leaves<T, M, D, CS, kTerms, kRedo>(As, binom, n, v, c, W, idx, prod, gmax, neg, zb, thr, act, sub,
+                                                     lp, acc, ts);
+  } else {
+    Rad<T> rW[D][P];
+    PrefixErr<Rad<T>> pe;
+    if constexpr (std::is_same<T, ff>::value) {
+      double Wd[D][P], prodd, gmaxd;
+      prefix_factor_b<double, M, D, ColStride<double, M>::value, double>(As64, c, Wd, rW, idx, prodd, gmaxd, neg,
+                                                                          pe.rel_alpha, pe.bad, uin);
+      prefix_to_pairs<D, P>(Wd, rW, prodd, gmaxd, pe.rel_alpha, W, prod, gmax);
+    } else {
+      prefix_factor_b<T, M, D, CS>(As, c, W, rW, idx, prod, gmax, neg, pe.rel_alpha, pe.bad, uin);
+    }
+    pe.kappa = 0.0f;
+    return prefix_leaves<T, M, D, CS, kTerms, kRedo>(As, binom, n, v, c, W, idx, prod, gmax, neg, zb, thr, act, sub,
+                                                     lp, acc, ts, colnorm, pe, rW, uin);
+  }
 }
 
 // Head sharing: the prefixes whose first H = m-D-1 columns (the head) agree
@@ -652,6 +977,112 @@ __device__ __forceinline__ void prefix_extend(const T* __restrict__ As, int v, c
   neg = ng;
 }
 
+// Radii of the D+1 Schur-complement entries of any column x against a
+// factored head (W1, rW1): |s_r - s^_r| <= k1[r] ||x||_2 (kappa_of, per row;
+// S: the staging type of x).
+template <typename T, int Dp1, int H, typename S = T>
+__device__ __forceinline__ void head_kappas(const T (&W1)[Dp1][H], const Rad<T> (&rW1)[Dp1][H], Rad<T> (&k1)[Dp1],
+                                            float uin = BoundTraits<S>::u_in) {
+  using R = Rad<T>;
+  constexpr R kU = BoundTraits<T>::u;
+  const R kUin = uin;
+#pragma unroll
+  for (int r = 0; r < Dp1; ++r) {
+    R w2 = R(0), r2 = R(0);
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const R w = mag(W1[r][j]);
+      w2 += w * w;
+      r2 += rW1[r][j] * rW1[r][j];
+    }
+    k1[r] = (sqrt(r2) * (R(1) + kUin) + (R(H) * kU + kUin) * (R(1) + sqrt(w2))) * R(1.0001);
+  }
+}
+
+// prefix_extend with running error radii: the elimination step that appends
+// column v to a factored head, with the radii of W, of the pivot product and
+// the pivot condition.  k1: head_kappas of the head; xnorm = ||A[:, v]||_2.
+template <typename T, int M, int D, int CS, typename S = T>
+__device__ __forceinline__ void prefix_extend_b(const S* __restrict__ As, int v, Rad<T> xnorm,
+                                                const T (&W1)[D + 1][M - D - 1],
+                                                const Rad<T> (&rW1)[D + 1][M - D - 1], const Rad<T> (&k1)[D + 1],
+                                                const int (&idx1)[M], T prod1, T gmax1, bool neg1, Rad<T> rel1,
+                                                bool bad1, T (&W)[D][M - D], Rad<T> (&rW)[D][M - D], int (&idx)[M],
+                                                T& prod, T& gmax, bool& neg, Rad<T>& rel_alpha, bool& bad) {
+  using R = Rad<T>;
+  using B = BoundTraits<T>;
+  constexpr int H = M - D - 1;
+  T s[D + 1];
+  prefix_column<T, M, D + 1, S>(As + v * CS, W1, idx1, s);
+  R rs[D + 1];
+#pragma unroll
+  for (int r = 0; r <= D; ++r) rs[r] = k1[r] * xnorm;
+  T Wr[D + 1][H];
+  R rWr[D + 1][H];
+  int ir[D + 1];
+#pragma unroll
+  for (int r = 0; r <= D; ++r) {
+    ir[r] = idx1[H + r];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      Wr[r][j] = W1[r][j];
+      rWr[r][j] = rW1[r][j];
+    }
+  }
+  bool ng = neg1;
+#pragma unroll
+  for (int r = 1; r <= D; ++r) {
+    const bool sw = fabs(s[r]) > fabs(s[0]);
+    const T a0 = s[0], ar = s[r];
+    s[0] = sw ? ar : a0;
+    s[r] = sw ? a0 : ar;
+    const R q0 = rs[0], qr = rs[r];
+    rs[0] = sw ? qr : q0;
+    rs[r] = sw ? q0 : qr;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const T x = Wr[0][j], y = Wr[r][j];
+      Wr[0][j] = sw ? y : x;
+      Wr[r][j] = sw ? x : y;
+      const R rx = rWr[0][j], ry = rWr[r][j];
+      rWr[0][j] = sw ? ry : rx;
+      rWr[r][j] = sw ? rx : ry;
+    }
+    const int i0 = ir[0], irr = ir[r];
+    ir[0] = sw ? irr : i0;
+    ir[r] = sw ? i0 : irr;
+    ng ^= sw;
+  }
+  const T piv = s[0];
+  const R ap = mag(piv), rp = rs[0];
+  bad = bad1 || pivot_unbounded(ap, rp);
+  const R ipm = ap > R(0) ? rcp_rad(ap) : R(0);
+  const R ipd = ap > rp ? rcp_rad(__fsub_rd(ap, rp)) : R(0);
+  rel_alpha = fmaf(R(1) + rel1, fmaf(R(1) + rp * ipm, B::u * R(1.01), rp * ipm), rel1);
+  const T rr = rcp_t(piv);
+  prod = prod1 * piv;
+  gmax = fmax(gmax1, fabs(piv));
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const T l = s[d + 1] * rr;
+    const R al = mag(l);
+    const R rl = (rs[d + 1] + al * rp) * ipd + B::c_div * B::u * al;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const R aw0 = mag(Wr[0][j]), awd = mag(Wr[d + 1][j]);
+      W[d][j] = fma(-l, Wr[0][j], Wr[d + 1][j]);
+      rW[d][j] = rWr[d + 1][j] + al * rWr[0][j] + (aw0 + rWr[0][j]) * rl + B::u * (al * aw0 + awd);
+    }
+    W[d][H] = -l;
+    rW[d][H] = rl;
+  }
+#pragma unroll
+  for (int j = 0; j < H; ++j) idx[j] = idx1[j];
+#pragma unroll
+  for (int r = 0; r <= D; ++r) idx[H + r] = ir[r];
+  neg = ng;
+}
+
 // ---------------------------------------------------------------------------
 // Single-matrix prefix kernel.
 // ---------------------------------------------------------------------------
@@ -677,9 +1108,18 @@ __global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(Singl
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.n;
   FpSmem<T> sm(smem_raw, n, M, CS);
-  const ZBuf<T, D> zb(smem_raw + fp_smem_bytes(n, M, CS, sizeof(T), blockDim.x), threadIdx.x, blockDim.x, n - M + D);
+  const ZBuf<T, D> zb(smem_raw + fp_smem_bytes(n, M, CS, sizeof(T), blockDim.x, std::is_same<T, ff>::value),
+                      threadIdx.x, blockDim.x, n - M + D);
   build_binom(sm.binom, n, M);
-  const int escale = stage_scaled<T>(a.A, a.dtype, M, n, a.lda, sm.As, CS, sm.row_exp);
+  bool exact_in;
+  const int escale = stage_scaled<T>(a.A, a.dtype, M, n, a.lda, sm.As, CS, sm.row_exp, &exact_in);
+  const float uin = exact_in ? 0.0f : static_cast<float>(BoundTraits<T>::u_in);
+  if constexpr (!kTerms) {
+    column_norms<T>(sm.As, CS, M, n, sm.colnorm, threadIdx.x, blockDim.x);
+    if constexpr (std::is_same<T, ff>::value)
+      stage_double_copy(sm.As, CS, M, n, sm.As64, ColStride<double, M>::value, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
 
   const int lane = threadIdx.x & 31;
   const unsigned long long gwarp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -724,7 +1164,8 @@ __global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(Singl
 #pragma unroll
       for (int j = 0; j < P - 1; ++j) c[j] = head[j];
       c[P - 1] = v;
-      const bool flag = prefix_one<T, M, D, CS, kTerms>(sm.As, sm.binom, n, v, c, zb, thr, act, sub, lp, acc, ts);
+      const bool flag = prefix_one<T, M, D, CS, kTerms, kMixed>(sm.As, sm.binom, n, v, c, zb, thr, act, sub, lp, acc,
+                                                                 ts, sm.colnorm, uin, sm.As64);
       if constexpr (kMixed && !kTerms) {
         if (act && flag) acc.drop_prefix();  // its leaves are recomputed in binary64
         // every lane of the group drops its share; the first one records the prefix
@@ -758,17 +1199,19 @@ __global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(Singl
       }
     }
     if constexpr (std::is_same<T, float>::value) {
-      block_reduce_ff(acc.tot, acc.tot_abs, fl, sm.scratch);
+      double bnd = static_cast<double>(acc.bnd);
+      block_reduce_ff(acc.tot, acc.tot_abs, fl, bnd, sm.scratch);
       if (threadIdx.x == 0)
         reinterpret_cast<FfPartial*>(a.partials)[blockIdx.x] =
-            FfPartial{acc.tot.hi, acc.tot.lo, acc.tot_abs.hi, acc.tot_abs.lo, fl, 0};
+            FfPartial{acc.tot.hi, acc.tot.lo, acc.tot_abs.hi, acc.tot_abs.lo, fl, bnd, {0, 0}};
       finish_ff_main(a, sm.scratch, escale, M);
     } else {
       acc.finish();
       Dd d = acc.acc;
       double ab = acc.abs_sum;
-      block_reduce_dd(d, ab, fl, sm.scratch);
-      if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{d.hi, d.lo, ab, fl};
+      double bnd = static_cast<double>(acc.bnd);
+      block_reduce_dd(d, ab, fl, bnd, sm.scratch);
+      if (threadIdx.x == 0) a.partials[blockIdx.x] = FpPartial{d.hi, d.lo, ab, fl, bnd, 0.0};
       finish_fp_main<kMixed>(a, sm.scratch, escale, M, tier_of<T, kMixed>());
     }
   }

@@ -59,7 +59,7 @@ def test_struct_layouts_match_header(tmp_path):
         for fname, _ in py._fields_:
             lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
     lines.append('  printf("radic_result size %zu\\n", sizeof(radic_result));')
-    for fname in ["value", "abs_sum", "err_est", "exact_lo", "exact_hi", "minors", "flagged", "status", "n_primes",
+    for fname in ["value", "abs_sum", "err_bound", "exact_lo", "exact_hi", "minors", "flagged", "status", "n_primes",
                   "tier", "exact_exp"]:
         lines.append(f'  printf("radic_result {fname} %zu\\n", offsetof(radic_result, {fname}));')
     lines.append("  return 0;\n}")
@@ -78,7 +78,7 @@ def test_struct_layouts_match_header(tmp_path):
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
     # the binding reads radic_result as 16 eight-byte words (parse_result)
     assert got[("radic_result", "size")] == 8 * L.RESULT_WORDS
-    order = ["value", "abs_sum", "err_est", "exact_lo", "exact_hi", "minors", "flagged", "status", "n_primes", "tier",
+    order = ["value", "abs_sum", "err_bound", "exact_lo", "exact_hi", "minors", "flagged", "status", "n_primes", "tier",
              "exact_exp"]
     for word, fname in enumerate(order):
         assert got[("radic_result", fname)] == 8 * word, fname

@@ -40,7 +40,10 @@ def test_prefix_ops_aggregate_every_prefix_and_leaf(m, n, D):
         "mul": w["prefixes"] * per_prefix_mul + w["cols"] + (3 * w["pairs"] if D == 3 else 0) + w["leaves"],
         "add": 2 * w["leaves"],
     }
-    assert bench.prefix_ops(m, n, D) == want
+    got = bench.prefix_ops(m, n, D)
+    assert (got["all_fma"], got["all_mul"], got["all_add"]) == (want["fma"], want["mul"], want["add"])
+    # the prefix factorisations alone
+    assert (got["pre_fma"], got["pre_mul"]) == (w["prefixes"] * per_prefix_fma, w["prefixes"] * per_prefix_mul)
     assert bench.prefix_flops(m, n, D) == 2 * want["fma"] + want["mul"] + want["add"]
 
 
@@ -62,10 +65,30 @@ def test_prefix_ops_head_sharing_aggregate(m, n, D):
         + w["leaves"],
         "add": 2 * w["leaves"],
     }
-    assert bench.prefix_ops(m, n, D, shared=True) == want
+    got = bench.prefix_ops(m, n, D, shared=True)
+    assert (got["all_fma"], got["all_mul"], got["all_add"]) == (want["fma"], want["mul"], want["add"])
+    assert (got["pre_fma"], got["pre_mul"]) == (heads * per_head_fma + w["prefixes"] * ((D + 1) * H + D * H),
+                                                heads * per_head_mul + w["prefixes"] * (D + 1))
+    # the pair tier: columns, pairs and leaves in binary32 flops of the pair algorithms,
+    # the prefix part in binary64 flops
+    f = bench.pair_flops(m, n, D, shared=True)
+    assert f["fp64"] == 2 * got["pre_fma"] + got["pre_mul"]
+    assert f["fp32"] == 18 * got["fma"] + 10 * got["mul"] + 12 * w["leaves"]
 
 
-def test_headline_flop_count():
-    # the roofline numerator of the 8 x 32 headline (depth 3), as the bench reports it
+def test_single_matrix_flop_count():
+    # the prefix path's flops on the 8 x 32 workload (depth 3)
     assert bench.prefix_flops(8, 32, 3) == 154415430
     assert bench.prefix_ops(8, 32, 3)["add"] == 2 * math.comb(32, 8)
+
+
+@pytest.mark.parametrize("m,n,D,K", [(5, 11, 2, 1), (6, 12, 3, 2), (10, 15, 3, 3), (12, 16, 3, 3)])
+def test_modp_multiplies_aggregate_every_prefix_and_leaf(m, n, D, K):
+    # 32-bit multiplies of the exact prefix path, against a walk over the prefixes
+    w = _walk(m, n, D)
+    P = m - D
+    per_pre = 4 * sum((m - 1 - k) * (P - 1 - k) for k in range(P)) + 3 * (2 * P + D - 1) + 9
+    per_col = 4 * sum(m - 1 - k for k in range(P)) + 5
+    want = K * (w["prefixes"] * per_pre + w["cols"] * per_col + (12 * w["pairs"] if D == 3 else 0)
+                + w["leaves"] * (7 if D == 3 else 4))
+    assert bench.modp_mults(m, n, D, K) == want

@@ -48,6 +48,12 @@ def small_batch(seed, count, max_m=10, max_d=6):
     return mats
 
 
+def assert_bounded(r, exact):
+    """The result's err_bound is an upper bound on its actual error against the exact value."""
+    err = abs(Fraction(r["value"]) - Fraction(exact))
+    assert err <= Fraction(r["err_bound"]), (float(err), r["err_bound"])
+
+
 def run_batch(mats, mode, dtype=np.float64, tuning=None, graph=False):
     data, ms, ns, offs = W.pack_batch(mats, dtype)
     A = torch.from_numpy(data).cuda()
@@ -85,6 +91,9 @@ def test_small_batch_matches_oracle(mode):
         else:
             # small matrices are routed to binary64 by the mixed plan
             assert abs(float(Fraction(r["value"]) - val)) <= 1e-10 * float(abs_sum)
+        assert_bounded(r, val)
+        if mode == "mixed":  # the device check keeps every bound within the plan's target
+            assert r["err_bound"] <= 1e-10 * float(abs_sum) * (1 + 1e-9)
     if mode == "fp64":
         assert info["matrices_fp32"] == 0
 
@@ -108,6 +117,7 @@ def test_batch_with_per_minor_tuning_and_float32_input():
         assert r["tier"] == 1
         m = a.shape[0]
         assert abs(float(Fraction(r["value"]) - val)) <= 8 * m * 2.0 ** -24 * float(abs_sum) * 4
+        assert_bounded(r, val)
 
 
 @pytest.mark.parametrize("depth", [2, 3])
@@ -118,6 +128,7 @@ def test_batch_prefix_depths_match_oracle(depth):
     for a, r in zip(mats, res):
         val, abs_sum = orc.radic_det_exact(a)
         assert abs(Fraction(r["value"]) - val) <= Fraction(1e-12) * abs_sum
+        assert_bounded(r, val)
 
 
 @pytest.mark.parametrize("mode,tiers", [("fp64", None), ("mixed", ["pair"]), ("mixed", ["fp32"])])
@@ -133,6 +144,7 @@ def test_batch_head_sharing_matches_oracle(mode, tiers, head_sharing):
         m = a.shape[0]
         tol = {0: 1e-12, 3: 1e-11}.get(r["tier"], 8 * m * 2.0 ** -24)
         assert abs(float(Fraction(r["value"]) - val)) <= tol * float(abs_sum)
+        assert_bounded(r, val)
 
 
 def test_batch_is_deterministic():
@@ -201,7 +213,7 @@ def _golden(name):
 @pytest.mark.parametrize("mode,dtype,golden,tol", [
     ("mixed", np.float32, "batched_4096_f32", 1e-10),
     ("mixed", np.float64, "batched_4096_f64", 1e-10),
-    ("mixed", np.float32, "batched_4096_f32", 1e-8),
+    ("mixed", np.float32, "batched_4096_f32", 1e-4),
     ("fp64", np.float64, "batched_4096_f64", 1e-12),
 ])
 def test_full_batched_4096(mode, dtype, golden, tol):
@@ -219,27 +231,35 @@ def test_full_batched_4096(mode, dtype, golden, tol):
             assert r["value"] == 0.0 and r["abs_sum"] == 0.0
             continue
         worst = max(worst, abs(r["value"] - w) / s)
-        # the GPU's magnitude sum agrees with the oracle's (binary32 elimination:
-        # each |term| carries its minor's rounding)
-        assert abs(r["abs_sum"] - s) <= (1e-5 if r["tier"] == 1 else 1e-9) * s, (r, s)
+        # the a-posteriori bound holds (against the correctly rounded exact
+        # value, so up to half an ulp of it); in the mixed mode it meets the
+        # target (the device check redoes in binary64 what does not), and
+        # binary64 bounds stay below 1e-10 (the errors themselves are checked
+        # against 1e-12 below)
+        assert abs(r["value"] - w) <= r["err_bound"] + 0.5 * math.ulp(w), (r, w)
+        assert r["err_bound"] <= (tol if mode == "mixed" else 1e-10) * s * (1 + 1e-5), (r, s)
+        # the GPU's magnitude sum agrees with the oracle's: binary64 to 1e-9;
+        # binary32 elimination to 1e-5 (each |term| carries its minor's
+        # rounding); pairs to 1e-6 (their magnitudes are summed in binary32)
+        assert abs(r["abs_sum"] - s) <= {1: 1e-5, 3: 1e-6}.get(r["tier"], 1e-9) * s, (r, s)
     assert worst <= tol, worst
     assert info["matrices_fp32"] + info["matrices_pair"] + info["matrices_fp64"] == len(mats)
     if mode == "mixed":
-        # binary32 when 2.5e-6 / sqrt(C) meets tol, else pairs (m >= 3) when
-        # 1e-11 / sqrt(C) does, else binary64
+        # first tier: binary32 when 1e-4 meets tol, else pairs (m >= 3) when
+        # 2e-11 does, else binary64; the device check then redoes in binary64
+        # every matrix whose bound misses tol
         want32 = want_pair = 0
         for a in mats:
             m, n = a.shape
             if m > n:
                 continue
-            rs = 1.0 / math.sqrt(math.comb(n, m))
-            if 2.5e-6 * rs <= tol:
+            if 1e-4 <= tol:
                 want32 += 1
-            elif m >= 3 and 1e-11 * rs <= tol:
+            elif m >= 3 and 2e-11 <= tol:
                 want_pair += 1
         assert info["matrices_fp32"] == want32
         assert info["matrices_pair"] == want_pair
-        if tol >= 1e-8:
+        if tol >= 1e-4:
             assert want32 > 0
         if tol <= 1e-10:
             assert want_pair > 0
@@ -260,8 +280,11 @@ def test_pair_tier_small_batch_matches_oracle():
         if m > n:
             assert r["value"] == 0.0
             continue
-        assert r["tier"] == (3 if m >= 3 else 0)
+        # pairs for m >= 3, unless the device check redid the matrix in binary64
+        assert r["tier"] in ((3, 0) if m >= 3 else (0,))
         assert abs(float(Fraction(r["value"]) - val)) <= 1e-11 * float(abs_sum)
+        assert_bounded(r, val)
+        assert r["err_bound"] <= 1e-10 * float(abs_sum) * (1 + 1e-9)
 
 
 @pytest.mark.parametrize("depth", [2, 3])
@@ -275,8 +298,9 @@ def test_pair_tier_both_depths(depth):
         val, abs_sum = orc.radic_det_exact(a)
         if a.shape[0] > a.shape[1]:
             continue
-        assert r["tier"] == 3
+        assert r["tier"] in (3, 0)  # pairs, or binary64 after the device check
         assert abs(float(Fraction(r["value"]) - val)) <= 1e-11 * float(abs_sum)
+        assert_bounded(r, val)
 
 
 def test_fp32_only_router_sends_the_rest_to_binary64():
@@ -284,3 +308,51 @@ def test_fp32_only_router_sends_the_rest_to_binary64():
     res, info = run_batch(mats, "mixed", tuning=R().make_tuning(tiers=["fp32"], tol=1e-10))
     assert info["matrices_pair"] == 0
     assert all(r["tier"] in (0, 1) for r in res)
+
+
+def structured_batch(seed):
+    """Inputs on which per-minor rounding errors do not behave like independent
+    random variables: nearly repeated columns, columns equal up to their last
+    bits, low rank plus a small perturbation, and column pairs whose terms
+    cancel across the whole sum."""
+    rng = np.random.default_rng(seed)
+    mats = []
+    for m, n in [(4, 11), (5, 12), (6, 12), (7, 13), (8, 14), (6, 14)]:
+        a = rng.standard_normal((m, n))
+        a[:, 1::3] = a[:, 0:-1:3][:, : a[:, 1::3].shape[1]] + 1e-9 * rng.standard_normal((m, a[:, 1::3].shape[1]))
+        mats.append(a)
+        b = rng.standard_normal((m, n))
+        b[:, 1::2] = b[:, 0:-1:2][:, : b[:, 1::2].shape[1]] * (1.0 + 2.0 ** -40)
+        mats.append(b)
+        r = m - 2
+        c = rng.standard_normal((m, r)) @ rng.standard_normal((r, n)) + 1e-4 * rng.standard_normal((m, n))
+        mats.append(c)
+        half = n // 2
+        d0, d1 = rng.uniform(-1, 1, (m, half)), rng.uniform(-1, 1, (m, half))
+        d = np.empty((m, 2 * half))
+        d[:, 0::2], d[:, 1::2] = d0, d0 + 0.25 * d1
+        mats.append(d)
+    return mats
+
+
+def test_structured_inputs_bound_holds_and_rerouting_keeps_target():
+    # The first tier of every matrix here is pairs of binary32 (tol 1e-10);
+    # the device check sends a matrix to binary64 when its own bound misses
+    # the target.  Every result's bound must hold, and every result must meet
+    # the target, or be a binary64 result whose own bound says why not.
+    mats = structured_batch(11)
+    tol = 1e-10
+    res, info = run_batch(mats, "mixed", tuning=R().make_tuning(tol=tol))
+    assert info["matrices_pair"] == len(mats)
+    rerouted = 0
+    for a, r in zip(mats, res):
+        val, abs_sum = orc.radic_det_exact(a)
+        assert r["status"] == 0
+        assert_bounded(r, val)
+        err = abs(float(Fraction(r["value"]) - val))
+        if r["err_bound"] <= tol * float(abs_sum) * (1 + 1e-9):
+            assert err <= tol * float(abs_sum)
+        else:
+            assert r["tier"] == 0, r
+        rerouted += r["tier"] == 0
+    assert rerouted >= 1

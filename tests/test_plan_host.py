@@ -129,12 +129,12 @@ def _check_batch_tasks(tasks, shapes):
 
 
 def _expected_tier(m, n, tol):
-    # the router's rule: binary32 when 2.5e-6 / sqrt(C) meets tol, pairs (m >= 3)
-    # when 1e-11 / sqrt(C) does, binary64 otherwise
-    c = math.comb(n, m)
-    if 2.5e-6 / math.sqrt(c) <= tol:
+    # the router's first-tier rule: binary32 when its bound envelope 1e-4
+    # meets tol, pairs (m >= 3) when 2e-11 does, binary64 otherwise (the
+    # device then checks each matrix's own bound)
+    if 1e-4 <= tol:
         return 1
-    if m >= 3 and 1e-11 / math.sqrt(c) <= tol:
+    if m >= 3 and 2e-11 <= tol:
         return 3
     return 0
 
