@@ -100,7 +100,20 @@ using Rad = typename BoundTraits<T>::R;
 
 // |x| as a radius-type value (pairs: the leading part, inflated by one
 // binary32 unit to cover the trailing part).
-__device__ __forceinline__ float mag(double x) { return static_cast<float>(fabs(x)); }
+//
+// Binary64: formed on the integer pipe, not by a conversion on the binary64
+// pipe (the scarce unit of binary64 work).  The high word of x holds the
+// exponent and the leading 20 fraction bits; re-biased to binary32 they give
+// |x| truncated to 20 fraction bits, and one unit of the 20th bit more makes
+// it an upper bound within 2^-20 relative.  Zero stays zero; magnitudes
+// below 2^-126 give 2^-126 and magnitudes beyond binary32's range +inf.
+__device__ __forceinline__ float mag(double x) {
+  const unsigned int h = static_cast<unsigned int>(__double2hiint(x)) & 0x7fffffffu;
+  const unsigned int e = h >> 20;  // biased binary64 exponent
+  if (e < 1023u - 126u) return (h | static_cast<unsigned int>(__double2loint(x))) == 0u ? 0.0f : 0x1p-126f;
+  if (e > 1023u + 127u) return __int_as_float(0x7f800000);
+  return __uint_as_float(((h - ((1023u - 127u) << 20)) << 3) + 8u);
+}
 __device__ __forceinline__ float mag(float x) { return fabsf(x); }
 __device__ __forceinline__ float mag(ff x) { return fabsf(x.hi) * (1.0f + 0x1p-23f); }
 

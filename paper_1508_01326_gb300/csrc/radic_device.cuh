@@ -216,6 +216,12 @@ __device__ __forceinline__ uint32_t mag_key(double x) {
 }
 __device__ __forceinline__ uint32_t mag_key(float x) { return __float_as_uint(x) & 0x7fffffffu; }
 
+// |a| > |b| for pivot selection: binary64 by the magnitude keys, binary32
+// directly, pairs by their leading parts.
+__device__ __forceinline__ bool abs_greater(double a, double b) { return mag_key(a) > mag_key(b); }
+__device__ __forceinline__ bool abs_greater(float a, float b) { return fabsf(a) > fabsf(b); }
+__device__ __forceinline__ bool abs_greater(ff a, ff b) { return fabsf(a.hi) > fabsf(b.hi); }
+
 // ---------------------------------------------------------------------------
 // Partial-pivot LU of one m x m minor held in registers (thread mapping).
 // Row exchanges are branch-free compare-and-swap steps that bubble the
@@ -274,7 +280,7 @@ __device__ __forceinline__ T lu_det_b(T (&a)[M][M], T& gmax, float& bnd, bool& b
 #pragma unroll
   for (int i = 0; i < M; ++i)
 #pragma unroll
-    for (int j = 0; j < M; ++j) ra[i][j] = u_in * static_cast<float>(fabs(a[i][j]));
+    for (int j = 0; j < M; ++j) ra[i][j] = u_in * mag(a[i][j]);
   T det = T(1);
   bool neg = false;
   float rel = 0.0f;
@@ -298,7 +304,7 @@ __device__ __forceinline__ T lu_det_b(T (&a)[M][M], T& gmax, float& bnd, bool& b
       neg ^= sw;
     }
     const T piv = a[k][k];
-    const float ap = static_cast<float>(fabs(piv)), rp = ra[k][k];
+    const float ap = mag(piv), rp = ra[k][k];
     const float ipm = ap > 0.0f ? __frcp_ru(ap) : 0.0f;        // 1 / |p|
     const float ipd = ap > rp ? __frcp_ru(__fsub_rd(ap, rp)) : 0.0f;  // 1 / (|p| - r_p)
     if constexpr (sizeof(T) == 8) {
@@ -308,13 +314,13 @@ __device__ __forceinline__ T lu_det_b(T (&a)[M][M], T& gmax, float& bnd, bool& b
         // enclosure of S (the factor covers the binary32 roundings here)
         float h = 1.0f + static_cast<float>(M * M + 4 * M) * 0x1p-23f;
 #pragma unroll
-        for (int kk = 0; kk < k; ++kk) h *= static_cast<float>(fabs(a[kk][kk])) + ra[kk][kk];
+        for (int kk = 0; kk < k; ++kk) h *= mag(a[kk][kk]) + ra[kk][kk];
 #pragma unroll
         for (int j = k; j < M; ++j) {
           float c2 = 0.0f;
 #pragma unroll
           for (int i = k; i < M; ++i) {
-            const float e = static_cast<float>(fabs(a[i][j])) + ra[i][j];
+            const float e = mag(a[i][j]) + ra[i][j];
             c2 = fmaf(e, e, c2);
           }
           h *= sqrtf(c2);
@@ -331,9 +337,9 @@ __device__ __forceinline__ T lu_det_b(T (&a)[M][M], T& gmax, float& bnd, bool& b
       if (pivot_unbounded(ap, rp) || ap == 0.0f) {
         float pr = 1.0f;
 #pragma unroll
-        for (int kk = 0; kk < M - 1; ++kk) pr *= static_cast<float>(fabs(a[kk][kk])) + ra[kk][kk];
+        for (int kk = 0; kk < M - 1; ++kk) pr *= mag(a[kk][kk]) + ra[kk][kk];
         bnd = pr * (ap + rp) * (1.0f + static_cast<float>(M) * u) * 1.0000002f + static_cast<float>(M) * u *
-              static_cast<float>(fabs(det));
+              mag(det);
         return neg ? -det : det;
       }
       rel = fmaf(1.0f + rel, rp * ipm, rel);
@@ -347,21 +353,21 @@ __device__ __forceinline__ T lu_det_b(T (&a)[M][M], T& gmax, float& bnd, bool& b
 #pragma unroll
     for (int i = k + 1; i < M; ++i) {
       const T l = a[i][k] * r;
-      const float al = static_cast<float>(fabs(l));
+      const float al = mag(l);
       const float rl = (ra[i][k] + al * rp) * ipd + c_div * u * al;
 #pragma unroll
       for (int j = k + 1; j < M; ++j) {
-        const float ax = static_cast<float>(fabs(a[k][j])), old = static_cast<float>(fabs(a[i][j]));
+        const float ax = mag(a[k][j]), old = mag(a[i][j]);
         a[i][j] = fma(-l, a[k][j], a[i][j]);
         ra[i][j] += al * ra[k][j] + (ax + ra[k][j]) * rl + u * (al * ax + old);
       }
     }
   }
   rel = fmaf(1.0f + rel, static_cast<float>(M - 1) * u * 1.01f, rel);
-  bnd = rel * static_cast<float>(fabs(det)) * 1.0000001f;
+  bnd = rel * mag(det) * 1.0000001f;
   // a failed pivot: |computed - exact| <= |computed| + |exact|, the latter
   // bounded above (binary64 only; the other arithmetics flag the minor)
-  if (sizeof(T) == 8 && bad) bnd = static_cast<float>(fabs(det)) * 1.0000002f + hs;
+  if (sizeof(T) == 8 && bad) bnd = mag(det) * 1.0000002f + hs;
   return neg ? -det : det;
 }
 

@@ -421,7 +421,7 @@ __device__ __forceinline__ T group_det_b(T (&x)[G], int m, int sub, int seg, T& 
   constexpr float c_div = static_cast<float>(BoundTraits<T>::c_div);
   float rx[G];
 #pragma unroll
-  for (int j = 0; j < G; ++j) rx[j] = u_in * static_cast<float>(fabs(x[j]));
+  for (int j = 0; j < G; ++j) rx[j] = u_in * mag(x[j]);
   bool alive = sub < m;
   T det = T(1);
   int par = 0;
@@ -444,7 +444,7 @@ __device__ __forceinline__ T group_det_b(T (&x)[G], int m, int sub, int seg, T& 
     if (sub == p) alive = false;
     det *= piv;
     gmax = fmax(gmax, fabs(piv));
-    const float ap = static_cast<float>(fabs(piv));
+    const float ap = mag(piv);
     pr *= ap + rp;
     const float ipm = ap > 0.0f ? __frcp_ru(ap) : 0.0f;
     const float ipd = ap > rp ? __frcp_ru(__fsub_rd(ap, rp)) : 0.0f;
@@ -460,14 +460,14 @@ __device__ __forceinline__ T group_det_b(T (&x)[G], int m, int sub, int seg, T& 
     if constexpr (sizeof(T) == 8) r = rcp_f64(piv);
     else r = rcp_f32(piv);
     const T l = alive ? x[k] * r : T(0);
-    const float al = static_cast<float>(fabs(l));
+    const float al = mag(l);
     const float rl = alive ? (rx[k] + al * rp) * ipd + c_div * u * al : 0.0f;
 #pragma unroll
     for (int j = k + 1; j < G; ++j) {
       if (j < m) {
         const T uj = __shfl_sync(kFull, x[j], p, G);
         const float ru = __shfl_sync(kFull, rx[j], p, G);
-        const float au = static_cast<float>(fabs(uj)), old = static_cast<float>(fabs(x[j]));
+        const float au = mag(uj), old = mag(x[j]);
         x[j] = fma(-l, uj, x[j]);
         rx[j] += al * ru + (au + ru) * rl + u * (al * au + old);
       }
@@ -475,8 +475,8 @@ __device__ __forceinline__ T group_det_b(T (&x)[G], int m, int sub, int seg, T& 
   }
   rel = fmaf(1.0f + rel, static_cast<float>(m - 1) * u * 1.01f, rel);
   bnd = last_open ? (pr * (1.0f + static_cast<float>(m) * u) + static_cast<float>(m) * u *
-                                                                      static_cast<float>(fabs(det))) * 1.0000002f
-                  : rel * static_cast<float>(fabs(det)) * 1.0000001f;
+                                                                      mag(det)) * 1.0000002f
+                  : rel * mag(det) * 1.0000001f;
   return par ? -det : det;
 }
 
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_group(SingleArgs a) {
 #pragma unroll
           for (int j = 0; j < G; ++j)
             if (j < m) h *= static_cast<float>(sm.colnorm[c[j]]);
-          b = static_cast<float>(fabs(det)) * 1.0000002f + h;
+          b = mag(det) * 1.0000002f + h;
         }
       }
       if (sign_negative_dyn<G>(c, m)) det = -det;

@@ -145,7 +145,7 @@ __device__ __forceinline__ void prefix_factor(const T* __restrict__ As, const in
   for (int k = 0; k < P; ++k) {
 #pragma unroll
     for (int i = k + 1; i < M; ++i) {
-      const bool sw = fabs(a[i][k]) > fabs(a[k][k]);
+      const bool sw = abs_greater(a[i][k], a[k][k]);
 #pragma unroll
       for (int j = 0; j < P; ++j) {
         const T x = a[k][j], y = a[i][j];
@@ -226,7 +226,7 @@ __device__ __forceinline__ void prefix_factor_b(const S* __restrict__ As, const 
   for (int k = 0; k < P; ++k) {
 #pragma unroll
     for (int i = k + 1; i < M; ++i) {
-      const bool sw = fabs(a[i][k]) > fabs(a[k][k]);
+      const bool sw = abs_greater(a[i][k], a[k][k]);
 #pragma unroll
       for (int j = 0; j < P; ++j) {
         const T x = a[k][j], y = a[i][j];
@@ -944,7 +944,7 @@ __device__ __forceinline__ void prefix_extend(const T* __restrict__ As, int v, c
   bool ng = neg1;
 #pragma unroll
   for (int r = 1; r <= D; ++r) {
-    const bool sw = fabs(s[r]) > fabs(s[0]);
+    const bool sw = abs_greater(s[r], s[0]);
     const T a0 = s[0], ar = s[r];
     s[0] = sw ? ar : a0;
     s[r] = sw ? a0 : ar;
@@ -1032,7 +1032,7 @@ __device__ __forceinline__ void prefix_extend_b(const S* __restrict__ As, int v,
   bool ng = neg1;
 #pragma unroll
   for (int r = 1; r <= D; ++r) {
-    const bool sw = fabs(s[r]) > fabs(s[0]);
+    const bool sw = abs_greater(s[r], s[0]);
     const T a0 = s[0], ar = s[r];
     s[0] = sw ? ar : a0;
     s[r] = sw ? a0 : ar;
