@@ -157,8 +157,11 @@ def prefix_ops(m: int, n: int, D: int, shared: bool = False) -> dict:
     update of W, one multiply into the pivot product.
 
     Returns the counts split into the prefix part ("pre_fma", "pre_mul":
-    factorisations, extensions) and the rest ("fma", "mul", "add": columns,
-    column pairs, leaves), plus their totals under "all_*".
+    factorisations, extensions; "upd_fma": the share of pre_fma in the
+    extensions' D x H update of W, which the pair tier runs in pairs of
+    binary32)
+    and the rest ("fma", "mul", "add": columns, column pairs, leaves), plus
+    their totals under "all_*".
     """
     P = m - D
     pre = {"fma": sum((m - k - 1) * (P - k - 1) for k in range(P)) + D * P * (P - 1) // 2,
@@ -166,7 +169,7 @@ def prefix_ops(m: int, n: int, D: int, shared: bool = False) -> dict:
     col = {"fma": D * P, "mul": 1}
     pair = {"fma": 3, "mul": 3} if D == 3 else {"fma": 0, "mul": 0}
     leaf = {"fma": D - 1, "mul": 1, "add": 2}
-    tot = {"pre_fma": 0, "pre_mul": 0, "fma": 0, "mul": 0, "add": 0}
+    tot = {"pre_fma": 0, "pre_mul": 0, "upd_fma": 0, "fma": 0, "mul": 0, "add": 0}
 
     def body(cnt, k):
         tot["fma"] += cnt * (k * col["fma"] + math.comb(k, 2) * pair["fma"] + math.comb(k, D) * leaf["fma"])
@@ -185,6 +188,7 @@ def prefix_ops(m: int, n: int, D: int, shared: bool = False) -> dict:
             for v in range(u + 1, n - D):
                 tot["pre_fma"] += cnt * ext["fma"]
                 tot["pre_mul"] += cnt * ext["mul"]
+                tot["upd_fma"] += cnt * D * H
                 body(cnt, n - 1 - v)
     else:
         for v in range(P - 1, n - D):
@@ -212,12 +216,13 @@ PAIR_FMA, PAIR_MUL, PAIR_ADD = 18, 10, 11
 
 def pair_flops(m: int, n: int, D: int, shared: bool = False) -> dict:
     """The pair tier's work: binary32 flops (pair algorithms) of the columns,
-    column pairs and leaves on the binary32 pipe, and the binary64 flops of
-    the prefix factorisations (or heads and extensions) on the binary64 pipe."""
+    column pairs and leaves, and with head sharing of the extensions' W
+    updates, on the binary32 pipe; the binary64 flops of the rest of the
+    prefix factorisations (heads, extensions) on the binary64 pipe."""
     c = prefix_ops(m, n, D, shared)
     leaves = c["add"] // 2
-    return {"fp32": PAIR_FMA * c["fma"] + PAIR_MUL * c["mul"] + PAIR_ADD * leaves + leaves,
-            "fp64": 2 * c["pre_fma"] + c["pre_mul"]}
+    return {"fp32": PAIR_FMA * (c["fma"] + c["upd_fma"]) + PAIR_MUL * c["mul"] + PAIR_ADD * leaves + leaves,
+            "fp64": 2 * (c["pre_fma"] - c["upd_fma"]) + c["pre_mul"]}
 
 
 def modp_mults(m: int, n: int, D: int, primes: int) -> int:

@@ -47,6 +47,8 @@ extern "C" {
 #define RADIC_MAX_M 32
 #define RADIC_MAX_N 64
 #define RADIC_MAX_PRIMES 4
+#define RADIC_WIDE_MAX_PRIMES 32
+#define RADIC_WIDE_LIMBS 32
 
 /* Status codes (return values and radic_result.status). */
 enum {
@@ -77,7 +79,9 @@ enum { RADIC_I8 = 0, RADIC_I32 = 1, RADIC_F32 = 2, RADIC_F64 = 3 };
  *           result is the integer times 2^exact_exp, exact_exp = sum_i e_i.
  *           Inputs with many significant bits per row (for instance random
  *           binary64 values) exceed the prime budget: status
- *           RADIC_EOVERFLOW.  A non-finite entry: status RADIC_EINVAL.
+ *           RADIC_EOVERFLOW; radic_det_exact_wide takes up to
+ *           RADIC_WIDE_MAX_PRIMES primes for them.  A non-finite entry:
+ *           status RADIC_EINVAL.
  *  PAIR  -- the MIXED scheme with the elimination carried out in pairs of
  *           binary32 numbers (hi + lo, about 48 significant bits, on the
  *           binary32 pipe): PREFIX mapping, 3 <= m <= 10; flagged prefixes
@@ -159,6 +163,22 @@ typedef struct radic_result {
   int64_t reserved[5];
 } radic_result;
 
+/* Device-resident result of radic_det_exact_wide (192 bytes). */
+typedef struct radic_wide_result {
+  double value;      /* det_R(A) rounded to binary64 (within one unit in the
+                        last place; +-inf beyond binary64's range)          */
+  int64_t status;    /* RADIC_OK, RADIC_EOVERFLOW (the bound needs more than
+                        RADIC_WIDE_MAX_PRIMES primes), RADIC_EINVAL (an
+                        entry is not finite)                                 */
+  int64_t n_primes;  /* primes used                                          */
+  int64_t exact_exp; /* det_R(A) = sign * magnitude * 2^exact_exp            */
+  int64_t sign;      /* -1, 0 or +1                                          */
+  int64_t n_limbs;   /* limbs holding the magnitude (the others are 0)       */
+  int64_t minors;    /* C(n, m), or 0 when m > n                             */
+  int64_t reserved;
+  uint32_t limbs[RADIC_WIDE_LIMBS]; /* magnitude = sum_i limbs[i] 2^(32 i)   */
+} radic_wide_result;
+
 /* ---- general ------------------------------------------------------------ */
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -221,6 +241,25 @@ int radic_prefix_plan_host(int m, int n, int mode, const radic_options* opts, in
 int radic_det(const void* A, int m, int n, int64_t lda, int dtype, int mode,
               const radic_options* opts, radic_result* out, void* workspace,
               size_t workspace_bytes, void* stream);
+
+/* EXACT det_R(A) (Definition 3, Eq. (1)) beyond the 128-bit range of
+ * radic_det: the same modular elimination and row scaling as RADIC_MODE_EXACT
+ * (integer inputs, and binary32/binary64 inputs as the dyadic rationals
+ * they are), with as many 31-bit primes as the Hadamard bound of the scaled
+ * integer rows needs, up to RADIC_WIDE_MAX_PRIMES (about 990 bits).  The
+ * primes are taken RADIC_MAX_PRIMES per pass of the EXACT kernels (passes
+ * whose primes the bound does not need return at once), and a last kernel
+ * rebuilds the integer by mixed-radix (Garner) reconstruction into base-2^32
+ * limbs.  Not a computation of the paper: its extension of the exact mode to
+ * inputs whose value does not fit 128 bits.
+ * A: device, row-major m x n, leading dimension lda; out: device;
+ * workspace: device, 256-byte aligned, radic_wide_workspace_bytes(m, n,
+ * opts) bytes.  Options as radic_det's (mapping, threads, prefix depth).
+ * Errors: RADIC_EINVAL (m or n out of range, lda < n, NULL pointers, unknown
+ * dtype), RADIC_EWORKSPACE, RADIC_ECUDA; device: out->status. */
+size_t radic_wide_workspace_bytes(int m, int n, const radic_options* opts);
+int radic_det_exact_wide(const void* A, int m, int n, int64_t lda, int dtype, const radic_options* opts,
+                         radic_wide_result* out, void* workspace, size_t workspace_bytes, void* stream);
 
 /* The signed terms (-1)^(r+s) det(A[:, J_q]) of Eq. (1) for the consecutive
  * dictionary ranks q = q0 .. q0+count-1 (all < C(n,m)), computed by the same
@@ -313,15 +352,19 @@ int radic_batch_plan_destroy(radic_batch_plan* plan);
 /* Host-only view of the tasks radic_batch_plan_create would make for the
  * same arguments (routing, task split and task order), without a GPU: the
  * Section 5 split of each matrix's ranks into contiguous runs, one run per
- * lane, 32 lanes per task.  tasks (host, capacity rows of eight int64):
- * matrix b, tier (RADIC_MODE_MIXED for binary32, _PAIR, _FP64), kind (0: per
- * minor, else the prefix depth D), shared (1: units are heads, the first
- * m-D-1 prefix columns), group (last prefix or head column; 0 per minor),
- * r0 (first unit of lane 0), run (units per lane), lim (end of the group's
- * unit range: C(v, m-D-1) prefixes, C(u, m-D-2) heads or C(n,m) ranks).
- * Lane l of a task takes units [r0 + l*run, min(r0 + (l+1)*run, lim)).
- * *n_tasks receives the total; rows past capacity are not written.  Errors
- * as radic_batch_plan_create's planning (RADIC_EINVAL, RADIC_EUNSUPPORTED). */
+ * lane, 32 lanes per task.  tasks (host, capacity rows of
+ * RADIC_BATCH_TASK_FIELDS int64): matrix b, tier (RADIC_MODE_MIXED for
+ * binary32, _PAIR, _FP64), kind (0: per minor, else the prefix depth D),
+ * shared (1: units are heads, the first m-D-1 prefix columns), group (last
+ * prefix or head column; 0 per minor), r0 (first unit of lane 0), run (units
+ * per lane), lim (end of the unit range: C(v, m-D-1) prefixes, C(u, m-D-2)
+ * heads or C(n,m) ranks), then for head-shared tasks the segment of each
+ * head's last prefix columns the task covers, vlo and vhi (last columns in
+ * [vlo, vhi]); zeros otherwise.  Lane l of a task takes units
+ * [r0 + l*run, min(r0 + (l+1)*run, lim)).  *n_tasks receives the total; rows
+ * past capacity are not written.  Errors as radic_batch_plan_create's
+ * planning (RADIC_EINVAL, RADIC_EUNSUPPORTED). */
+#define RADIC_BATCH_TASK_FIELDS 10
 int radic_batch_plan_tasks_host(const int32_t* m, const int32_t* n, const int64_t* offsets, int batch, int mode,
                                 const radic_batch_tuning* tuning, int64_t* tasks, int64_t capacity,
                                 int64_t* n_tasks);
@@ -349,7 +392,11 @@ int radic_batch_upload(const radic_batch_plan* plan, void* workspace, size_t wor
 
 /* det_R of every matrix of the batch.  A: device, packed matrices of type
  * dtype; out: device, `batch` radic_result; workspace: uploaded with
- * radic_batch_upload.  Calls on the same workspace must not overlap. */
+ * radic_batch_upload.  Calls on the same workspace must not overlap.  The
+ * per-group kernels of each phase run concurrently on `stream` and two
+ * streams the plan owns (joined back into `stream` before the call's later
+ * work); calls with one plan must therefore be issued from one host thread
+ * at a time.  Stream capture records the same fork and join. */
 int radic_det_batched(const radic_batch_plan* plan, const void* A, int dtype, radic_result* out, void* workspace,
                       size_t workspace_bytes, void* stream);
 

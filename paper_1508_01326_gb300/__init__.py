@@ -13,11 +13,14 @@ from .api import (  # noqa: F401
     BatchPlan,
     DetGraph,
     det,
+    det_exact_wide,
     make_tuning,
     parse_results,
     new_result,
     parse_result,
+    parse_wide_result,
     radic_det,
+    radic_det_exact_wide,
     radic_plan_info,
     prefix_plan_host,
     batch_tasks_host,

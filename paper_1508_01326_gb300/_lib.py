@@ -10,6 +10,8 @@ LIB_PATH = os.path.join(HERE, "libradic.so")
 RADIC_MAX_M = 32
 RADIC_MAX_N = 64
 RADIC_MAX_PRIMES = 4
+RADIC_WIDE_MAX_PRIMES = 32
+RADIC_WIDE_LIMBS = 32
 
 STATUS = {0: "RADIC_OK", 1: "RADIC_EINVAL", 2: "RADIC_EOVERFLOW", 3: "RADIC_ECUDA", 4: "RADIC_ETIMEOUT",
           5: "RADIC_EWORKSPACE", 6: "RADIC_EUNSUPPORTED"}
@@ -118,6 +120,8 @@ def _declare_optional(L: ctypes.CDLL) -> None:
         "radic_det_backward": ([vp, i32, i32, i32, i64, i64, vp, vp, vp, sz, vp], i32),
         "radic_det_backward_mode": ([vp, i32, i32, i32, i64, i64, vp, vp, vp, sz, i32, vp], i32),
         "radic_det_noalloc": ([vp, i32, i32, i64, i32, vp, vp, vp], i32),
+        "radic_wide_workspace_bytes": ([i32, i32, ctypes.POINTER(RadicOptions)], sz),
+        "radic_det_exact_wide": ([vp, i32, i32, i64, i32, ctypes.POINTER(RadicOptions), vp, vp, sz, vp], i32),
     }
     for name, (args, res) in table.items():
         fn = getattr(L, name, None)

@@ -6,6 +6,7 @@ the library is missing or CUDA is unavailable these functions raise.
 from __future__ import annotations
 
 import ctypes
+import struct
 from fractions import Fraction
 from typing import Optional
 
@@ -182,6 +183,53 @@ def det(A, mode="fp64", options=None, stream=None) -> dict:
     return res
 
 
+WIDE_RESULT_BYTES = 64 + 4 * L.RADIC_WIDE_LIMBS
+
+
+def radic_det_exact_wide(A: torch.Tensor, options=None, out: Optional[torch.Tensor] = None,
+                         workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Enqueues the exact det_R(A) with up to RADIC_WIDE_MAX_PRIMES primes (radic_det_exact_wide);
+    returns the device radic_wide_result buffer (not synchronised)."""
+    _check_matrix(A)
+    m, n = A.shape
+    lib = L.lib()
+    if out is None:
+        out = torch.zeros(WIDE_RESULT_BYTES, dtype=torch.uint8, device=A.device)
+    ws_bytes = int(lib.radic_wide_workspace_bytes(int(m), int(n), _opts(options)))
+    if workspace is None:
+        workspace = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=A.device)
+    rc = lib.radic_det_exact_wide(A.data_ptr(), int(m), int(n), int(A.stride(0)), _TORCH_DTYPES[A.dtype],
+                                  _opts(options), out.data_ptr(), workspace.data_ptr(), workspace.numel(),
+                                  _stream(stream))
+    L.check("radic_det_exact_wide", rc)
+    return out
+
+
+def parse_wide_result(buf: torch.Tensor) -> dict:
+    """Host dictionary of a radic_wide_result buffer: the fields, the signed integer and the exact
+    value as a Fraction (integer times 2^exact_exp)."""
+    raw = buf.detach().to("cpu").contiguous().view(torch.uint8).numpy().tobytes()
+    value, status, n_primes, exact_exp, sign, n_limbs, minors, _ = struct.unpack_from("<d7q", raw, 0)
+    limbs = struct.unpack_from(f"<{L.RADIC_WIDE_LIMBS}I", raw, 64)
+    mag = 0
+    for i in reversed(range(L.RADIC_WIDE_LIMBS)):
+        mag = (mag << 32) | limbs[i]
+    integer = sign * mag
+    return {"value": value, "status": status, "n_primes": n_primes, "exact_exp": exact_exp, "sign": sign,
+            "n_limbs": n_limbs, "minors": minors, "integer": integer,
+            "value_exact": Fraction(integer) * (Fraction(2) ** exact_exp)}
+
+
+def det_exact_wide(A, options=None, stream=None) -> dict:
+    """Convenience call of the wide exact mode: host (numpy) or device input, synchronises."""
+    if isinstance(A, np.ndarray):
+        A = torch.from_numpy(np.ascontiguousarray(A)).to("cuda")
+    res = parse_wide_result(radic_det_exact_wide(A, options=options, stream=stream))
+    if res["status"] != 0:
+        raise L.RadicError("radic_det_exact_wide (device)", res["status"])
+    return res
+
+
 # ---------------------------------------------------------------------------
 # Batches of matrices of uneven shape
 # ---------------------------------------------------------------------------
@@ -219,7 +267,7 @@ def make_tuning(kind=None, task_cost=None, tol=0.0, growth_threshold=0.0, blocks
     return t
 
 
-BATCH_TASK_KEYS = ["b", "tier", "kind", "shared", "group", "r0", "run", "lim"]
+BATCH_TASK_KEYS = ["b", "tier", "kind", "shared", "group", "r0", "run", "lim", "vlo", "vhi"]
 
 
 def batch_tasks_host(shapes, mode="mixed", tuning=None) -> list:
@@ -239,10 +287,11 @@ def batch_tasks_host(shapes, mode="mixed", tuning=None) -> list:
     total = ctypes.c_int64(0)
     L.check("radic_batch_plan_tasks_host",
             lib.radic_batch_plan_tasks_host(ms, ns, off, batch, _mode(mode), tun, None, 0, ctypes.byref(total)))
-    buf = (ctypes.c_int64 * (8 * max(total.value, 1)))()
+    F = len(BATCH_TASK_KEYS)
+    buf = (ctypes.c_int64 * (F * max(total.value, 1)))()
     L.check("radic_batch_plan_tasks_host",
             lib.radic_batch_plan_tasks_host(ms, ns, off, batch, _mode(mode), tun, buf, total.value, ctypes.byref(total)))
-    return [dict(zip(BATCH_TASK_KEYS, [int(x) for x in buf[8 * i:8 * i + 8]])) for i in range(total.value)]
+    return [dict(zip(BATCH_TASK_KEYS, [int(x) for x in buf[F * i:F * i + F]])) for i in range(total.value)]
 
 
 class BatchPlan:

@@ -2,10 +2,13 @@
 
     python -m paper_1508_01326_gb300.cli --workload fp64_8x32 --mode mixed --reps 3
     python -m paper_1508_01326_gb300.cli --batched-m 10 --mode mixed --tol 1e-10 --reps 2
+    python -m paper_1508_01326_gb300.cli --backward --batch 32 --mode fp64 --reps 1
 
 Prints the parsed result and the CUDA-event time of each repetition.  Useful
 as a small, self-contained target for profilers.  With --batched-m the run
-is the batched path over the matrices with that m of the 4096-matrix batch.
+is the batched path over the matrices with that m of the 4096-matrix batch;
+with --backward it is the gradient kernel over the first --batch matrices of
+the 256 x 6 x 28 workload with grad_out = 1.
 """
 from __future__ import annotations
 
@@ -49,6 +52,24 @@ def run_batched(args) -> None:
     plan.close()
 
 
+def run_backward(args) -> None:
+    from .autograd import radic_det_backward
+
+    A = torch.from_numpy(np.ascontiguousarray(W.diff_256x6x28()[: args.batch])).cuda()
+    g = torch.ones(A.shape[0], dtype=torch.float64, device="cuda")
+    mode = args.mode if args.mode in ("fp64", "pair") else "fp64"
+    times = []
+    for _ in range(args.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        grad = radic_det_backward(A, g, mode=mode)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    print(json.dumps({"backward": list(A.shape), "mode": mode, "ms": times,
+                      "grad_abs_max": float(grad.abs().max().item())}))
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="fp64_8x32", choices=sorted(WORKLOADS))
@@ -61,10 +82,15 @@ def main() -> None:
     ap.add_argument("--depth", type=int, default=0, help="prefix depth (0: library default)")
     ap.add_argument("--batched-m", type=int, default=0, help="batched path over this m of the 4096 batch")
     ap.add_argument("--tol", type=float, default=1e-10, help="batched MIXED router tolerance")
+    ap.add_argument("--backward", action="store_true", help="gradient kernel over the 6 x 28 workload")
+    ap.add_argument("--batch", type=int, default=32, help="matrices of the 256 x 6 x 28 workload (--backward)")
     args = ap.parse_args()
     from . import build as B
 
     B.build()
+    if args.backward:
+        run_backward(args)
+        return
     if args.batched_m:
         run_batched(args)
         return

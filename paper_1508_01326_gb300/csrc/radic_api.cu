@@ -505,6 +505,53 @@ int radic_det(const void* A, int m, int n, int64_t lda, int dtype, int mode, con
   return r;
 }
 
+size_t radic_wide_workspace_bytes(int m, int n, const radic_options* opts) {
+  SinglePlan p;
+  const unsigned long long total = (m >= 1 && n >= 1 && m <= n && n <= kMaxN) ? binom_host(n, m) : 0ull;
+  if (make_plan(m, n, kModeExact, opts, total, &p) != RADIC_OK) return 0;
+  // the EXACT workspace, then the residues of every pass (kWidePrimes words,
+  // then needed, exponent and status)
+  return align_up(p.ws_bytes, 256) + 256;
+}
+
+int radic_det_exact_wide(const void* A, int m, int n, int64_t lda, int dtype, const radic_options* opts,
+                         radic_wide_result* out, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!A || !out || lda < n || !valid_dtype(dtype)) return RADIC_EINVAL;
+  SinglePlan p;
+  const unsigned long long total = (m >= 1 && n >= 1 && m <= n && n <= kMaxN) ? binom_host(n, m) : 0ull;
+  const int rc = make_plan(m, n, kModeExact, opts, total, &p);
+  if (rc != RADIC_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p.total == 0) return launch_wide_crt(nullptr, out, 0ull, s);
+  const size_t off_wide = align_up(p.ws_bytes, 256);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u) || workspace_bytes < off_wide + 256)
+    return RADIC_EWORKSPACE;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  uint32_t* wide = reinterpret_cast<uint32_t*>(ws + off_wide);
+  for (int base = 0; base < kWidePrimes; base += kMaxPrimes) {
+    if (cudaMemsetAsync(ws, 0, 256, s) != cudaSuccess) return RADIC_ECUDA;
+    SingleArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.A = A;
+    a.lda = lda;
+    a.dtype = dtype;
+    a.m = m;
+    a.n = n;
+    a.ranks_per_task = p.ranks_per_task;
+    a.total = p.total;
+    a.tasks = p.tasks;
+    a.growth = p.growth;
+    a.n_warps = p.blocks * p.threads / 32;
+    a.hdr = reinterpret_cast<WsHeader*>(ws);
+    a.modp_partials = reinterpret_cast<uint32_t*>(ws + p.off_modp);
+    a.prime_base = base;
+    a.wide = wide;
+    const int r = launch_modp(p, a, s);
+    if (r != RADIC_OK) return r;
+  }
+  return launch_wide_crt(wide, out, p.total, s);
+}
+
 int radic_terms(const void* A, int m, int n, int64_t lda, int dtype, int mode, const radic_options* opts,
                 uint64_t q0, uint64_t count, void* terms, void* stream) {
   if (!A || !terms || lda < n || !valid_dtype(dtype)) return RADIC_EINVAL;

@@ -47,6 +47,23 @@ struct radic_batch_plan {
   int launches = 0;                      // kernel launches per call
   int dom_queue = -1, dom_group = -1;    // the low-tier kernel with the most estimated work
   void* events = nullptr;                // optional cudaEvent_t[2] around it
+  // launch order of the per-group kernels, most estimated work first:
+  // (queue, group) of the low tiers, groups of the binary64 kernels
+  std::vector<std::pair<int, int>> order_low;
+  std::vector<int> order64;
+  // the per-group kernels of one phase run concurrently on the caller's
+  // stream and kAux more (fork and join by events), so that a kernel's tail,
+  // when its work queue runs dry, is filled by the next kernel's blocks
+  static constexpr int kAux = 2;
+  cudaStream_t aux[kAux] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[kAux] = {nullptr, nullptr};
+  ~radic_batch_plan() {
+    for (int i = 0; i < kAux; ++i) {
+      if (aux[i]) cudaStreamDestroy(aux[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+  }
 };
 
 struct radic_batch_graph {
@@ -58,16 +75,36 @@ namespace {
 
 double cost_minor(int m) { return 10.0 * m * m * m / 3.0 + 40.0; }
 
-// Cost of one head (H = m-D-1 columns, last column u): its factorisation,
-// then per appended column v one elimination step and the prefix's leaves.
-double head_cost(int m, int D, int n, int u) {
+// Cost of one head (H = m-D-1 columns) whose last prefix columns run over
+// [v0, v1]: its factorisation, then per appended column v one elimination
+// step and the prefix's leaves.
+double head_cost(int m, int D, int n, int v0, int v1) {
   const int H = m - D - 1, P = m - D;
   double c = (double)m * H * H;
-  for (int v = u + 1; v <= n - 1 - D; ++v) {
-    const int k = n - 1 - v;
-    c += m + 4.0 * (D + 1) * H + prefix_cost(m, D, k) - (double)m * P * P;
-  }
+  for (int v = v0; v <= v1; ++v) c += m + 4.0 * (D + 1) * H + prefix_cost(m, D, n - 1 - v) - (double)m * P * P;
   return c;
+}
+
+// Minors one lane works for one unit of a head-shared task at most (a single
+// prefix, up to C(n-m+D, D) minors, is never split): a head's whole subtree
+// holds up to C(n-m+1, D+1) minors, and the longest unit sets the kernel's
+// critical path.
+constexpr unsigned long long kSegmentMinors = 4096;
+
+// Splits the last columns v = u+1 .. n-1-D of the heads with last column u
+// into consecutive ranges of at most kSegmentMinors minors.
+std::vector<std::pair<int, int>> head_segments(int n, int D, int u) {
+  std::vector<std::pair<int, int>> out;
+  const int ve = n - 1 - D;
+  int v = u + 1;
+  while (v <= ve) {
+    int v1 = v;
+    unsigned long long sm = binom_host(n - 1 - v, D);
+    while (v1 + 1 <= ve && sm + binom_host(n - 2 - v1, D) <= kSegmentMinors) sm += binom_host(n - 1 - ++v1, D);
+    out.push_back({v, v1});
+    v = v1 + 1;
+  }
+  return out;
 }
 
 int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* tun) {
@@ -93,21 +130,28 @@ int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* 
   // columns, where heads are few and their work uneven).
   const bool share = kind != kKindMinor && m - kind - 1 >= 5 && !(tun && tun->head_sharing < 0);
   if (share) {
-    // head-shared tasks: group u = last head column, C(u, H-1) heads each
+    // head-shared tasks: group u = last head column, C(u, H-1) heads each,
+    // one task list per segment of the heads' last columns
     const int D = kind, H = m - D - 1;
     t.shared = 1;
     for (int u = H - 1; u <= n - 2 - D; ++u) {
       const unsigned long long cnt = binom_host(u, H - 1);
-      const double c = head_cost(m, D, n, u);
-      unsigned long long run = (unsigned long long)std::max(1.0, std::floor(lane_cost / c));
-      run = std::min(run, (cnt + 31) / 32);
-      if (run < 1) run = 1;
-      for (unsigned long long r0 = 0; r0 < cnt; r0 += 32 * run) {
-        t.v = u;
-        t.r0 = r0;
-        t.run = run;
-        t.lim = cnt;
-        out.push_back(t);
+      for (const auto& sg : head_segments(n, D, u)) {
+        const double c = head_cost(m, D, n, sg.first, sg.second);
+        unsigned long long run = (unsigned long long)std::max(1.0, std::floor(lane_cost / c));
+        run = std::min(run, (cnt + 31) / 32);
+        if (run < 1) run = 1;
+        t.vlo = sg.first;
+        t.vhi = sg.second;
+        t.per_unit = 0;
+        for (int v = sg.first; v <= sg.second; ++v) t.per_unit += binom_host(n - 1 - v, D);
+        for (unsigned long long r0 = 0; r0 < cnt; r0 += 32 * run) {
+          t.v = u;
+          t.r0 = r0;
+          t.run = run;
+          t.lim = cnt;
+          out.push_back(t);
+        }
       }
     }
   } else if (kind != kKindMinor) {
@@ -118,6 +162,7 @@ int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* 
       unsigned long long run = (unsigned long long)std::max(1.0, std::floor(lane_cost / c));
       run = std::min(run, (cnt + 31) / 32);
       if (run < 1) run = 1;
+      t.per_unit = binom_host(n - 1 - v, D);
       for (unsigned long long r0 = 0; r0 < cnt; r0 += 32 * run) {
         t.v = v;
         t.r0 = r0;
@@ -131,6 +176,7 @@ int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* 
     unsigned long long run = (unsigned long long)std::max(1.0, std::floor(lane_cost / cost_minor(m)));
     run = std::min(run, (total + 31) / 32);
     if (run < 1) run = 1;
+    t.per_unit = 1;
     for (unsigned long long r0 = 0; r0 < total; r0 += 32 * run) {
       t.v = 0;
       t.r0 = r0;
@@ -143,7 +189,7 @@ int make_tasks(radic_batch_plan& pl, int b, int tier, const radic_batch_tuning* 
 }
 
 double task_cost(const BatchTask& t) {
-  if (t.kind != kKindMinor && t.shared) return (double)t.run * head_cost(t.m, t.kind, t.n, t.v);
+  if (t.kind != kKindMinor && t.shared) return (double)t.run * head_cost(t.m, t.kind, t.n, t.vlo, t.vhi);
   if (t.kind != kKindMinor) return (double)t.run * prefix_cost(t.m, t.kind, t.n - 1 - t.v);
   return (double)t.run * cost_minor(t.m);
 }
@@ -187,31 +233,50 @@ int enqueue(const radic_batch_plan* pl, const void* A, int dtype, radic_result* 
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (ev && cudaStreamIsCapturing(s, &cap) != cudaSuccess) return RADIC_ECUDA;
   const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
-  auto launch = [&](int queue, int g, int slice) {
+  // the caller's stream and the plan's auxiliary streams; kernel i of a
+  // phase goes to stream i mod (kAux + 1)
+  cudaStream_t lanes[radic_batch_plan::kAux + 1] = {s, pl->aux[0], pl->aux[1]};
+  const int nl = pl->fork ? radic_batch_plan::kAux + 1 : 1;
+  auto fork = [&]() {
+    if (nl == 1) return true;
+    if (cudaEventRecord(pl->fork, s) != cudaSuccess) return false;
+    for (int i = 1; i < nl; ++i)
+      if (cudaStreamWaitEvent(lanes[i], pl->fork, 0) != cudaSuccess) return false;
+    return true;
+  };
+  auto join = [&]() {
+    for (int i = 1; i < nl; ++i) {
+      if (cudaEventRecord(pl->join[i - 1], lanes[i]) != cudaSuccess) return false;
+      if (cudaStreamWaitEvent(s, pl->join[i - 1], 0) != cudaSuccess) return false;
+    }
+    return true;
+  };
+  auto launch = [&](int queue, int g, int slice, cudaStream_t st) {
     a.group = g;
     a.queue = queue;
     a.slice_bytes = slice;
     void* params[] = {&a};
     const bool dom = ev && queue == pl->dom_queue && g == pl->dom_group;
-    if (dom && cudaEventRecordWithFlags(ev[0], s, ev_flags) != cudaSuccess) return false;
+    if (dom && cudaEventRecordWithFlags(ev[0], st, ev_flags) != cudaSuccess) return false;
     if (cudaLaunchKernel(group_kernel(queue, g), dim3(pl->blocks[queue][g]), dim3(kBatchThreads), params,
-                         (size_t)slice * (kBatchThreads / 32), s) != cudaSuccess)
+                         (size_t)slice * (kBatchThreads / 32), st) != cudaSuccess)
       return false;
-    return !dom || cudaEventRecordWithFlags(ev[1], s, ev_flags) == cudaSuccess;
+    return !dom || cudaEventRecordWithFlags(ev[1], st, ev_flags) == cudaSuccess;
   };
-  // binary32 and pair tiers, one persistent kernel per tier and group present
-  for (int g = 0; g < kGroups; ++g) {
-    const int m = g / kPaths;
+  // binary32 and pair tiers, one persistent kernel per tier and group
+  // present, most work first
+  if (!fork()) return RADIC_ECUDA;
+  int li = 0;
+  for (const auto& qg : pl->order_low) {
+    const int queue = qg.first, g = qg.second, m = g / kPaths;
     a.flag_base = pl->g32[g];
     a.begin64 = pl->g64[g];
     a.end64 = pl->g64[g + 1];
-    a.begin32 = pl->g32[g];
-    a.end32 = pl->gpair[g];
-    if (a.end32 > a.begin32 && !launch(0, g, pl->slice32[m])) return RADIC_ECUDA;
-    a.begin32 = pl->gpair[g];
-    a.end32 = pl->g32[g + 1];
-    if (a.end32 > a.begin32 && !launch(1, g, pl->slicep[m])) return RADIC_ECUDA;
+    a.begin32 = queue == 0 ? pl->g32[g] : pl->gpair[g];
+    a.end32 = queue == 0 ? pl->gpair[g] : pl->g32[g + 1];
+    if (!launch(queue, g, queue == 0 ? pl->slice32[m] : pl->slicep[m], lanes[li++ % nl])) return RADIC_ECUDA;
   }
+  if (!join()) return RADIC_ECUDA;
   ReduceArgs r;
   r.csr_ptr = reinterpret_cast<const int*>(ws + pl->off_csr_ptr);
   r.csr_idx = reinterpret_cast<const int*>(ws + pl->off_csr_idx);
@@ -232,15 +297,18 @@ int enqueue(const radic_batch_plan* pl, const void* A, int dtype, radic_result* 
       return RADIC_ECUDA;
   }
   // binary64 tier (and the flagged or rerouted binary32 and pair tasks), one
-  // kernel per group present
-  for (int g = 0; g < kGroups; ++g) {
+  // kernel per group present, most binary64 work first
+  if (!fork()) return RADIC_ECUDA;
+  li = 0;
+  for (const int g : pl->order64) {
     a.flag_base = pl->g32[g];
     a.begin32 = pl->g32[g];
     a.end32 = pl->g32[g + 1];
     a.begin64 = pl->g64[g];
     a.end64 = pl->g64[g + 1];
-    if ((a.end64 > a.begin64 || a.end32 > a.begin32) && !launch(2, g, pl->slice64[g / kPaths])) return RADIC_ECUDA;
+    if (!launch(2, g, pl->slice64[g / kPaths], lanes[li++ % nl])) return RADIC_ECUDA;
   }
+  if (!join()) return RADIC_ECUDA;
   void* rparams[] = {&r};
   if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_batch_reduce), dim3(blocks > 0 ? blocks : 1), dim3(128),
                        rparams, 0, s) != cudaSuccess)
@@ -404,26 +472,48 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
       }
     }
   }
-  // launches per call, and the dominant low-tier kernel (most estimated work)
+  // launches per call, their order (most estimated work first), and the
+  // dominant low-tier kernel
   {
-    double best = -1.0;
+    std::vector<std::pair<double, std::pair<int, int>>> low;
+    std::vector<std::pair<double, int>> hi;
     for (int g = 0; g < kGroups; ++g) {
       const int ranges[2][2] = {{pl->g32[g], pl->gpair[g]}, {pl->gpair[g], pl->g32[g + 1]}};
       for (int q = 0; q < 2; ++q) {
         if (ranges[q][1] <= ranges[q][0]) continue;
-        ++pl->launches;
         double c = 0.0;
         for (int i = ranges[q][0]; i < ranges[q][1]; ++i) c += task_cost(pl->t32[i]);
-        if (c > best) {
-          best = c;
-          pl->dom_queue = q;
-          pl->dom_group = g;
-        }
+        low.push_back({c, {q, g}});
       }
-      if (pl->g64[g + 1] > pl->g64[g] || pl->g32[g + 1] > pl->g32[g]) ++pl->launches;
+      if (pl->g64[g + 1] > pl->g64[g] || pl->g32[g + 1] > pl->g32[g]) {
+        double c = 0.0;
+        for (int i = pl->g64[g]; i < pl->g64[g + 1]; ++i) c += task_cost(pl->t64[i]);
+        hi.push_back({c, g});
+      }
     }
-    pl->launches += 1 + (pl->t32.empty() ? 0 : 1);  // reduce, check
+    // stable order: most work first, ties by (queue, group)
+    std::stable_sort(low.begin(), low.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::stable_sort(hi.begin(), hi.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    for (const auto& e : low) pl->order_low.push_back(e.second);
+    for (const auto& e : hi) pl->order64.push_back(e.second);
+    if (!low.empty()) {
+      pl->dom_queue = low[0].second.first;
+      pl->dom_group = low[0].second.second;
+    }
+    pl->launches = (int)(low.size() + hi.size()) + 1 + (pl->t32.empty() ? 0 : 1);  // + reduce, check
     if (tuning) pl->events = tuning->kernel_events;
+  }
+  // auxiliary streams and fork/join events of the concurrent phases
+  for (int i = 0; i < radic_batch_plan::kAux; ++i) {
+    if (cudaStreamCreateWithFlags(&pl->aux[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->join[i], cudaEventDisableTiming) != cudaSuccess) {
+      delete pl;
+      return RADIC_ECUDA;
+    }
+  }
+  if (cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming) != cudaSuccess) {
+    delete pl;
+    return RADIC_ECUDA;
   }
   // workspace layout
   size_t off = kBatchHeaderBytes;
@@ -447,6 +537,8 @@ int radic_batch_plan_create(const int32_t* m, const int32_t* n, const int64_t* o
   return RADIC_OK;
 }
 
+constexpr int kTaskRow = RADIC_BATCH_TASK_FIELDS;
+
 int radic_batch_plan_tasks_host(const int32_t* m, const int32_t* n, const int64_t* offsets, int batch, int mode,
                                 const radic_batch_tuning* tuning, int64_t* tasks, int64_t capacity,
                                 int64_t* n_tasks) {
@@ -460,7 +552,7 @@ int radic_batch_plan_tasks_host(const int32_t* m, const int32_t* n, const int64_
   for (const std::vector<BatchTask>* list : {&pl.t32, &pl.t64}) {
     for (const BatchTask& t : *list) {
       if (i >= capacity) return RADIC_OK;
-      int64_t* r = tasks + 8 * i;
+      int64_t* r = tasks + kTaskRow * i;
       r[0] = t.b;
       r[1] = t.tier;
       r[2] = t.kind;
@@ -469,6 +561,8 @@ int radic_batch_plan_tasks_host(const int32_t* m, const int32_t* n, const int64_
       r[5] = (int64_t)t.r0;
       r[6] = (int64_t)t.run;
       r[7] = (int64_t)t.lim;
+      r[8] = t.vlo;
+      r[9] = t.vhi;
       ++i;
     }
   }

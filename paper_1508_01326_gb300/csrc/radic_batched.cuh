@@ -52,6 +52,9 @@ struct BatchTask {
   int b, m, n, v;           // matrix, shape, prefix group
   int kind, tier;           // kKindMinor or the prefix depth; kModeMixed, kModePair or kModeFp64
   int shared;               // prefix kind: units are heads (first m-D-1 columns, v = their last column)
+  int vlo, vhi;             // head sharing: last prefix columns in [max(v+1, vlo), vhi] (a segment
+                            // of each head's subtree)
+  unsigned long long per_unit;  // minors under one unit (prefix, group segment or rank)
 };
 
 struct BatchHeader {
@@ -228,7 +231,11 @@ __device__ bool run_prefix(const BatchArgs& a, const BatchTask& t, const WarpSli
 
 // Head-shared prefix task: each lane takes a run of heads (the first
 // H = m-D-1 prefix columns, H-1 of them from {0..u-1} plus u = t.v), factors
-// each head once and appends every last column v = u+1 .. n-1-D in turn.
+// each head once and appends every last column v of the task's segment
+// [max(u+1, vlo), vhi] in turn (one elimination step each).  The segment
+// bounds the work of one unit (a head's whole subtree can hold over ten
+// thousand minors, and the longest unit sets the kernel's critical path);
+// its trip count is the same in every lane.
 template <typename T, int M, int D, bool kFlag>
 __device__ bool run_prefix_heads(const BatchArgs& a, const BatchTask& t, const WarpSlice<T>& w, TaskAcc<T>& acc,
                                  unsigned long long first, unsigned long long last, float uin) {
@@ -243,20 +250,20 @@ __device__ bool run_prefix_heads(const BatchArgs& a, const BatchTask& t, const W
   unrank<H - 1>(first < t.lim ? first : 0ull, u, w.binom, M + 1, hc);
   TermsSink ts{nullptr, 0, 0, 0, 0};
   const ZBuf<T, D> zb(w.zbuf, lane, 32, t.n - M + D);
+  // the head and its extensions are factored in FT: binary64 for pairs,
+  // from the binary64 copy (prefix_extend_pair), the element type otherwise
+  constexpr bool kPair = std::is_same<T, ff>::value;
+  using FT = typename std::conditional<kPair, double, T>::type;
+  constexpr int CSF = ColStride<FT, M>::value;
+  const FT* AsF;
+  if constexpr (kPair) AsF = w.As64;
+  else AsF = w.As;
   for (unsigned long long it = 0; it < t.run; ++it) {
     const bool act = first + it < last;
     int c[P];
 #pragma unroll
     for (int j = 0; j < H - 1; ++j) c[j] = hc[j];
     c[H - 1] = u;
-    // the head and its extensions are factored in FT: binary64 for pairs,
-    // from the binary64 copy (see prefix_to_pairs), the element type otherwise
-    constexpr bool kPair = std::is_same<T, ff>::value;
-    using FT = typename std::conditional<kPair, double, T>::type;
-    constexpr int CSF = ColStride<FT, M>::value;
-    const FT* AsF;
-    if constexpr (kPair) AsF = w.As64;
-    else AsF = w.As;
     FT W1[D + 1][H];
     Rad<T> rW1[D + 1][H], k1[D + 1];
     int idx1[M];
@@ -270,7 +277,7 @@ __device__ bool run_prefix_heads(const BatchArgs& a, const BatchTask& t, const W
       prefix_factor_b<FT, M, D + 1, CSF, FT>(AsF, ch, W1, rW1, idx1, prod1, gmax1, neg1, rel1, bad1, uin);
     }
     head_kappas<FT, D + 1, H, FT>(W1, rW1, k1, uin);
-    for (int v = u + 1; v <= t.n - 1 - D; ++v) {
+    for (int v = max(u + 1, t.vlo); v <= t.vhi; ++v) {
       c[P - 1] = v;
       T W[D][P];
       Rad<T> rW[D][P];
@@ -279,10 +286,8 @@ __device__ bool run_prefix_heads(const BatchArgs& a, const BatchTask& t, const W
       bool neg;
       PrefixErr<Rad<T>> pe;
       if constexpr (kPair) {
-        double Wd[D][P], prodd, gmaxd;
-        prefix_extend_b<double, M, D, CSF, double>(AsF, v, w.colnorm[v], W1, rW1, k1, idx1, prod1, gmax1, neg1, rel1,
-                                                   bad1, Wd, rW, idx, prodd, gmaxd, neg, pe.rel_alpha, pe.bad);
-        prefix_to_pairs<D, P>(Wd, rW, prodd, gmaxd, pe.rel_alpha, W, prod, gmax);
+        prefix_extend_pair<M, D, CSF>(AsF, v, w.colnorm[v], W1, rW1, k1, idx1, prod1, gmax1, neg1, rel1, bad1, W, rW,
+                                      idx, prod, gmax, neg, pe.rel_alpha, pe.bad);
       } else {
         prefix_extend_b<T, M, D, CS>(w.As, v, w.colnorm[v], W1, rW1, k1, idx1, prod1, gmax1, neg1, rel1, bad1, W, rW,
                                      idx, prod, gmax, neg, pe.rel_alpha, pe.bad);
@@ -342,6 +347,7 @@ __device__ bool run_task(const BatchArgs& a, const BatchTask& t, const WarpSlice
 
 template <typename T>
 __device__ __forceinline__ void warp_sum(TaskAcc<T>& acc, Dd& d, double& ab, double& bnd) {
+  if constexpr (!std::is_same<T, float>::value) acc.p.finish();  // adds the lane total's own bound
   bnd = static_cast<double>(acc.p.bnd);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) bnd += __shfl_xor_sync(kFull, bnd, off);
@@ -355,7 +361,6 @@ __device__ __forceinline__ void warp_sum(TaskAcc<T>& acc, Dd& d, double& ab, dou
     ab = static_cast<double>(ta.hi) + static_cast<double>(ta.lo);
     return;
   }
-  acc.p.finish();
   d = acc.p.acc;
   ab = acc.p.abs_sum;
 #pragma unroll
@@ -393,10 +398,7 @@ __device__ void do_task(const BatchArgs& a, const BatchTask& t, unsigned char* s
       long long redone = 0;
       if (!kFlag && t.tier != kModeFp64) {
         const unsigned long long units = min(32ull * t.run, t.lim - t.r0);
-        const int D = t.kind;
-        redone = (long long)(D == kKindMinor ? units
-                             : t.shared     ? units * c_binom.v[t.n - 1 - t.v][D + 1]
-                                            : units * c_binom.v[t.n - 1 - t.v][D]);
+        redone = (long long)(units * t.per_unit);
       }
       a.slots[slot_id] = FpPartial{d.hi, d.lo, ab, redone, bnd, 0.0};
     }

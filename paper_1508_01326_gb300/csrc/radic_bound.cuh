@@ -16,7 +16,9 @@
 //      fl(a*b + c) = a*b + c + e,  |e| <= u (|a*b| + |c|),
 //    u the unit of the arithmetic: binary64 2^-53, binary32 2^-24, pairs of
 //    binary32 2^-43 (the pair multiply-add of radic_ff.cuh errs by at most
-//    about 19 2^-48 (|a*b| + |c|), its multiplication and addition by less).
+//    about 19 2^-48 (|a*b| + |c|), its multiplication and addition by less;
+//    its dot products with one renormalisation, dot_acc, by less than u
+//    times the operation count of the chained form they replace).
 //    A multiplier a / p formed with an approximate reciprocal counts as 2
 //    (binary64, pairs) or 3 (binary32) roundings.
 //  * A pivot whose enclosure reaches zero (r_p >= |p|) cannot be bounded this

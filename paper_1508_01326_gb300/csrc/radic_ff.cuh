@@ -106,6 +106,56 @@ __device__ __forceinline__ ff rcp_t(ff a) {
   return fast_sum(r, r * res);
 }
 
+// Leading product of two pairs with its error term: a.hi b.hi = p + e exactly
+// (fma), then the cross terms a.hi b.lo and a.lo b.hi folded into e; the
+// lo lo term (below 2^-48 |ab|) is dropped.  |p + e - ab| <= 1.5 2^-46 |ab|.
+__device__ __forceinline__ void prod_terms(ff a, ff b, float& p, float& e) {
+  p = a.hi * b.hi;
+  e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+}
+
+// sum_i a[i] b[i] + c with one renormalisation (N >= 1): the leading parts of
+// the products are added by a TwoSum chain (error-free), the error terms,
+// the chain's errors and c.lo in binary32, then one Fast2Sum.  With
+// S = sum |a_i b_i| + |c| the error is at most
+//   (1.5 + N + N (N + 5) / 4 + (N + 5) / 4) 2^-46 S,
+// below 2^-43 times (2 S for N = 2, 3 S for N = 3, 7 S for N = 7): the
+// per-operation unit BoundTraits<ff>::u times the operation count of the
+// chained multiply-adds it replaces.
+template <int N, bool kC>
+__device__ __forceinline__ ff dot_acc(const ff* a, const ff* b, ff c) {
+  float s, lo;
+  int i0;
+  if constexpr (kC) {
+    s = c.hi;
+    lo = c.lo;
+    i0 = 0;
+  } else {
+    prod_terms(a[0], b[0], s, lo);
+    i0 = 1;
+  }
+#pragma unroll
+  for (int i = i0; i < N; ++i) {
+    float p, e, t;
+    prod_terms(a[i], b[i], p, e);
+    two_sum(s, p, s, t);
+    lo += e + t;
+  }
+  return fast_sum(s, lo);
+}
+
+// a b - c d for pairs (2 x 2 determinants and cross-product entries).
+__device__ __forceinline__ ff diff_prod(ff a, ff b, ff c, ff d) {
+  const ff x[2] = {a, -c}, y[2] = {b, d};
+  return dot_acc<2, false>(x, y, ff(0.0f, 0.0f));
+}
+
+// The ordinary conversion, kept out of line so that the rare branch of
+// split_to_pair costs nothing on the binary64 pipe when it is not taken.
+static __device__ __noinline__ ff pair_from_double(double x) { return ff(x); }
+
 // A pair within 2^-47 of a binary64 value, without the binary64 pipe: the high
 // part takes the leading 24 significand bits (truncated), the low part the
 // remaining 29 bits rounded once to binary32 (error at most 2^-47 |x|), then
@@ -114,7 +164,7 @@ __device__ __forceinline__ ff rcp_t(ff a) {
 __device__ __forceinline__ ff split_to_pair(double x) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   const int e = static_cast<int>((b >> 52) & 0x7ffu);
-  if (e < 1023 - 70 || e > 1023 + 100) return ff(x);
+  if (__builtin_expect(e < 1023 - 70 || e > 1023 + 100, 0)) return pair_from_double(x);
   const unsigned long long mant = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
   const unsigned int sign = static_cast<unsigned int>(b >> 63) << 31;
   const float hi = __uint_as_float(sign | (static_cast<unsigned int>(e - 1023 + 127) << 23) |
@@ -127,6 +177,8 @@ __device__ __forceinline__ ff split_to_pair(double x) {
 
 }  // namespace pairs
 
+using pairs::diff_prod;
+using pairs::dot_acc;
 using pairs::ff;
 using pairs::split_to_pair;
 

@@ -29,8 +29,17 @@ constexpr int kPrefixMaxMFp32 = 12;
 constexpr int kPrefixMaxMPair = 10;
 constexpr int kPrefixMaxMModp = 12;
 
-// 31-bit primes of the exact mode (largest primes below 2^31).
-constexpr uint32_t kPrime0 = 2147483647u, kPrime1 = 2147483629u, kPrime2 = 2147483587u, kPrime3 = 2147483579u;
+// 31-bit primes of the exact mode: the largest primes below 2^31, in
+// descending order.  radic_det uses the first RADIC_MAX_PRIMES; the wide
+// exact entry point up to RADIC_WIDE_MAX_PRIMES, RADIC_MAX_PRIMES per pass.
+constexpr int kWidePrimes = RADIC_WIDE_MAX_PRIMES;
+constexpr uint32_t kPrimeTable[kWidePrimes] = {
+    2147483647u, 2147483629u, 2147483587u, 2147483579u, 2147483563u, 2147483549u, 2147483543u, 2147483497u,
+    2147483489u, 2147483477u, 2147483423u, 2147483399u, 2147483353u, 2147483323u, 2147483269u, 2147483249u,
+    2147483237u, 2147483179u, 2147483171u, 2147483137u, 2147483123u, 2147483077u, 2147483069u, 2147483059u,
+    2147483053u, 2147483033u, 2147483029u, 2147482951u, 2147482949u, 2147482943u, 2147482937u, 2147482921u};
+constexpr uint32_t kPrime0 = kPrimeTable[0], kPrime1 = kPrimeTable[1], kPrime2 = kPrimeTable[2],
+                   kPrime3 = kPrimeTable[3];
 constexpr uint32_t kPrimes[kMaxPrimes] = {kPrime0, kPrime1, kPrime2, kPrime3};  // host use
 
 // Header at the start of every workspace (zeroed by the launcher).
@@ -122,6 +131,8 @@ struct SingleArgs {
   int* flag_count;
   unsigned long long* flag_ranks;
   uint32_t* modp_partials;  // blocks x kMaxPrimes residues
+  int prime_base;           // EXACT: first prime of this pass (wide entry point; 0 otherwise)
+  uint32_t* wide;           // EXACT wide passes: residues by prime index, then needed, exponent, status
   radic_result* out;
   // terms mode
   unsigned long long q0, count;
@@ -137,6 +148,8 @@ int launch_fp64(const SinglePlan& p, const SingleArgs& a, cudaStream_t s);
 int launch_mixed(const SinglePlan& p, const SingleArgs& a, cudaStream_t s);
 int launch_pair(const SinglePlan& p, const SingleArgs& a, cudaStream_t s);
 int launch_modp(const SinglePlan& p, const SingleArgs& a, cudaStream_t s);
+// Wide exact result from the residues of the passes (total 0: a zero result).
+int launch_wide_crt(const uint32_t* wide, radic_wide_result* out, unsigned long long total, cudaStream_t s);
 int launch_unrank(int n, int m, unsigned long long q0, unsigned long long count, uint8_t* cols,
                   int ranks_per_task, cudaStream_t s);
 

@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(kMaxThreadsModp) k_modp_thread(SingleArgs a) {
   ModpSmem sm(smem_raw, n, M, CS, blockDim.x);
   int needed;
   const int K = stage_modp(a, sm, M, CS, &needed);
+  if (K == 0) return;  // a wide pass whose primes the bound does not need
 
   const int lane = threadIdx.x & 31;
   const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(kMaxThreadsModp) k_modp_group(SingleArgs a) {
   ModpSmem sm(smem_raw, n, m, cs, blockDim.x);
   int needed;
   const int K = stage_modp(a, sm, m, cs, &needed);
+  if (K == 0) return;  // a wide pass whose primes the bound does not need
 
   const int lane = threadIdx.x & 31, sub = lane & (G - 1), seg = lane / G;
   constexpr int kSegs = 32 / G;
@@ -249,6 +251,96 @@ int blocks_per_sm_modp(const SinglePlan& p) {
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, p.threads, smem_modp(p)) != cudaSuccess) return 0;
   return nb;
+}
+
+// ---------------------------------------------------------------------------
+// Wide exact result: mixed-radix (Garner) reconstruction of the integer from
+// its residues modulo the first K primes, then base-2^32 limbs by Horner's
+// rule over the mixed-radix digits, the symmetric range (-M/2, M/2) for the
+// sign, M the product of the primes.  One thread; K <= 32.
+// ---------------------------------------------------------------------------
+__device__ void limbs_mul_add(uint32_t* x, int nl, uint32_t mul, uint32_t add) {
+  uint64_t carry = add;
+  for (int i = 0; i < nl; ++i) {
+    const uint64_t t = static_cast<uint64_t>(x[i]) * mul + carry;
+    x[i] = static_cast<uint32_t>(t);
+    carry = t >> 32;
+  }
+}
+
+__global__ void k_wide_crt(const uint32_t* wide, radic_wide_result* out, unsigned long long total) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  constexpr int NL = RADIC_WIDE_LIMBS + 1;  // one spare limb for M
+  const int needed = static_cast<int>(wide[kWidePrimes]);
+  const int escale = static_cast<int>(wide[kWidePrimes + 1]);
+  const int status = static_cast<int>(wide[kWidePrimes + 2]);
+  const int K = needed < kWidePrimes ? needed : kWidePrimes;
+  uint64_t v[kWidePrimes];
+  for (int i = 0; i < K; ++i) {
+    const uint64_t p = prime_at(i);
+    uint64_t acc = 0, prod = 1;  // digits so far and prod_{l<i} p_l, modulo p
+    for (int l = 0; l < i; ++l) {
+      acc = (acc + v[l] * prod) % p;
+      prod = (prod * (prime_at(l) % p)) % p;
+    }
+    const uint64_t diff = (wide[i] + p - acc) % p;
+    v[i] = (diff * powmod64(prod, p - 2, p)) % p;
+  }
+  uint32_t x[NL], mm[NL];
+  for (int i = 0; i < NL; ++i) x[i] = mm[i] = 0u;
+  mm[0] = 1u;
+  for (int i = K - 1; i >= 0; --i) limbs_mul_add(x, NL, prime_at(i), static_cast<uint32_t>(v[i]));
+  for (int i = 0; i < K; ++i) limbs_mul_add(mm, NL, prime_at(i), 0u);
+  // d = M - x; the value is x when x < d (that is x < M/2), else -(M - x)
+  uint32_t d[NL];
+  long long borrow = 0;
+  for (int i = 0; i < NL; ++i) {
+    const long long t = static_cast<long long>(mm[i]) - x[i] - borrow;
+    d[i] = static_cast<uint32_t>(t);
+    borrow = t < 0 ? 1 : 0;
+  }
+  bool x_less = false;
+  for (int i = NL - 1; i >= 0; --i) {
+    if (x[i] != d[i]) {
+      x_less = x[i] < d[i];
+      break;
+    }
+  }
+  const uint32_t* mag = x_less ? x : d;
+  int nl = 0;
+  for (int i = 0; i < RADIC_WIDE_LIMBS; ++i)
+    if (mag[i]) nl = i + 1;
+  for (int i = 0; i < RADIC_WIDE_LIMBS; ++i) out->limbs[i] = mag[i];
+  double val = 0.0;
+  const int lo = nl > 3 ? nl - 3 : 0;
+  for (int i = nl - 1; i >= lo; --i) val = val * 4294967296.0 + static_cast<double>(mag[i]);
+  const int sgn = nl == 0 ? 0 : (x_less ? 1 : -1);
+  out->value = sgn < 0 ? -ldexp(val, 32 * lo + escale) : ldexp(val, 32 * lo + escale);
+  out->status = (needed > kWidePrimes) ? RADIC_EOVERFLOW : status;
+  out->n_primes = K;
+  out->exact_exp = escale;
+  out->sign = sgn;
+  out->n_limbs = nl;
+  out->minors = static_cast<long long>(total);
+  out->reserved = 0;
+}
+
+__global__ void k_wide_zero(radic_wide_result* out) {
+  out->value = 0.0;
+  out->status = RADIC_OK;
+  out->n_primes = 0;
+  out->exact_exp = 0;
+  out->sign = 0;
+  out->n_limbs = 0;
+  out->minors = 0;
+  out->reserved = 0;
+  for (int i = 0; i < RADIC_WIDE_LIMBS; ++i) out->limbs[i] = 0u;
+}
+
+int launch_wide_crt(const uint32_t* wide, radic_wide_result* out, unsigned long long total, cudaStream_t s) {
+  if (total == 0) k_wide_zero<<<1, 1, 0, s>>>(out);
+  else k_wide_crt<<<1, 32, 0, s>>>(wide, out, total);
+  return cudaGetLastError() == cudaSuccess ? RADIC_OK : RADIC_ECUDA;
 }
 
 int launch_modp(const SinglePlan& p, const SingleArgs& a, cudaStream_t s) {

@@ -12,8 +12,20 @@ namespace {
 
 constexpr int kMaxThreadsModp = 128;
 
+__constant__ uint32_t c_prime_table[kWidePrimes] = {
+    kPrimeTable[0],  kPrimeTable[1],  kPrimeTable[2],  kPrimeTable[3],  kPrimeTable[4],  kPrimeTable[5],
+    kPrimeTable[6],  kPrimeTable[7],  kPrimeTable[8],  kPrimeTable[9],  kPrimeTable[10], kPrimeTable[11],
+    kPrimeTable[12], kPrimeTable[13], kPrimeTable[14], kPrimeTable[15], kPrimeTable[16], kPrimeTable[17],
+    kPrimeTable[18], kPrimeTable[19], kPrimeTable[20], kPrimeTable[21], kPrimeTable[22], kPrimeTable[23],
+    kPrimeTable[24], kPrimeTable[25], kPrimeTable[26], kPrimeTable[27], kPrimeTable[28], kPrimeTable[29],
+    kPrimeTable[30], kPrimeTable[31]};
+
 __host__ __device__ __forceinline__ uint32_t prime_at(int k) {
-  return k == 0 ? kPrime0 : k == 1 ? kPrime1 : k == 2 ? kPrime2 : kPrime3;
+#ifdef __CUDA_ARCH__
+  return c_prime_table[k];
+#else
+  return kPrimeTable[k];
+#endif
 }
 
 struct Mont {
@@ -89,7 +101,7 @@ struct ModpSmem {
   uint32_t* As;  // prime k at As + k * n * cs
   uint32_t* rows;
   uint32_t* scratch;
-  int* misc;  // [0] primes the bound needs, [1] total row exponent
+  int* misc;  // [0] primes the bound needs, [1] total row exponent, [2] non-finite flag
   Mont* mont;
   int* row_e;  // floating-point inputs: row i times 2^-row_e[i] is integer
   __device__ ModpSmem(unsigned char* base, int n, int m, int cs, int threads) {
@@ -223,12 +235,16 @@ __device__ inline int primes_needed(const void* A, int dtype, int m, int n, long
   return k < 1 ? 1 : k;
 }
 
-// Stage binom and, for each prime, (T A mod p) in Montgomery form.  Returns K
-// (primes used) in every thread; sets *needed to the primes the bound asks for.
+// Stage binom and, for each prime of the pass, (T A mod p) in Montgomery
+// form.  Slot k holds prime a.prime_base + k.  Returns K (primes this pass
+// uses; 0 when the bound needs none of them) in every thread; sets *needed
+// to the primes the bound asks for.
 __device__ inline int stage_modp(const SingleArgs& a, const ModpSmem& sm, int m, int cs, int* needed) {
   const int n = a.n;
+  const int base = a.prime_base;
   build_binom(sm.binom, n, m);
-  if (threadIdx.x < kMaxPrimes) sm.mont[threadIdx.x] = make_mont(prime_at(threadIdx.x));
+  if (threadIdx.x < kMaxPrimes && base + (int)threadIdx.x < kWidePrimes)
+    sm.mont[threadIdx.x] = make_mont(prime_at(base + threadIdx.x));
   const bool fp = is_fp_dtype(a.dtype);
   {
     // the rows scratch (m x n words) is free until the residues are staged
@@ -261,9 +277,9 @@ __device__ inline int stage_modp(const SingleArgs& a, const ModpSmem& sm, int m,
   }
   __syncthreads();
   *needed = sm.misc[0];
-  const int K = min(sm.misc[0], kMaxPrimes);
+  const int K = max(0, min(min(sm.misc[0], kWidePrimes) - base, kMaxPrimes));
   for (int k = 0; k < K; ++k) {
-    const uint32_t p = prime_at(k);
+    const uint32_t p = prime_at(base + k);
     for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
       const int i = idx / n, j = idx - i * n;
       if (fp) {
@@ -385,13 +401,13 @@ __device__ __forceinline__ bool ff_det(uint32_t (&x)[M][M], const Mont& mp, uint
 }
 
 // Block sum modulo each prime; result in thread 0's r[].
-__device__ inline void block_reduce_modp(uint32_t (&r)[kMaxPrimes], int K, uint32_t* scratch) {
+__device__ inline void block_reduce_modp(uint32_t (&r)[kMaxPrimes], int K, uint32_t* scratch, const Mont* mont) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < kMaxPrimes; ++k) {
     if (k < K) {
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) r[k] = add_mod(r[k], __shfl_xor_sync(kFull, r[k], off), prime_at(k));
+      for (int off = 16; off > 0; off >>= 1) r[k] = add_mod(r[k], __shfl_xor_sync(kFull, r[k], off), mont[k].p);
     }
   }
   __syncthreads();
@@ -401,7 +417,7 @@ __device__ inline void block_reduce_modp(uint32_t (&r)[kMaxPrimes], int K, uint3
   if (threadIdx.x == 0) {
     for (int k = 0; k < K; ++k) {
       uint32_t s = 0;
-      for (int w = 0; w < nw; ++w) s = add_mod(s, scratch[w * kMaxPrimes + k], prime_at(k));
+      for (int w = 0; w < nw; ++w) s = add_mod(s, scratch[w * kMaxPrimes + k], mont[k].p);
       r[k] = s;
     }
   }
@@ -460,17 +476,31 @@ __device__ inline void crt_write(radic_result* out, const uint32_t* res, int K, 
 }
 
 // Last-block epilogue shared by both mappings.
+// Wide passes write the pass's residues into a.wide[prime index] instead;
+// the pass with the first primes also writes needed, the exponent and the
+// status after the kWidePrimes residue slots.
 __device__ inline void finish_modp(const SingleArgs& a, const ModpSmem& sm, uint32_t (&r)[kMaxPrimes], int K,
                                    int needed) {
-  block_reduce_modp(r, K, sm.scratch);
+  block_reduce_modp(r, K, sm.scratch, sm.mont);
   if (threadIdx.x == 0)
     for (int k = 0; k < kMaxPrimes; ++k) a.modp_partials[blockIdx.x * kMaxPrimes + k] = (k < K) ? r[k] : 0u;
   if (last_block(&a.hdr->ticket[0])) {
     uint32_t t[kMaxPrimes] = {0, 0, 0, 0};
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-      for (int k = 0; k < K; ++k) t[k] = add_mod(t[k], __ldcg(&a.modp_partials[b * kMaxPrimes + k]), prime_at(k));
-    block_reduce_modp(t, K, sm.scratch);
-    if (threadIdx.x == 0) crt_write(a.out, t, K, needed, __ldcg(&a.hdr->status), a.total, sm.misc[1]);
+      for (int k = 0; k < K; ++k) t[k] = add_mod(t[k], __ldcg(&a.modp_partials[b * kMaxPrimes + k]), sm.mont[k].p);
+    block_reduce_modp(t, K, sm.scratch, sm.mont);
+    if (threadIdx.x == 0) {
+      if (a.wide) {
+        for (int k = 0; k < K; ++k) a.wide[a.prime_base + k] = t[k];
+        if (a.prime_base == 0) {
+          a.wide[kWidePrimes] = static_cast<uint32_t>(needed);
+          a.wide[kWidePrimes + 1] = static_cast<uint32_t>(sm.misc[1]);
+          a.wide[kWidePrimes + 2] = static_cast<uint32_t>(__ldcg(&a.hdr->status));
+        }
+      } else {
+        crt_write(a.out, t, K, needed, __ldcg(&a.hdr->status), a.total, sm.misc[1]);
+      }
+    }
   }
 }
 

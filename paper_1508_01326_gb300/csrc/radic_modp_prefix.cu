@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(kMaxThreadsModp) k_modp_prefix(SingleArgs a, P
   const ZBuf<uint32_t, D> zb(smem_raw + modp_smem_bytes(n, M, CS, blockDim.x), threadIdx.x, blockDim.x, n - M + D);
   int needed;
   const int K = stage_modp(a, sm, M, CS, &needed);
+  if (K == 0) return;  // a wide pass whose primes the bound does not need
 
   const int lane = threadIdx.x & 31;
   const unsigned long long gwarp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;

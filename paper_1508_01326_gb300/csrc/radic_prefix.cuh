@@ -358,11 +358,15 @@ struct PrefixAcc<float> {
 
 template <>
 struct PrefixAcc<ff> {
-  // per prefix: pair sums; per thread: binary64 two-sum of the prefix sums
-  // (one flush per prefix, off the leaf loop), binary32 pairs for |terms|
+  // per prefix: pair sums; per thread: a pair total of the prefix sums (the
+  // binary64 pipe stays free) whose additions are bounded by running error
+  // analysis: each errs by at most 2^-46 (|total| + |prefix sum|), and run
+  // sums those magnitudes; binary32 pairs for |terms|
   ff pre = ff(0.0f, 0.0f);
   float pre_abs = 0.0f;
   float pre_bnd = 0.0f, bnd = 0.0f;
+  ff tot = ff(0.0f, 0.0f);
+  float run = 0.0f;
   Ff tot_abs;
   Dd acc;
   double abs_sum = 0.0;
@@ -372,8 +376,8 @@ struct PrefixAcc<ff> {
   }
   __device__ __forceinline__ void add_bound(float b) { pre_bnd += b; }
   __device__ __forceinline__ void end_prefix() {
-    acc.add(static_cast<double>(pre.hi));
-    acc.add(static_cast<double>(pre.lo));
+    tot += pre;
+    run += fabsf(tot.hi) + fabsf(pre.hi);
     tot_abs.add(pre_abs);
     bnd += pre_bnd;
     pre = ff(0.0f, 0.0f);
@@ -386,6 +390,11 @@ struct PrefixAcc<ff> {
     pre_bnd = 0.0f;
   }
   __device__ __forceinline__ void finish() {
+    acc.add(static_cast<double>(tot.hi));
+    acc.add(static_cast<double>(tot.lo));
+    // 2^-43 covers the 2^-46 per addition, the binary32 magnitudes of the
+    // pairs and the binary32 sum `run` itself
+    bnd += 0x1p-43f * run;
     abs_sum = static_cast<double>(tot_abs.hi) + static_cast<double>(tot_abs.lo);
   }
 };
@@ -441,6 +450,17 @@ __device__ __forceinline__ void cross3(const T (&x)[3], const T (&y)[3], T (&w)[
 template <typename T>
 __device__ __forceinline__ T dot3(const T (&x)[3], const T (&w)[3]) {
   return fma(x[0], w[0], fma(x[1], w[1], x[2] * w[2]));
+}
+// Pairs: one renormalisation per determinant or entry (radic_ff.cuh dot_acc),
+// within the rounding the chained form is bounded by.
+__device__ __forceinline__ ff det2(const ff (&x)[2], const ff (&y)[2]) { return diff_prod(x[0], y[1], x[1], y[0]); }
+__device__ __forceinline__ void cross3(const ff (&x)[3], const ff (&y)[3], ff (&w)[3]) {
+  w[0] = diff_prod(x[1], y[2], x[2], y[1]);
+  w[1] = diff_prod(x[2], y[0], x[0], y[2]);
+  w[2] = diff_prod(x[0], y[1], x[1], y[0]);
+}
+__device__ __forceinline__ ff dot3(const ff (&x)[3], const ff (&w)[3]) {
+  return dot_acc<3, false>(x, w, ff(0.0f, 0.0f));
 }
 
 // Error-bound state of one prefix's leaf phase (radic_bound.cuh): the
@@ -506,12 +526,17 @@ __device__ __forceinline__ void leaf_column(const T* __restrict__ As, int col, c
   T x[M];
 #pragma unroll
   for (int s = 0; s < M; ++s) x[s] = cp[idx[s]];
+  if constexpr (std::is_same<T, ff>::value) {
 #pragma unroll
-  for (int d = 0; d < D; ++d) z[d] = x[P + d];
+    for (int d = 0; d < D; ++d) z[d] = dot_acc<P, true>(W[d], x, x[P + d]);
+  } else {
 #pragma unroll
-  for (int j = 0; j < P; ++j) {
+    for (int d = 0; d < D; ++d) z[d] = x[P + d];
 #pragma unroll
-    for (int d = 0; d < D; ++d) z[d] = fma(W[d][j], x[j], z[d]);
+    for (int j = 0; j < P; ++j) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) z[d] = fma(W[d][j], x[j], z[d]);
+    }
   }
   if constexpr (kB) {
     Rad<T> ax[M];
@@ -1074,6 +1099,107 @@ __device__ __forceinline__ void prefix_extend_b(const S* __restrict__ As, int v,
       rW[d][j] = rWr[d + 1][j] + al * rWr[0][j] + (aw0 + rWr[0][j]) * rl + B::u * (al * aw0 + awd);
     }
     W[d][H] = -l;
+    rW[d][H] = rl;
+  }
+#pragma unroll
+  for (int j = 0; j < H; ++j) idx[j] = idx1[j];
+#pragma unroll
+  for (int r = 0; r <= D; ++r) idx[H + r] = ir[r];
+  neg = ng;
+}
+
+// prefix_extend_b for pairs of binary32 from a binary64 head: the Schur
+// complement s of column v, the pivot and the multipliers l are formed in
+// binary64 (their radii are divided by the pivot, so they need its
+// precision); the update W[d][j] = W1[d+1][j] - l_d W1[0][j] runs in pairs on
+// the binary32 pipe, on the pairs nearest to W1 and l (split_to_pair, 2^-47
+// relative, added to their radii), with the pair rounding of BoundTraits<ff>.
+template <int M, int D, int CS>
+__device__ __forceinline__ void prefix_extend_pair(const double* __restrict__ As, int v, float xnorm,
+                                                   const double (&W1)[D + 1][M - D - 1],
+                                                   const float (&rW1)[D + 1][M - D - 1], const float (&k1)[D + 1],
+                                                   const int (&idx1)[M], double prod1, double gmax1, bool neg1,
+                                                   float rel1, bool bad1, ff (&W)[D][M - D], float (&rW)[D][M - D],
+                                                   int (&idx)[M], ff& prod, ff& gmax, bool& neg, float& rel_alpha,
+                                                   bool& bad) {
+  using B64 = BoundTraits<double>;
+  using BP = BoundTraits<ff>;
+  constexpr int H = M - D - 1;
+  constexpr float kSplit = 0x1p-47f;
+  double s[D + 1];
+  prefix_column<double, M, D + 1, double>(As + v * CS, W1, idx1, s);
+  float rs[D + 1];
+#pragma unroll
+  for (int r = 0; r <= D; ++r) rs[r] = k1[r] * xnorm;
+  double Wr[D + 1][H];
+  float rWr[D + 1][H];
+  int ir[D + 1];
+#pragma unroll
+  for (int r = 0; r <= D; ++r) {
+    ir[r] = idx1[H + r];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      Wr[r][j] = W1[r][j];
+      rWr[r][j] = rW1[r][j];
+    }
+  }
+  bool ng = neg1;
+#pragma unroll
+  for (int r = 1; r <= D; ++r) {
+    const bool sw = abs_greater(s[r], s[0]);
+    const double a0 = s[0], ar = s[r];
+    s[0] = sw ? ar : a0;
+    s[r] = sw ? a0 : ar;
+    const float q0 = rs[0], qr = rs[r];
+    rs[0] = sw ? qr : q0;
+    rs[r] = sw ? q0 : qr;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const double x = Wr[0][j], y = Wr[r][j];
+      Wr[0][j] = sw ? y : x;
+      Wr[r][j] = sw ? x : y;
+      const float rx = rWr[0][j], ry = rWr[r][j];
+      rWr[0][j] = sw ? ry : rx;
+      rWr[r][j] = sw ? rx : ry;
+    }
+    const int i0 = ir[0], irr = ir[r];
+    ir[0] = sw ? irr : i0;
+    ir[r] = sw ? i0 : irr;
+    ng ^= sw;
+  }
+  const double piv = s[0];
+  const float ap = mag(piv), rp = rs[0];
+  bad = bad1 || pivot_unbounded(ap, rp);
+  const float ipm = ap > 0.0f ? rcp_rad(ap) : 0.0f;
+  const float ipd = ap > rp ? rcp_rad(__fsub_rd(ap, rp)) : 0.0f;
+  rel_alpha = fmaf(1.0f + rel1, fmaf(1.0f + rp * ipm, B64::u * 1.01f, rp * ipm), rel1);
+  const double rr = rcp_t(piv);
+  prod = split_to_pair(prod1 * piv);
+  gmax = split_to_pair(fmax(gmax1, fabs(piv)));
+  rel_alpha = fmaf(1.0f + rel_alpha, kSplit, rel_alpha);
+  // the pivot row in pairs, shared by the D updates
+  ff w0[H];
+  float aw0[H], rw0[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    w0[j] = split_to_pair(Wr[0][j]);
+    aw0[j] = mag(w0[j]);
+    rw0[j] = fmaf(kSplit, aw0[j], rWr[0][j]);
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const ff lp = split_to_pair(s[d + 1] * rr);
+    const float al = mag(lp);
+    const float rl = (rs[d + 1] + al * rp) * ipd + (B64::c_div * B64::u + kSplit) * al;
+    const ff nl = -lp;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const ff wd = split_to_pair(Wr[d + 1][j]);
+      const float awd = mag(wd);
+      W[d][j] = fma(nl, w0[j], wd);
+      rW[d][j] = fmaf(kSplit, awd, rWr[d + 1][j]) + al * rw0[j] + (aw0[j] + rw0[j]) * rl + BP::u * (al * aw0[j] + awd);
+    }
+    W[d][H] = nl;
     rW[d][H] = rl;
   }
 #pragma unroll

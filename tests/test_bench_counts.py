@@ -58,6 +58,7 @@ def test_prefix_ops_head_sharing_aggregate(m, n, D):
     per_head_mul = sum(m - k - 1 for k in range(H)) + H
     # heads that have at least one prefix with a leaf (last head column <= n-D-2)
     heads = sum(math.comb(u, H - 1) for u in range(H - 1, n - D - 1))
+    assert heads == w["heads"]
     want = {
         "fma": heads * per_head_fma + w["prefixes"] * ((D + 1) * H + D * H) + w["cols"] * D * P
         + (3 * w["pairs"] if D == 3 else 0) + w["leaves"] * (D - 1),
@@ -69,11 +70,13 @@ def test_prefix_ops_head_sharing_aggregate(m, n, D):
     assert (got["all_fma"], got["all_mul"], got["all_add"]) == (want["fma"], want["mul"], want["add"])
     assert (got["pre_fma"], got["pre_mul"]) == (heads * per_head_fma + w["prefixes"] * ((D + 1) * H + D * H),
                                                 heads * per_head_mul + w["prefixes"] * (D + 1))
-    # the pair tier: columns, pairs and leaves in binary32 flops of the pair algorithms,
-    # the prefix part in binary64 flops
+    assert got["upd_fma"] == w["prefixes"] * D * H
+    # the pair tier: columns, pairs, leaves and the extensions' W updates in
+    # binary32 flops of the pair algorithms, the rest of the prefix part in
+    # binary64 flops
     f = bench.pair_flops(m, n, D, shared=True)
-    assert f["fp64"] == 2 * got["pre_fma"] + got["pre_mul"]
-    assert f["fp32"] == 18 * got["fma"] + 10 * got["mul"] + 12 * w["leaves"]
+    assert f["fp64"] == 2 * (got["pre_fma"] - got["upd_fma"]) + got["pre_mul"]
+    assert f["fp32"] == 18 * (got["fma"] + got["upd_fma"]) + 10 * got["mul"] + 12 * w["leaves"]
 
 
 def test_single_matrix_flop_count():

@@ -102,9 +102,10 @@ def _check_batch_tasks(tasks, shapes):
         _, kind, shared = kinds.pop()
         groups = defaultdict(list)
         for t in ts:
-            groups[t["group"]].append(t)
+            # head-shared tasks: one task list per (last head column, segment)
+            groups[(t["group"], t["vlo"], t["vhi"])].append(t)
         total = 0
-        for g, gl in groups.items():
+        for (g, vlo, vhi), gl in groups.items():
             lim = gl[0]["lim"]
             assert all(t["lim"] == lim for t in gl)
             # 32 lanes per task, lane l takes [r0 + l*run, r0 + (l+1)*run) clipped at lim:
@@ -118,9 +119,15 @@ def _check_batch_tasks(tasks, shapes):
                 assert lim == math.comb(n, m)
                 total += lim
             elif shared:
+                # units are heads (first m-D-1 prefix columns, g the last of
+                # them); a task covers the last columns v in [vlo, vhi]
                 H = m - kind - 1
                 assert lim == math.comb(g, H - 1)
-                total += lim * sum(math.comb(n - 1 - v, kind) for v in range(g + 1, n - kind))
+                assert g < vlo <= vhi <= n - kind - 1
+                seg = sum(math.comb(n - 1 - v, kind) for v in range(vlo, vhi + 1))
+                # one lane's unit is bounded (a single prefix is never split)
+                assert 0 < seg <= max(4096, math.comb(n - m + kind, kind)), (m, n, g, vlo, vhi, seg)
+                total += lim * seg
             else:
                 P = m - kind
                 assert lim == math.comb(g, P - 1)
