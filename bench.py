@@ -711,6 +711,18 @@ def measure_configs(R, W, torch, np, stream, flush, peaks, mats, A, minors, gold
                      "frac": mult_rate / peaks["int32_mad_wide_tops"] if peaks else None,
                      "work": mults, "peak_source": "measured: 32x32->64-bit multiply-add chain probe in this run"}}
 
+    # exact 8 x 32 binary64 (rows scaled to integers, beyond 128 bits): wide exact mode
+    a = torch.from_numpy(W.fp64_8x32()).cuda()
+    wres = torch.zeros(R.api.WIDE_RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    wws = torch.empty(int(R._lib.lib().radic_wide_workspace_bytes(8, 32, None)), dtype=torch.uint8, device="cuda")
+    ms = ev_time(lambda: R.radic_det_exact_wide(a, out=wres, workspace=wws), reps=3)
+    wr = R.parse_wide_result(wres)
+    out["fp64_8x32_exact_wide"] = {
+        "value": math.comb(32, 8) / (ms / 1e3), "unit": UNIT, "ms": ms, "n_primes": wr["n_primes"],
+        "bits": abs(wr["integer"]).bit_length(),
+        "exact_ok": wr["value_exact"] == golden_fraction("fp64_8x32"),
+        "what": "radic_det_exact_wide: RADIC_MAX_PRIMES primes per pass of the exact kernels, Garner to limbs"}
+
     # differentiation 256 x 6 x 28: forward (batched binary64) and backward
     Dm = torch.from_numpy(W.diff_256x6x28()).cuda()
     g_out = torch.ones(256, dtype=torch.float64, device="cuda")
