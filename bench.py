@@ -517,6 +517,25 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> None:
                       "leaves (multiply-add 18, multiply 10, addition 11 + 1 for the magnitude sum); the prefix "
                       "factorisations run in binary64 and are reported as fp64_flop_per_launch"),
     }
+    # the whole step: every pair-tier matrix's algorithmic work over the step time (the per-group
+    # kernels of a phase run concurrently, so the dominant kernel's own span also holds the others' tails)
+    step_fp32 = step_fp64 = 0
+    for a, r in zip(mats, rs):
+        mm, nn = a.shape
+        if r["tier"] != 3 or mm > nn or mm < 3:
+            continue
+        dflt = 3 if mm >= 6 and 2 * (nn - mm) <= 7 * mm else 2
+        v = table.get(str(mm), table.get(mm, {}))
+        dd = v.get("depth") or dflt
+        f = pair_flops(mm, nn, dd, mm - dd - 1 >= 5)
+        step_fp32 += f["fp32"]
+        step_fp64 += f["fp64"]
+    step_achieved = step_fp32 / (ms_per_step / 1e3) / 1e12
+    roofline["step"] = {
+        "achieved": step_achieved, "frac": step_achieved / fp32_peak if fp32_peak else None,
+        "fp64_frac": step_fp64 / (ms_per_step / 1e3) / 1e12 / peaks["fp64_tflops"] if peaks else None,
+        "flop": step_fp32, "fp64_flop": step_fp64,
+        "rule": "binary32 flops of every pair-tier matrix (same rule) over ms_per_step"}
     headline_tiers = {"binary64": tiers.get(0, 0), "binary32": tiers.get(1, 0), "pairs": tiers.get(3, 0)}
 
     configs = None

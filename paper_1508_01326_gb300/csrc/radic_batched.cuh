@@ -218,8 +218,7 @@ __device__ bool run_prefix(const BatchArgs& a, const BatchTask& t, const WarpSli
     for (int j = 0; j < P - 1; ++j) c[j] = head[j];
     c[P - 1] = t.v;
     const bool f =
-        prefix_one<T, M, D, CS, false, kFlag>(w.As, w.binom, t.n, t.v, c, zb, thr, act, 0, 1, acc.p, ts, w.colnorm,
-                                              uin, w.As64);
+        prefix_one<T, M, D, CS, false, kFlag>(w.As, w.binom, t.n, t.v, c, zb, thr, act, 0, 1, acc.p, ts, uin, w.As64);
     if (kFlag && act && f) flagged = true;
     acc.p.end_prefix();
     if constexpr (P > 1) {
@@ -294,7 +293,7 @@ __device__ bool run_prefix_heads(const BatchArgs& a, const BatchTask& t, const W
       }
       pe.kappa = 0.0f;
       const bool f = prefix_leaves<T, M, D, CS, false, kFlag>(w.As, w.binom, t.n, v, c, W, idx, prod, gmax, neg, zb,
-                                                              thr, act, 0, 1, acc.p, ts, w.colnorm, pe, rW, uin);
+                                                              thr, act, 0, 1, acc.p, ts, pe, rW, uin);
       if (kFlag && act && f) flagged = true;
       acc.p.end_prefix();
     }

@@ -381,10 +381,9 @@ __device__ __forceinline__ T lu_det_b(T (&a)[M][M], T& gmax, float& bnd, bool& b
 // p_K's enclosure reaches zero, det = prod_{k<K} p_k det(S) with S the
 // remaining Schur complement, so |det| <= prod_{k<K} (|p_k| + r_k) times
 // Hadamard's bound of S's enclosure, prod_j ||(|s_j| + r_j)||, and the error
-// is at most that plus |computed det| (cn: unused, kept for the callers).
+// is at most that plus |computed det|.
 template <int MC>
-__device__ double lu_det_local(double (&a)[MC * MC], int m, const double* cn, double* bnd) {
-  (void)cn;
+__device__ double lu_det_local(double (&a)[MC * MC], int m, double* bnd) {
   constexpr double u = 0x1p-53;
   double ra[MC * MC];
   for (int i = 0; i < m * MC; ++i) ra[i] = 0.0;

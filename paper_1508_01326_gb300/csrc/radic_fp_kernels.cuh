@@ -260,10 +260,6 @@ __global__ void __launch_bounds__(kMaxThreadsFp) k_fp_thread(SingleArgs a) {
   bool exact_in;
   const int escale = stage_scaled<T>(a.A, a.dtype, M, n, a.lda, sm.As, CS, sm.row_exp, &exact_in);
   const float uin = exact_in ? 0.0f : static_cast<float>(BoundTraits<T>::u_in);
-  if constexpr (!kTerms) {
-    column_norms<T>(sm.As, CS, M, n, sm.colnorm, threadIdx.x, blockDim.x);
-    __syncthreads();
-  }
 
   const int lane = threadIdx.x & 31;
   const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;

@@ -16,11 +16,10 @@ __device__ double signed_minor_f64(const FpSmem<double>& sm, int n, int m, unsig
                                    double& bnd) {
   int c[MC];
   unrank_dyn<MC>(q, n, m, sm.binom, m + 1, c);
-  double a[MC * MC], cn[MC];
-  for (int j = 0; j < m; ++j) cn[j] = sm.colnorm[c[j]];
+  double a[MC * MC];
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < m; ++j) a[i * MC + j] = sm.As[c[j] * m + i];
-  double det = lu_det_local<MC>(a, m, cn, &bnd);
+  double det = lu_det_local<MC>(a, m, &bnd);
   absd = fabs(det);
   return sign_negative_dyn<MC>(c, m) ? -det : det;
 }
@@ -40,11 +39,10 @@ __device__ long long prefix_leaves_f64(const FpSmem<double>& sm, int n, int m, i
   for (int d = 0; d < D; ++d) cols[P + d] = v + 1 + d;
   if (cols[m - 1] >= n) return 0;
   for (;;) {
-    double a[MC * MC], cn[MC], b;
-    for (int j = 0; j < m; ++j) cn[j] = sm.colnorm[cols[j]];
+    double a[MC * MC], b;
     for (int i = 0; i < m; ++i)
       for (int j = 0; j < m; ++j) a[i * MC + j] = sm.As[cols[j] * m + i];
-    double det = lu_det_local<MC>(a, m, cn, &b);
+    double det = lu_det_local<MC>(a, m, &b);
     if (sign_negative_dyn<MC>(cols, m)) det = -det;
     acc.add(det);
     abs_sum += fabs(det);
@@ -90,8 +88,6 @@ __global__ void __launch_bounds__(128) k_mixed_fixup(SingleArgs a, int main_bloc
   if (has_work) {
     build_binom(sm.binom, n, m);
     stage_scaled<double>(a.A, a.dtype, m, n, a.lda, sm.As, m, sm.row_exp);
-    column_norms<double>(sm.As, m, m, n, sm.colnorm, threadIdx.x, blockDim.x);
-    __syncthreads();
     if (overflow) {
       const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
       const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -766,7 +766,7 @@ __device__ __forceinline__ void prefix_leaves_terms(const T* __restrict__ As, co
 // first leaf column (D = 2), counted from v+1, is congruent to sub mod lp.
 template <int M, int D, int CS>
 __device__ __noinline__ void prefix_minors_f64(const double* __restrict__ As, const int (&c)[M - D], int v, int n,
-                                               int sub, int lp, PrefixAcc<double>& acc, const float* colnorm) {
+                                               int sub, int lp, PrefixAcc<double>& acc) {
   constexpr int P = M - D;
   const int k = n - 1 - v;
   if (k < D) return;
@@ -781,12 +781,10 @@ __device__ __noinline__ void prefix_minors_f64(const double* __restrict__ As, co
     if (key % lp == sub) {
 #pragma unroll
       for (int d = 0; d < D; ++d) cols[P + d] = v + 1 + q[d];
-      double a[M * M], cn[M], b;
-      for (int j = 0; j < M; ++j) {
-        cn[j] = static_cast<double>(colnorm[cols[j]]);
+      double a[M * M], b;
+      for (int j = 0; j < M; ++j)
         for (int i = 0; i < M; ++i) a[i * M + j] = As[cols[j] * CS + i];
-      }
-      double det = lu_det_local<M>(a, M, cn, &b);
+      double det = lu_det_local<M>(a, M, &b);
       if (sign_negative<M>(cols)) det = -det;
       acc.add_column(det, fabs(det));
       acc.add_bound(b);
@@ -804,7 +802,6 @@ __device__ __forceinline__ bool prefix_leaves(const T* __restrict__ As, const ui
                                               const int (&c)[M - D], const T (&W)[D][M - D], const int (&idx)[M],
                                               T prod, T gmax, bool neg, const ZBuf<T, D>& zb, T thr, bool act,
                                               int sub, int lp, PrefixAcc<T>& acc, const TermsSink& ts,
-                                              const Rad<T>* colnorm = nullptr,
                                               const PrefixErr<Rad<T>>& pe = PrefixErr<Rad<T>>{},
                                               const Rad<T> (*rW)[M - D] = nullptr, float uin = 0.0f) {
   using R = Rad<T>;
@@ -879,7 +876,7 @@ __device__ __forceinline__ bool prefix_leaves(const T* __restrict__ As, const ui
            (lb.poly.perturbation() + R(leaf_round_coef<D>()) * B::u * lb.poly.hadamard());
     if (act) acc.add_bound(b);
     if constexpr (kSlow) {
-      if (slow && act_in) prefix_minors_f64<M, D, CS>(As, c, v, n, sub, lp, acc, colnorm);
+      if (slow && act_in) prefix_minors_f64<M, D, CS>(As, c, v, n, sub, lp, acc);
     } else if (pe.bad) {
       bad = true;  // the caller redoes the prefix in binary64
     }
@@ -915,7 +912,7 @@ template <typename T, int M, int D, int CS, bool kTerms, bool kRedo = true>
 __device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint64_t* binom, int n, int v,
                                            const int (&c)[M - D], const ZBuf<T, D>& zb, T thr, bool act, int sub,
                                            int lp, PrefixAcc<T>& acc, const TermsSink& ts,
-                                           const Rad<T>* colnorm = nullptr, float uin = BoundTraits<T>::u_in,
+                                           float uin = BoundTraits<T>::u_in,
                                            const double* As64 = nullptr) {
   constexpr int P = M - D;
   T W[D][P];
@@ -939,7 +936,7 @@ __device__ __forceinline__ bool prefix_one(const T* __restrict__ As, const uint6
     }
     pe.kappa = 0.0f;
     return prefix_leaves<T, M, D, CS, kTerms, kRedo>(As, binom, n, v, c, W, idx, prod, gmax, neg, zb, thr, act, sub,
-                                                     lp, acc, ts, colnorm, pe, rW, uin);
+                                                     lp, acc, ts, pe, rW, uin);
   }
 }
 
@@ -1213,9 +1210,11 @@ __device__ __forceinline__ void prefix_extend_pair(const double* __restrict__ As
 // Single-matrix prefix kernel.
 // ---------------------------------------------------------------------------
 // Minimum resident blocks per SM the compiler must allow for (register cap)
-// of the binary32 prefix kernels.
+// of the binary32 and pair prefix kernels.  Binary32: three blocks of 128
+// threads (168 registers, a few spilled bytes) rather than the 254 registers
+// the error-bound code takes unconstrained, which leave room for two.
 #ifndef RADIC_PREFIX_MIN_BLOCKS_F32
-#define RADIC_PREFIX_MIN_BLOCKS_F32 1
+#define RADIC_PREFIX_MIN_BLOCKS_F32 3
 #endif
 #ifndef RADIC_PREFIX_MIN_BLOCKS_FF
 #define RADIC_PREFIX_MIN_BLOCKS_FF 1
@@ -1240,10 +1239,8 @@ __global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(Singl
   bool exact_in;
   const int escale = stage_scaled<T>(a.A, a.dtype, M, n, a.lda, sm.As, CS, sm.row_exp, &exact_in);
   const float uin = exact_in ? 0.0f : static_cast<float>(BoundTraits<T>::u_in);
-  if constexpr (!kTerms) {
-    column_norms<T>(sm.As, CS, M, n, sm.colnorm, threadIdx.x, blockDim.x);
-    if constexpr (std::is_same<T, ff>::value)
-      stage_double_copy(sm.As, CS, M, n, sm.As64, ColStride<double, M>::value, threadIdx.x, blockDim.x);
+  if constexpr (!kTerms && std::is_same<T, ff>::value) {
+    stage_double_copy(sm.As, CS, M, n, sm.As64, ColStride<double, M>::value, threadIdx.x, blockDim.x);
     __syncthreads();
   }
 
@@ -1291,7 +1288,7 @@ __global__ void __launch_bounds__(128, prefix_min_blocks<T>()) k_fp_prefix(Singl
       for (int j = 0; j < P - 1; ++j) c[j] = head[j];
       c[P - 1] = v;
       const bool flag = prefix_one<T, M, D, CS, kTerms, kMixed>(sm.As, sm.binom, n, v, c, zb, thr, act, sub, lp, acc,
-                                                                 ts, sm.colnorm, uin, sm.As64);
+                                                                 ts, uin, sm.As64);
       if constexpr (kMixed && !kTerms) {
         if (act && flag) acc.drop_prefix();  // its leaves are recomputed in binary64
         // every lane of the group drops its share; the first one records the prefix
