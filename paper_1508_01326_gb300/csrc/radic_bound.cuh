@@ -38,7 +38,9 @@
 //      |det Z^ - det Z| <= prod_c (n_c + r_c) - prod_c n_c,
 //    and summed over all leaves of the prefix these are symmetric functions
 //    of the columns' (n_c, r_c), accumulated in O(1) per column (LeafPoly).
-//    r_c = kappa * ||A[:, c]||_2 with kappa from the radii of W = -L21 L11^-1.
+//    r_c is the column's exact radius from the radii of W = -L21 L11^-1 and
+//    its own entries (binary64, pairs), or kappa * ||A[:, c]||_2 with kappa
+//    from the row norms of W and its radii (binary32: one multiply).
 //    The rounding of each leaf determinant adds c_D u prod_c n_c, the radius
 //    of alpha adds rel_alpha |term|, and the summation of the prefix's terms
 //    adds u_sum * depth * |term| for the longest addition chain.

@@ -469,45 +469,55 @@ __device__ __forceinline__ ff dot3(const ff (&x)[3], const ff (&w)[3]) {
 template <typename T, int D, int P, bool kOn>
 struct LeafBound {
   using R = Rad<T>;
-  R rW[kOn ? D : 1][kOn ? P : 1];  // radii of W
-  R aW[kOn ? D : 1][kOn ? P : 1];  // |W|
-  R cround;                        // P u + u_in: rounding of a Schur-complement entry per unit of its terms
+  // binary64 and pairs: the exact per-column radius; binary32 (whose bound
+  // only has to meet 1e-4 targets): kappa times the column's norm, one
+  // multiply per column
+  static constexpr bool kExact = kOn && !std::is_same<T, float>::value;
+  R cW[kExact ? D : 1][kExact ? P : 1];  // rW (1 + u_in) + cround |W|: the radius weight of |x_j| in entry d
+  R cround;                              // P u + u_in: rounding of a Schur-complement entry per unit of its terms
   R uin;
+  R kappa;                               // binary32: radius of z(x) per unit of ||x||_2 (kappa_of)
   LeafPoly<R, D> poly;
   R pabs;
   template <typename W_t>
   __device__ __forceinline__ LeafBound(const W_t& W, const R (*rw)[P], R uin_) : uin(uin_), pabs(R(0)) {
-    if constexpr (kOn) {
+    if constexpr (kExact) {
       cround = R(P) * R(BoundTraits<T>::u) + uin_;
 #pragma unroll
       for (int d = 0; d < D; ++d)
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-          rW[d][j] = rw[d][j] * (R(1) + uin_);
-          aW[d][j] = mag(W[d][j]);
-        }
+        for (int j = 0; j < P; ++j) cW[d][j] = fmaf(cround, mag(W[d][j]), rw[d][j] * (R(1) + uin_)) * R(1.0000002);
+    } else if constexpr (kOn) {
+      kappa = kappa_of<T, D, P>(W, *reinterpret_cast<const R(*)[D][P]>(rw), uin_);
     }
   }
   // z: the column's computed Schur complement (before its sign and alpha),
   // ax: the magnitudes of its column entries in the prefix's row order.
   // |z_d - z^_d| <= sum_j rW_dj |x_j| + (P u + u_in)(|x_Bd| + sum_j |W_dj| |x_j|)
+  //              = cround |x_Bd| + sum_j cW_dj |x_j|
   __device__ __forceinline__ void column(const T (&z)[D], const R (&ax)[P + D]) {
-    if constexpr (kOn) {
+    if constexpr (kExact) {
       R n2 = R(0), r2 = R(0);
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const R a = mag(z[d]);
         n2 += a * a;
-        R s1 = R(0), s2 = ax[P + d];
+        R rz = cround * ax[P + d];
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-          s1 += rW[d][j] * ax[j];
-          s2 += aW[d][j] * ax[j];
-        }
-        const R rz = s1 + cround * s2;
+        for (int j = 0; j < P; ++j) rz = fmaf(cW[d][j], ax[j], rz);
         r2 += rz * rz;
       }
       poly.add(sqrt(n2) * R(1.0000005), sqrt(r2) * R(1.000002));
+    } else if constexpr (kOn) {
+      R n2 = R(0), x2 = R(0);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const R a = mag(z[d]);
+        n2 += a * a;
+      }
+#pragma unroll
+      for (int s = 0; s < P + D; ++s) x2 += ax[s] * ax[s];
+      poly.add(sqrt(n2) * R(1.0000005), kappa * sqrt(x2) * R(1.000002));
     }
   }
   __device__ __forceinline__ void term_abs(const T& babs) {
