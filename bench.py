@@ -46,9 +46,10 @@ WORKLOAD = ("batched_4096: 4096 matrices, m uniform in {2..10}, n = m + uniform{
             "N(0,1) from numpy PCG64 seed 4, 3,373,693,081 signed minors; MIXED router at err_bound <= 1e-10 "
             "of sum|terms| per matrix")
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernel from an ncu capture of that kernel; None until the current
-# kernel has been captured (the bench then reports traffic null).
-DOMINANT_DRAM_BYTES = None
+# dominant kernel (the pair tier's m = 10 group of the 4096-matrix batch)
+# from one ncu capture of that kernel on the same 493 matrices
+# (`cli --batched-m 10 --mode mixed`): 7.308 MB read + 0.074 MB written.  Set to None whenever that kernel changes until it is recaptured.
+DOMINANT_DRAM_BYTES = 7_382_272
 ORACLE_SAMPLE_OFFSET = 1_000_000
 
 
