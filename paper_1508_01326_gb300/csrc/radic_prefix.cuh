@@ -410,6 +410,9 @@ struct TermsSink {
 // shared memory serves kLeafBlock leaves (fewer loads per leaf, kLeafBlock
 // independent sums in flight).  Binary64 keeps one column per step: its
 // leaves are bound by the binary64 pipe, and wider blocks only cost registers.
+// Pairs too (measured on the batched m = 9 and 10 pair kernels: one column
+// per step 1-2% faster than two, three 7% slower): their kernels are bound
+// by dependency latency at 255 registers.
 #ifndef RADIC_LEAF_BLOCK_F32
 #define RADIC_LEAF_BLOCK_F32 4
 #endif
@@ -417,7 +420,7 @@ struct TermsSink {
 #define RADIC_LEAF_BLOCK_F64 1
 #endif
 #ifndef RADIC_LEAF_BLOCK_FF
-#define RADIC_LEAF_BLOCK_FF 2
+#define RADIC_LEAF_BLOCK_FF 1
 #endif
 template <typename T>
 __host__ __device__ constexpr int leaf_block() {
