@@ -67,9 +67,11 @@ enum { RADIC_I8 = 0, RADIC_I32 = 1, RADIC_F32 = 2, RADIC_F64 = 3 };
 /* Arithmetic of the minor determinants.
  *  FP64  -- binary64 partial-pivot LU per minor, binary64 compensated sum.
  *  MIXED -- binary32 partial-pivot LU per minor; minors whose pivot growth
- *           exceeds the threshold, or whose result is not finite, are
- *           recomputed in binary64; sums are compensated (float-float per
- *           run of ranks, then binary64 two-sum across runs and blocks).
+ *           exceeds the threshold, whose result is not finite, or one of
+ *           whose dividing pivots is not bounded away from zero by its
+ *           error radius, are recomputed in binary64; sums are compensated
+ *           (float-float per run of ranks, then binary64 two-sum across
+ *           runs and blocks).
  *  EXACT -- LU modulo 31-bit primes (as many as a Hadamard bound needs, at
  *           most RADIC_MAX_PRIMES) and Chinese remaindering to a signed
  *           128-bit integer, bit-exact.  Integer inputs directly; binary32
@@ -82,11 +84,12 @@ enum { RADIC_I8 = 0, RADIC_I32 = 1, RADIC_F32 = 2, RADIC_F64 = 3 };
  *           RADIC_EOVERFLOW; radic_det_exact_wide takes up to
  *           RADIC_WIDE_MAX_PRIMES primes for them.  A non-finite entry:
  *           status RADIC_EINVAL.
- *  PAIR  -- the MIXED scheme with the elimination carried out in pairs of
+ *  PAIR  -- the MIXED scheme with the leaves carried out in pairs of
  *           binary32 numbers (hi + lo, about 48 significant bits, on the
- *           binary32 pipe): PREFIX mapping, 3 <= m <= 10; flagged prefixes
- *           are recomputed in binary64.  Also the value of a batched
- *           result's `tier` field for matrices routed to pairs. */
+ *           binary32 pipe) and the prefix factorisations in binary64:
+ *           PREFIX mapping, 3 <= m <= 10; flagged prefixes are recomputed
+ *           in binary64.  Also the value of a batched result's `tier`
+ *           field for matrices routed to pairs. */
 enum { RADIC_MODE_FP64 = 0, RADIC_MODE_MIXED = 1, RADIC_MODE_EXACT = 2, RADIC_MODE_PAIR = 3 };
 
 /* Minor-to-thread mapping.
@@ -143,14 +146,18 @@ typedef struct radic_result {
   double value;     /* det_R(A) rounded to binary64 (EXACT: from exact value)  */
   double abs_sum;   /* sum over J of |det(A[:, J])| in the mode's arithmetic   */
   double err_bound; /* floating-point modes: an upper bound on
-                       |value - det_R(A)| for A as given (before the final
-                       rounding of value to binary64 it also covers), from
+                       |value - det_R(A)| for A as given (it also covers
+                       the final rounding of value to binary64), from
                        running error analysis of the eliminations actually
-                       performed (first order, safeguarded: every pivot's
-                       radius below 2^-12 of its magnitude, else the
-                       minor is redone in binary64 or bounded by Hadamard's
-                       inequality) and of the summations; +inf or NaN when
-                       no bound could be formed.  EXACT: 0.               */
+                       performed (midpoint-radius enclosures of every
+                       quantity; a pivot whose enclosure reaches zero gets
+                       its minor or prefix redone in binary64, or in
+                       binary64 is bounded by Hadamard's inequality on the
+                       enclosure of the remaining Schur complement) and of
+                       the summations; +inf or NaN when no bound could be
+                       formed.  Entries below about 2^-100 (binary32,
+                       pairs) or 2^-70 (binary64) of their row's largest are
+                       not covered.  EXACT: 0.                             */
   int64_t exact_lo; /* EXACT: low 64 bits of det_R(A), two's complement int128 */
   int64_t exact_hi; /* EXACT: high 64 bits                                     */
   int64_t minors;   /* C(n, m), or 0 when m > n                                */
