@@ -14,7 +14,7 @@
 // (m-1) x (m-1) determinants.
 //
 // For 3 <= m the default kernel shares the work per (m-2)-column prefix, as
-// the forward prefix kernels do.  With the prefix rows T (pivot order) and B
+// the forward prefix kernels do, in binary64 or in pairs of binary32.  With the prefix rows T (pivot order) and B
 // (the other two), A = A_TT, W = -A_BT A^{-1}, the Schur complement of a leaf
 // (x, y) is S = [z(x) z(y)], z = x_B + W x_T, det(N) = det(A) det(S) for the
 // row-permuted minor N, and by the block inverse
@@ -30,8 +30,23 @@
 // operations for its k candidate columns and its C(k, 2) leaves, and scatters
 // m (m - 2 + k) gradient entries.  A prefix with an exactly zero pivot falls
 // back to the per-minor cofactors for its leaves.
+//
+// Gathering those entries: each warp adds into its own gradient tile in
+// shared memory (binary64 or pairs, as the kernel computes), without
+// atomics, and the block adds its warps' tiles in warp order at the end.  The
+// 32 lanes of a warp task hold prefixes with the same last column v, so they
+// share the candidate columns and v: those columns are summed over the warp in
+// registers (a reduce-scatter of the m rows, one lane per entry), v's entries
+// first per lane over the lane's run.  Of the other prefix columns, the ones
+// that change slowly in dictionary order are summed per lane in shared memory
+// and added when the column moves on; the fastest one is added per prefix,
+// lanes with the same column taking turns.  (Atomic binary64 additions to
+// shared memory retry under contention; adding every entry that way, with 32
+// lanes on one column, made them the bulk of the kernel.)
+//
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "radic_prefix.cuh"
 
@@ -297,9 +312,121 @@ __device__ __forceinline__ bool is_zero(ff x) { return x.hi == 0.0f; }
 __device__ __forceinline__ double to_double(double x) { return x; }
 __device__ __forceinline__ double to_double(ff x) { return static_cast<double>(x); }
 
+__device__ __forceinline__ double shfl_x(double x, int off) { return __shfl_xor_sync(kFull, x, off); }
+__device__ __forceinline__ ff shfl_x(ff x, int off) {
+  return ff(__shfl_xor_sync(kFull, x.hi, off), __shfl_xor_sync(kFull, x.lo, off));
+}
+
+// Adds the sum over the warp's 32 lanes of v[0..M-1] (one value per row of
+// the matrix) to column `tcol` of the warp's gradient tile.  Three exchange
+// steps on lane bits 4, 3 and 2 halve the vector each time (a
+// reduce-scatter), so each group of four lanes ends with one row summed over
+// eight lanes; two butterfly steps on bits 1 and 0 finish the sum, and the
+// group's first lane adds it in: one lane per entry, so no atomics.  Nine
+// additions and nine exchanges per lane.  Every lane of the warp must call it.
+template <typename T, int M>
+__device__ __forceinline__ void warp_add_column(const T (&v)[M], T* tcol, int n, int lane) {
+  static_assert(M <= 8, "rows are spread over lane bits 4..2");
+  T p[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) p[j] = T(0);
+#pragma unroll
+  for (int j = 0; j < M; ++j) p[j] = v[j];
+  const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+  T w4[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const T keep = b4 ? p[j + 4] : p[j], send = b4 ? p[j] : p[j + 4];
+    w4[j] = keep + shfl_x(send, 16);
+  }
+  T w2[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const T keep = b3 ? w4[j + 2] : w4[j], send = b3 ? w4[j] : w4[j + 2];
+    w2[j] = keep + shfl_x(send, 8);
+  }
+  T w = (b2 ? w2[1] : w2[0]) + shfl_x(b2 ? w2[0] : w2[1], 4);
+  w = w + shfl_x(w, 2);
+  w = w + shfl_x(w, 1);
+  const int row = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
+  if ((lane & 3) == 0 && row < M) tcol[row * n] += w;
+  __syncwarp();
+}
+
+// The same for two adjacent columns at once: lane bit 4 picks the column and
+// bits 3..1 the row, so the five exchange steps serve both columns (at most
+// fourteen additions per lane for m <= 8) and lanes with bit 0 clear add the
+// sums.  `second` (the same on every lane) says whether column tcol + 1 exists.
+template <typename T, int M>
+__device__ __forceinline__ void warp_add_columns2(const T (&va)[M], const T (&vb)[M], T* tcol, int n, int lane,
+                                                  bool second) {
+  static_assert(M <= 8, "rows are spread over lane bits 3..1");
+  const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0, b1 = (lane & 2) != 0;
+  T w8[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) w8[j] = T(0);
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const T keep = b4 ? vb[j] : va[j], send = b4 ? va[j] : vb[j];
+    w8[j] = keep + shfl_x(send, 16);
+  }
+  T w4[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const T keep = b3 ? w8[j + 4] : w8[j], send = b3 ? w8[j] : w8[j + 4];
+    w4[j] = keep + shfl_x(send, 8);
+  }
+  T w2[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const T keep = b2 ? w4[j + 2] : w4[j], send = b2 ? w4[j] : w4[j + 2];
+    w2[j] = keep + shfl_x(send, 4);
+  }
+  T w = (b1 ? w2[1] : w2[0]) + shfl_x(b1 ? w2[0] : w2[1], 2);
+  w = w + shfl_x(w, 1);
+  const int row = (b3 ? 4 : 0) + (b2 ? 2 : 0) + (b1 ? 1 : 0);
+  if ((lane & 1) == 0 && row < M && (!b4 || second)) tcol[(b4 ? 1 : 0) + row * n] += w;
+  __syncwarp();
+}
+
+// Adds u[0..M-1] to rows 0..M-1 of column `key` of the warp's tile for the
+// lanes with key >= 0.  Lanes with the same column take turns, in lane order,
+// one round per lane of the largest such group, so no two lanes write one
+// entry in the same round.  Every lane of the warp must call it.
+template <typename T, int M>
+__device__ __forceinline__ void warp_tile_add(T* tile, int n, int key, const T (&u)[M], int lane) {
+  const unsigned grp = __match_any_sync(kFull, key);
+  const unsigned rank = __popc(grp & ((1u << lane) - 1u));
+  const unsigned rounds = __reduce_max_sync(kFull, key >= 0 ? (unsigned)__popc(grp) : 0u);
+  for (unsigned it = 0; it < rounds; ++it) {
+    if (key >= 0 && rank == it) {
+#pragma unroll
+      for (int i = 0; i < M; ++i) tile[i * n + key] += u[i];
+    }
+    __syncwarp();
+  }
+}
+
+// u[rho] = x[r] for the slot r with idx[r] == rho: values in pivot order back
+// to the matrix's row order (selects only, no indexed registers).
+template <typename T, int M>
+__device__ __forceinline__ void unpermute(const T (&x)[M], const int (&idx)[M], T (&u)[M]) {
+#pragma unroll
+  for (int rho = 0; rho < M; ++rho) {
+    T s = T(0);
+#pragma unroll
+    for (int r = 0; r < M; ++r) s = (idx[r] == rho) ? x[r] : s;
+    u[rho] = s;
+  }
+}
+
 template <typename T, int M>
 __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, PrefixTable tab) {
   constexpr int D = 2, P = M - D;
+  // head positions 0 .. P-3 change slowly in dictionary order and are summed
+  // per lane in shared memory (NS of them); position P-2 changes with every
+  // prefix and is added directly; column v is the same for the whole warp
+  constexpr int NS = P > 2 ? P - 2 : 0;
   constexpr int CS = ColStride<T, M>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.n;
@@ -308,9 +435,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, Pref
   size_t off = ((size_t)(n + 1) * (M + 1) * 8 + 15) / 16 * 16;
   T* As = reinterpret_cast<T*>(smem_raw + off);
   off += ((size_t)n * CS * sizeof(T) + 15) / 16 * 16;
-  double* G = reinterpret_cast<double*>(smem_raw + off);  // M x n gradient tile
+  double* G = reinterpret_cast<double*>(smem_raw + off);  // M x n tile of the singular-prefix path
   off += ((size_t)M * n * 8 + 15) / 16 * 16;
   const ZBuf<T, D> zb(smem_raw + off, threadIdx.x, blockDim.x, n - M + D);
+  off += (zbuf_bytes(n - M + D, blockDim.x, D, 8) + 15) / 16 * 16;
+  T* Hacc = reinterpret_cast<T*>(smem_raw + off) + threadIdx.x;  // [NS][M] per lane, lane-strided
+  off += (size_t)NS * M * blockDim.x * sizeof(T);
+  T* Gall = reinterpret_cast<T*>(smem_raw + off);  // one M x n tile per warp
   build_binom(binom, n, M);
   const double* Ab = a.A + (long long)b * a.stride;
   for (int idx = threadIdx.x; idx < n * CS; idx += blockDim.x) {
@@ -318,23 +449,41 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, Pref
     As[idx] = (i < M) ? to_elem<T>(Ab[(long long)i * a.lda + j]) : T(0);
   }
   for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) G[idx] = 0.0;
+  for (int idx = threadIdx.x; idx < (int)(blockDim.x >> 5) * M * n; idx += blockDim.x) Gall[idx] = T(0);
   __syncthreads();
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int bs = M + 1;
+  const int hs = blockDim.x;
+  T* Gw = Gall + (size_t)warp * M * n;  // stride between a lane's accumulator entries
   for (unsigned long long t = (unsigned long long)chunk * wpb + warp; t < tab.total_tasks;
        t += (unsigned long long)a.chunks * wpb) {
+    // everything up to the step loop is the same for the 32 lanes of the task
     int v = tab.v_lo;
     while (v < tab.v_hi && t >= tab.task_start[v + 1]) ++v;
     const unsigned long long runlen = tab.run[v], cnt = tab.count[v];
     const unsigned long long r0 = (t - tab.task_start[v]) * 32ull * runlen + (unsigned long long)lane * runlen;
     const unsigned long long r1 = min(r0 + runlen, cnt);
-    if (r0 >= r1) continue;  // lanes past the group's end (no warp-wide operations below)
+    const bool ever = r0 < r1;  // true for lane 0: a task starts below cnt
     constexpr int H = P > 1 ? P - 1 : 1;
     int head[H];
-    if constexpr (P > 1) unrank<P - 1>(r0, v, binom, bs, head);
+    if constexpr (P > 1) unrank<P - 1>(ever ? r0 : cnt - 1, v, binom, bs, head);
     const int k = n - 1 - v;
-    for (unsigned long long r = r0; r < r1; ++r) {
+    T vacc[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) vacc[i] = T(0);
+    int hcol[NS > 0 ? NS : 1];
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+      hcol[p] = head[p];
+#pragma unroll
+      for (int i = 0; i < M; ++i) Hacc[(p * M + i) * hs] = T(0);
+    }
+    // lanes past their run repeat their last prefix with zero weight, so that
+    // the whole warp takes every step (the column sums exchange registers)
+    for (unsigned long long st = 0; st < runlen; ++st) {
+      const unsigned long long r = r0 + st;
+      const bool live = r < r1;
       int c[P];
 #pragma unroll
       for (int j = 0; j < P - 1; ++j) c[j] = head[j];
@@ -378,7 +527,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, Pref
           for (int j = kk + 1; j < P; ++j) fa[i][j] = fma(-l, fa[kk][j], fa[i][j]);
         }
       }
-      if (zp) {  // singular prefix: per-minor cofactors of its leaves
+      if (live && zp) {  // singular prefix: per-minor cofactors of its leaves
         for (int x = v + 1; x < n; ++x)
           for (int y = x + 1; y < n; ++y) {
             int cm[M];
@@ -387,99 +536,184 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward_prefix(BwdArgs a, Pref
             cm[P + 1] = y;
             minor_cofactors_scatter_global<M>(Ab, a.lda, cm, G, n);
           }
+      }
+      // below, a singular or repeated prefix runs with non-finite or unwanted
+      // values that `use` replaces by zeros
+      const bool use = live && !zp;
+      // W = -L21 L11^{-1} (D x P) and Ainv = U11^{-1} L11^{-1} (P x P)
+      T W[D][P];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+#pragma unroll
+        for (int j = P - 1; j >= 0; --j) {
+          T sum = -fa[P + d][j];
+#pragma unroll
+          for (int i = j + 1; i < P; ++i) sum = fma(-W[d][i], fa[i][j], sum);
+          W[d][j] = sum;
+        }
+      }
+      T Ai[P][P];
+      {
+        T top[P][P];
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+#pragma unroll
+          for (int j = 0; j < P; ++j) top[i][j] = fa[i][j];
+        inverse_factors<P, T>(top, Ai);
+      }
+      int sp = M * (M + 1) / 2 + D;
+#pragma unroll
+      for (int j = 0; j < P; ++j) sp += c[j] + 1;
+      const T alpha = ((sp & 1) != neg) ? -prod : prod;
+      // pass 1: z~ of every candidate column, their sum, and s
+      T zt0 = T(0), zt1 = T(0), ssum = T(0);
+      for (int q = 0; q < k; ++q) {
+        const int col = v + 1 + q;
+        T z[D];
+        prefix_column<T, M, D>(As + col * CS, W, idx, z);
+        if (col & 1) {
+          z[0] = -z[0];
+          z[1] = -z[1];
+        }
+        ssum = fma(zt0, z[1], fma(-zt1, z[0], ssum));  // det[Z_<q, z~_q]
+        zt0 += z[0];
+        zt1 += z[1];
+        zb.put(q, z);
+      }
+      // the gradient of candidate column q at pivot slot r is
+      // (-1)^q alpha ([W^T; I] g_q)[r]; Ca, Cb hold [W^T; I] in row order
+      T Ca[M], Cb[M];
+      {
+        T ca[M], cb[M];
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+          ca[r] = r < P ? W[0][r < P ? r : 0] : (r == P ? T(1) : T(0));
+          cb[r] = r < P ? W[1][r < P ? r : 0] : (r == P + 1 ? T(1) : T(0));
+        }
+        unpermute<T, M>(ca, idx, Ca);
+        unpermute<T, M>(cb, idx, Cb);
+      }
+      // pass 2: candidate-column gradients (summed over the warp) and Q
+      T Q[P][D];
+#pragma unroll
+      for (int i = 0; i < P; ++i) Q[i][0] = Q[i][1] = T(0);
+      T zp0 = T(0), zp1 = T(0);
+      auto column = [&](int q, T (&val)[M]) {
+        const int col = v + 1 + q;
+        T z[D];
+        zb.get(q, z);
+        const T h0 = zt0 - (zp0 + zp0) - z[0], h1 = zt1 - (zp1 + zp1) - z[1];
+        const T g0 = h1, g1 = -h0;  // rot(Z_>q - Z_<q)
+        zp0 += z[0];
+        zp1 += z[1];
+        const T sc = (col & 1) ? -alpha : alpha;
+#pragma unroll
+        for (int i = 0; i < M; ++i) val[i] = use ? sc * fma(Ca[i], g0, Cb[i] * g1) : T(0);
+        const T* xc = As + col * CS;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          const T xt = (col & 1) ? -xc[idx[i]] : xc[idx[i]];
+          Q[i][0] = fma(xt, g0, Q[i][0]);
+          Q[i][1] = fma(xt, g1, Q[i][1]);
+        }
+      };
+      if constexpr (std::is_same<T, ff>::value) {
+        // pairs: one column per warp sum (the column body is long; inlining
+        // it twice measured slower, with instruction-fetch stalls)
+        for (int q = 0; q < k; ++q) {
+          T va[M];
+          column(q, va);
+          warp_add_column<T, M>(va, Gw + v + 1 + q, n, lane);
+        }
       } else {
-        // W = -L21 L11^{-1} (D x P) and Ainv = U11^{-1} L11^{-1} (P x P)
-        T W[D][P];
+        for (int q = 0; q < k; q += 2) {  // binary64: two columns per warp sum
+          const bool two = q + 1 < k;
+          T va[M], vb[M];
+          column(q, va);
+          if (two) {
+            column(q + 1, vb);
+          } else {
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-#pragma unroll
-          for (int j = P - 1; j >= 0; --j) {
-            T sum = -fa[P + d][j];
-#pragma unroll
-            for (int i = j + 1; i < P; ++i) sum = fma(-W[d][i], fa[i][j], sum);
-            W[d][j] = sum;
+            for (int i = 0; i < M; ++i) vb[i] = T(0);
           }
+          warp_add_columns2<T, M>(va, vb, Gw + v + 1 + q, n, lane, two);
         }
-        T Ai[P][P];
-        {
-          T top[P][P];
+      }
+      // prefix columns: alpha [s Ainv - Ainv Q W | -Ainv Q]^T, formed in row
+      // order: with a = (Ainv row tt, 0, 0) in pivot order, row idx[r] of
+      // column c[tt] receives alpha (s a[r] - (Ainv Q)[tt] . [W^T; I][r])
 #pragma unroll
-          for (int i = 0; i < P; ++i)
+      for (int tt = 0; tt < P; ++tt) {
+        T R0 = T(0), R1 = T(0);  // (Ainv Q)[tt][:]
 #pragma unroll
-            for (int j = 0; j < P; ++j) top[i][j] = fa[i][j];
-          inverse_factors<P, T>(top, Ai);
+        for (int u = 0; u < P; ++u) {
+          R0 = fma(Ai[tt][u], Q[u][0], R0);
+          R1 = fma(Ai[tt][u], Q[u][1], R1);
         }
-        int sp = M * (M + 1) / 2 + D;
+        T ai[M], air[M];
 #pragma unroll
-        for (int j = 0; j < P; ++j) sp += c[j] + 1;
-        const T alpha = ((sp & 1) != neg) ? -prod : prod;
-        // pass 1: z~ of every candidate column, their sum, and s
-        T zt0 = T(0), zt1 = T(0), ssum = T(0);
-        for (int q = 0; q < k; ++q) {
-          const int col = v + 1 + q;
-          T z[D];
-          prefix_column<T, M, D>(As + col * CS, W, idx, z);
-          if (col & 1) {
-            z[0] = -z[0];
-            z[1] = -z[1];
+        for (int r = 0; r < M; ++r) ai[r] = r < P ? Ai[tt][r < P ? r : 0] : T(0);
+        unpermute<T, M>(ai, idx, air);
+        T u[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) u[i] = alpha * (ssum * air[i] - fma(R0, Ca[i], R1 * Cb[i]));
+        if (tt == P - 1) {
+#pragma unroll
+          for (int i = 0; i < M; ++i) vacc[i] += use ? u[i] : T(0);
+        } else if (tt < NS) {
+#pragma unroll
+          for (int i = 0; i < M; ++i) {
+            T& h = Hacc[(tt * M + i) * hs];
+            h += use ? u[i] : T(0);
           }
-          ssum = fma(zt0, z[1], fma(-zt1, z[0], ssum));  // det[Z_<q, z~_q]
-          zt0 += z[0];
-          zt1 += z[1];
-          zb.put(q, z);
-        }
-        // pass 2: candidate-column gradients and Q
-        T Q[P][D];
-#pragma unroll
-        for (int i = 0; i < P; ++i) Q[i][0] = Q[i][1] = T(0);
-        T zp0 = T(0), zp1 = T(0);
-        for (int q = 0; q < k; ++q) {
-          const int col = v + 1 + q;
-          T z[D];
-          zb.get(q, z);
-          const T h0 = zt0 - (zp0 + zp0) - z[0], h1 = zt1 - (zp1 + zp1) - z[1];
-          const T g0 = h1, g1 = -h0;  // rot(Z_>q - Z_<q)
-          zp0 += z[0];
-          zp1 += z[1];
-          const T sc = (col & 1) ? -alpha : alpha;
-          double* gcol = G + col;
-#pragma unroll
-          for (int r = 0; r < P; ++r) atomicAdd(gcol + idx[r] * n, to_double(sc * fma(W[0][r], g0, W[1][r] * g1)));
-          atomicAdd(gcol + idx[P] * n, to_double(sc * g0));
-          atomicAdd(gcol + idx[P + 1] * n, to_double(sc * g1));
-          const T* xc = As + col * CS;
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-            const T xt = (col & 1) ? -xc[idx[i]] : xc[idx[i]];
-            Q[i][0] = fma(xt, g0, Q[i][0]);
-            Q[i][1] = fma(xt, g1, Q[i][1]);
-          }
-        }
-        // prefix columns: alpha [s Ainv - Ainv Q W | -Ainv Q]^T
-#pragma unroll
-        for (int tt = 0; tt < P; ++tt) {
-          T R0 = T(0), R1 = T(0);  // (Ainv Q)[tt][:]
-#pragma unroll
-          for (int u = 0; u < P; ++u) {
-            R0 = fma(Ai[tt][u], Q[u][0], R0);
-            R1 = fma(Ai[tt][u], Q[u][1], R1);
-          }
-          double* gcol = G + c[tt];
-#pragma unroll
-          for (int r = 0; r < P; ++r)
-            atomicAdd(gcol + idx[r] * n, to_double(alpha * (ssum * Ai[tt][r] - fma(R0, W[0][r], R1 * W[1][r]))));
-          atomicAdd(gcol + idx[P] * n, to_double(-(alpha * R0)));
-          atomicAdd(gcol + idx[P + 1] * n, to_double(-(alpha * R1)));
+        } else {
+          warp_tile_add<T, M>(Gw, n, use ? c[tt] : -1, u, lane);
         }
       }
       if constexpr (P > 1) {
-        if (r + 1 < r1) successor<P - 1>(head, v);
+        const bool adv = r + 1 < r1;
+        if (adv) successor<P - 1>(head, v);
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+          const bool moved = adv && head[p] != hcol[p];
+          if (__any_sync(kFull, moved)) {  // a slow head column moved on: add its sum
+            T u[M];
+#pragma unroll
+            for (int i = 0; i < M; ++i) u[i] = Hacc[(p * M + i) * hs];
+            warp_tile_add<T, M>(Gw, n, moved ? hcol[p] : -1, u, lane);
+            if (moved) {
+#pragma unroll
+              for (int i = 0; i < M; ++i) Hacc[(p * M + i) * hs] = T(0);
+              hcol[p] = head[p];
+            }
+          }
+        }
+      }
+    }
+    // the task's sums of column v and of the slow head columns
+    warp_add_column<T, M>(vacc, Gw + v, n, lane);
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+      T u[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) u[i] = Hacc[(p * M + i) * hs];
+      const int c0 = __shfl_sync(kFull, hcol[p], 0);
+      if (__all_sync(kFull, !ever || hcol[p] == c0)) {
+        warp_add_column<T, M>(u, Gw + c0, n, lane);
+      } else {
+        warp_tile_add<T, M>(Gw, n, ever ? hcol[p] : -1, u, lane);
       }
     }
   }
   __syncthreads();
+  // the block's tile: the singular-prefix entries plus the warps' tiles in
+  // warp order
   double* slot = a.slots + ((size_t)b * a.chunks + chunk) * (size_t)M * n;
-  for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) slot[idx] = G[idx];
+  for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) {
+    double sum = G[idx];
+    for (int w = 0; w < wpb; ++w) sum += to_double(Gall[(size_t)w * M * n + idx]);
+    slot[idx] = sum;
+  }
 }
 
 // grad_A[b] = grad_out[b] * sum over chunks (in order) of the tiles.
@@ -574,7 +808,10 @@ size_t bwd_prefix_smem(int m, int n) {  // binary64 and pair elements are both 8
   size_t off = ((size_t)(n + 1) * (m + 1) * 8 + 15) / 16 * 16;
   off += ((size_t)n * cs * 8 + 15) / 16 * 16;
   off += ((size_t)m * n * 8 + 15) / 16 * 16;
-  off += zbuf_bytes(n - m + 2, kBwdThreads, 2, 8);
+  off += (zbuf_bytes(n - m + 2, kBwdThreads, 2, 8) + 15) / 16 * 16;
+  const int ns = m - 2 > 2 ? m - 4 : 0;  // per-lane sums of the slow head columns
+  off += (size_t)ns * m * kBwdThreads * 8;
+  off += (size_t)(kBwdThreads / 32) * m * n * 8;  // the warps' gradient tiles
   return off;
 }
 

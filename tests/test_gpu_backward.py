@@ -68,8 +68,9 @@ def test_backward_singular_prefixes(mode):
 
 def test_autograd_function_and_gradcheck():
     A = torch.from_numpy(W.uniform_matrix(5, 3, 6)).cuda().unsqueeze(0).requires_grad_(True)
-    # the backward adds cofactor sums with shared-memory atomics, so repeated
-    # calls agree up to the rounding of the addition order
+    # the prefix backward adds in a fixed order except on its singular-prefix
+    # path, which (like the per-minor backward for m <= 2) uses shared-memory
+    # atomics; nondet_tol covers that addition order
     assert torch.autograd.gradcheck(R().RadicDet.apply, (A,), eps=1e-6, atol=1e-7, rtol=1e-6, nondet_tol=1e-12)
     x = torch.from_numpy(W.uniform_matrix(6, 4, 8)).cuda().requires_grad_(True)
     y = R().radic_det_autograd(x)
@@ -126,3 +127,14 @@ def test_full_diff_256x6x28_mixed_precision(diff_batch):
         assert abs(float(vals[b].detach()) - float(exact)) <= 1e-10 * ABS[b]
     want = np.array([[float(v) for v in row] for row in orc.radic_grad_exact(diff_batch[0], use_pfaffian=True)])
     assert np.abs(grad[0] - want).max() <= 1e-10 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "pair"])
+def test_backward_prefix_deterministic(diff_batch, mode):
+    # with no singular prefix the prefix backward adds every entry in a fixed
+    # order (per-warp tiles, no atomics): repeated calls agree bit for bit
+    A = torch.from_numpy(diff_batch[:64]).cuda()
+    g = torch.ones(64, dtype=torch.float64, device="cuda")
+    first = R().radic_det_backward(A, g, mode=mode)
+    for _ in range(3):
+        assert torch.equal(R().radic_det_backward(A, g, mode=mode), first)
