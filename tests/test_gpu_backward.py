@@ -138,3 +138,55 @@ def test_backward_prefix_deterministic(diff_batch, mode):
     first = R().radic_det_backward(A, g, mode=mode)
     for _ in range(3):
         assert torch.equal(R().radic_det_backward(A, g, mode=mode), first)
+
+
+def _column_norm_symmetric_sum(a):
+    # e_m of the column norms: by Hadamard's inequality an upper bound of
+    # sum over J of |det A[:, J]|, computed on the host without the GPU
+    m = a.shape[0]
+    e = np.zeros(m + 1)
+    e[0] = 1.0
+    for x in np.linalg.norm(a, axis=0):
+        for k in range(m, 0, -1):
+            e[k] += x * e[k - 1]
+    return e[m]
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-12), ("pair", 1e-10)])
+@pytest.mark.parametrize("m,n", [(3, 64), (4, 40), (6, 24), (8, 20)])
+def test_backward_long_rows_against_central_differences(m, n, mode, tol):
+    # many candidate columns per prefix (the largest column buffers and
+    # tiles); det_R is affine in every entry, so the central difference with
+    # step 1 through the oracle's binary64 enumeration is the gradient entry
+    # up to rounding
+    from oracle import cpu_enum
+
+    rng = np.random.default_rng(1000 * m + n)
+    a = rng.uniform(-1, 1, (m, n))
+    grad = R().radic_det_backward(torch.from_numpy(a[None].copy()).cuda(),
+                                  torch.ones(1, dtype=torch.float64, device="cuda"), mode=mode).cpu().numpy()[0]
+    scale = 0.0
+    for i in range(m):
+        for j in range(n):
+            p, q = a.copy(), a.copy()
+            p[i, j] += 1.0
+            q[i, j] -= 1.0
+            fp, sp, _ = cpu_enum.radic_cpu_sum(p)
+            fq, sq, _ = cpu_enum.radic_cpu_sum(q)
+            scale = max(scale, sp, sq)
+            assert abs(grad[i, j] - (fp - fq) / 2) <= tol * scale, (i, j, grad[i, j], (fp - fq) / 2)
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-12), ("pair", 1e-10)])
+def test_backward_largest_tiles_row_identity(mode, tol):
+    # m = 8, n = 64: the largest shared-memory layout.  det_R is linear in
+    # each row, so sum_j a_ij d det_R / d a_ij = det_R(A) for every row i
+    # (Euler's identity, the Laplace expansion of every minor along row i),
+    # checked against the binary64 forward value
+    a = W.uniform_matrix(41, 8, 64)
+    grad = R().radic_det_backward(torch.from_numpy(a[None].copy()).cuda(),
+                                  torch.ones(1, dtype=torch.float64, device="cuda"), mode=mode).cpu().numpy()[0]
+    det = R().det(a, mode="fp64")["value"]
+    bound = _column_norm_symmetric_sum(a)
+    for i in range(8):
+        assert abs(float(np.dot(a[i], grad[i])) - det) <= tol * bound, (i, float(np.dot(a[i], grad[i])), det)
