@@ -249,30 +249,6 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(BwdArgs a) {
   for (int idx = threadIdx.x; idx < M * n; idx += blockDim.x) slot[idx] = G[idx];
 }
 
-// Signed cofactors of one minor (columns c) added into the gradient tile G.
-template <int M>
-__device__ __noinline__ void minor_cofactors_scatter(const double* As, int cs, const int (&c)[M], double* G, int n) {
-  double mm[M][M];
-  for (int j = 0; j < M; ++j)
-    for (int i = 0; i < M; ++i) mm[i][j] = As[c[j] * cs + i];
-  int idx[M];
-  bool zp;
-  const double det = lu_full<M>(mm, idx, zp);
-  const double sgn = sign_negative<M>(c) ? -1.0 : 1.0;
-  if (!zp) {
-    double B[M][M];
-    inverse_factors<M>(mm, B);
-    const double s = sgn * det;
-    for (int sl = 0; sl < M; ++sl)
-      for (int j = 0; j < M; ++j) atomicAdd(G + idx[sl] * n + c[j], s * B[j][sl]);
-  } else {
-    double cof[M][M];
-    cofactors_slow<M>(As, cs, c, cof);
-    for (int i = 0; i < M; ++i)
-      for (int j = 0; j < M; ++j) atomicAdd(G + i * n + c[j], sgn * cof[i][j]);
-  }
-}
-
 // Signed cofactors of one minor read from the binary64 matrix in global
 // memory (row stride lda), added into the gradient tile G.
 template <int M>
